@@ -72,8 +72,9 @@ def _load():
             lib.or_hop.argtypes = [vp, vp, vp, vp, vp, ip, vp, vp, ip]
             lib.or_field_strength.argtypes = [vp, vp, vp]
             lib.or_clover.argtypes = [vp, vp, vp, dp, vp, vp, ip]
-            lib.or_dirac.argtypes = [vp, vp, vp, vp, vp, dp, dp, vp, vp, ip, vp, vp, ip]
-            lib.or_bicgstab.argtypes = [vp, vp, vp, vp, vp, dp, dp, vp, vp, ip, vp, vp,
+            lib.or_clover_matrix.argtypes = [vp, vp, vp, dp, vp]
+            lib.or_dirac.argtypes = [vp, vp, vp, vp, dp, vp, vp, ip, vp, vp, ip]
+            lib.or_bicgstab.argtypes = [vp, vp, vp, vp, dp, vp, vp, ip, vp, vp,
                                         ip, dp, ip, vp, vp]
             lib.or_bicgstab.restype = ip
             lib.or_num_threads.restype = ip
@@ -244,6 +245,14 @@ class WilsonClover:
         self.sig = _c128(sigmas())
         self.F = np.zeros((self.V, 4, 4, 3, 3), np.complex128)
         _load().or_field_strength(_p(self.d), _p(self.U), _p(self.F))
+        # the clover term as one 12x12 matrix per site (same definition)
+        self.Cm = None
+        if self.csw != 0.0:
+            self.Cm = np.zeros((self.V, 12, 12), np.complex128)
+            _load().or_clover_matrix(_p(self.d), _p(self.F), _p(self.sig), self.csw, _p(self.Cm))
+
+    def _cm(self):
+        return _p(self.Cm) if self.Cm is not None else None
 
     def tables(self, profile=None):
         if profile is None:
@@ -278,8 +287,8 @@ class WilsonClover:
         psi, n = self._spin(psi)
         fwd, bwd, ldt, _ = self.tables(profile)
         out = np.empty_like(psi)
-        _load().or_dirac(_p(self.d), _p(self.U), _p(self.F), _p(self.gam), _p(self.sig),
-                         self.csw, float(M), _p(fwd), _p(bwd), ldt, _p(psi), _p(out), n)
+        _load().or_dirac(_p(self.d), _p(self.U), self._cm(), _p(self.gam), float(M), _p(fwd),
+                         _p(bwd), ldt, _p(psi), _p(out), n)
         return out
 
     def solve(self, b, M, profile=None, tol=1e-13, maxit=20000, x0=None):
@@ -289,9 +298,9 @@ class WilsonClover:
         x = np.zeros_like(b) if x0 is None else _c128(x0).copy()
         iters = np.zeros(n, np.int32)
         rel = np.zeros(n)
-        st = _load().or_bicgstab(_p(self.d), _p(self.U), _p(self.F), _p(self.gam),
-                                 _p(self.sig), self.csw, float(M), _p(fwd), _p(bwd), ldt,
-                                 _p(b), _p(x), n, float(tol), int(maxit), _p(iters), _p(rel))
+        st = _load().or_bicgstab(_p(self.d), _p(self.U), self._cm(), _p(self.gam), float(M),
+                                 _p(fwd), _p(bwd), ldt, _p(b), _p(x), n, float(tol), int(maxit),
+                                 _p(iters), _p(rel))
         return x, iters, rel, st == 0
 
 

@@ -233,22 +233,66 @@ void or_clover(const int *d, const cplx *F, const cplx *sigma, double csw,
     }
 }
 
-/* full operator: out = (4+M) psi + hop(psi) + clover(psi) */
-void or_dirac(const int *d, const cplx *U, const cplx *F, const cplx *gam,
-              const cplx *sigma, double csw, double M, const double *fwd,
-              const double *bwd, int ldt, const cplx *psi, cplx *out, int nrhs)
+/*
+ * The same clover term as a 12x12 matrix per site, Cm[i][row][col] with
+ * row/col = spin*3 + colour: Cm = c_sw (i/4) sum_{mu,nu} sigma_{mu nu} (x) Fhat_{mu nu}.
+ */
+void or_clover_matrix(const int *d, const cplx *F, const cplx *sigma, double csw, cplx *Cm)
+{
+    long V = volume(d);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < V; i++) {
+        cplx *m = Cm + i * 144;
+        for (int k = 0; k < 144; k++) m[k] = 0;
+        for (int mu = 0; mu < 4; mu++)
+            for (int nu = 0; nu < 4; nu++) {
+                if (mu == nu) continue;
+                const cplx *f = F + ((i * 4 + mu) * 4 + nu) * 9;
+                const cplx *sg = sigma + (mu * 4 + nu) * 16;
+                for (int s = 0; s < 4; s++)
+                    for (int a = 0; a < 3; a++)
+                        for (int sp = 0; sp < 4; sp++)
+                            for (int b = 0; b < 3; b++)
+                                m[(s * 3 + a) * 12 + sp * 3 + b] += csw * 0.25 * I * sg[s * 4 + sp] * f[a * 3 + b];
+            }
+    }
+}
+
+/* out(x) = Cm(x) psi(x) */
+static void clover_mat_apply(const int *d, const cplx *Cm, const cplx *psi, cplx *out, int nrhs)
+{
+    long V = volume(d);
+    for (int r = 0; r < nrhs; r++) {
+        const cplx *in = psi + (long)r * V * 12;
+        cplx *o = out + (long)r * V * 12;
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < V; i++) {
+            const cplx *m = Cm + i * 144;
+            for (int k = 0; k < 12; k++) {
+                cplx t = 0;
+                for (int l = 0; l < 12; l++) t += m[k * 12 + l] * in[i * 12 + l];
+                o[i * 12 + k] = t;
+            }
+        }
+    }
+}
+
+/* full operator: out = (4+M) psi + hop(psi) + clover(psi); Cm NULL: no clover */
+void or_dirac(const int *d, const cplx *U, const cplx *Cm, const cplx *gam, double M,
+              const double *fwd, const double *bwd, int ldt, const cplx *psi, cplx *out,
+              int nrhs)
 {
     long n = volume(d) * 12 * (long)nrhs;
-    cplx *tmp = (cplx *)malloc(sizeof(cplx) * n);
     or_hop(d, U, gam, fwd, bwd, ldt, psi, out, nrhs);
-    if (csw != 0.0) {
-        or_clover(d, F, sigma, csw, psi, tmp, nrhs);
+    if (Cm) {
+        cplx *tmp = (cplx *)malloc(sizeof(cplx) * n);
+        clover_mat_apply(d, Cm, psi, tmp, nrhs);
 #pragma omp parallel for schedule(static)
         for (long k = 0; k < n; k++) out[k] += tmp[k];
+        free(tmp);
     }
 #pragma omp parallel for schedule(static)
     for (long k = 0; k < n; k++) out[k] += (4.0 + M) * psi[k];
-    free(tmp);
 }
 
 static cplx dot(const cplx *a, const cplx *b, long n)
@@ -274,8 +318,8 @@ static double norm2(const cplx *a, long n) { return creal(dot(a, a, n)); }
  * iters[r] receives the number of operator applications pairs, relres[r] the
  * final true relative residual.  Returns 0 if every RHS converged, else 1.
  */
-int or_bicgstab(const int *d, const cplx *U, const cplx *F, const cplx *gam,
-                const cplx *sigma, double csw, double M, const double *fwd,
+int or_bicgstab(const int *d, const cplx *U, const cplx *Cm, const cplx *gam,
+                double M, const double *fwd,
                 const double *bwd, int ldt, const cplx *b_all, cplx *x_all,
                 int nrhs, double tol, int maxit, int *iters, double *relres)
 {
@@ -298,7 +342,7 @@ int or_bicgstab(const int *d, const cplx *U, const cplx *F, const cplx *gam,
         }
         while (!done && it < maxit) {
             /* (re)start from the true residual */
-            or_dirac(d, U, F, gam, sigma, csw, M, fwd, bwd, ldt, x, r, 1);
+            or_dirac(d, U, Cm, gam, M, fwd, bwd, ldt, x, r, 1);
             for (long k = 0; k < n; k++) r[k] = b[k] - r[k];
             rel = sqrt(norm2(r, n)) / bn;
             if (rel < tol) { done = 1; break; }
@@ -311,12 +355,12 @@ int or_bicgstab(const int *d, const cplx *U, const cplx *F, const cplx *gam,
                 if (cabs(rho_new) == 0.0) break; /* breakdown: restart */
                 cplx beta = (rho_new / rho) * (alpha / omega);
                 for (long k = 0; k < n; k++) p[k] = r[k] + beta * (p[k] - omega * v[k]);
-                or_dirac(d, U, F, gam, sigma, csw, M, fwd, bwd, ldt, p, v, 1);
+                or_dirac(d, U, Cm, gam, M, fwd, bwd, ldt, p, v, 1);
                 cplx rv = dot(rh, v, n);
                 if (cabs(rv) == 0.0) break;
                 alpha = rho_new / rv;
                 for (long k = 0; k < n; k++) s[k] = r[k] - alpha * v[k];
-                or_dirac(d, U, F, gam, sigma, csw, M, fwd, bwd, ldt, s, t, 1);
+                or_dirac(d, U, Cm, gam, M, fwd, bwd, ldt, s, t, 1);
                 it++;
                 double tt = norm2(t, n);
                 if (tt == 0.0) {
@@ -333,7 +377,7 @@ int or_bicgstab(const int *d, const cplx *U, const cplx *F, const cplx *gam,
                 if (cabs(omega) == 0.0) break;
             }
             /* confirm on the true residual (next loop pass recomputes it) */
-            or_dirac(d, U, F, gam, sigma, csw, M, fwd, bwd, ldt, x, r, 1);
+            or_dirac(d, U, Cm, gam, M, fwd, bwd, ldt, x, r, 1);
             for (long k = 0; k < n; k++) r[k] = b[k] - r[k];
             rel = sqrt(norm2(r, n)) / bn;
             if (rel < tol) done = 1;

@@ -87,3 +87,16 @@ def test_clover_term_hermitian():
     a = op.clover(np.einsum("st,...tc->...sc", g5, psi))
     b = np.einsum("st,...tc->...sc", g5, op.clover(psi))
     assert np.abs(a - b).max() < 1e-13
+
+
+def test_operator_is_diagonal_plus_hop_plus_clover():
+    """(D+M) = (4+M) + hopping term + clover term, the clover term applied from
+    its per-site matrix form inside the operator."""
+    dims = (4, 4, 4, 4)
+    op = oracle.WilsonClover(li.su3_links(dims, 0.4, seed=6), dims, csw=1.9)
+    psi = li.random_spinor(dims, 2, 3)
+    M = 0.27
+    prof = ("cosh_4d", 0.3, (1, 2, 3, 0))
+    lhs = op.apply(psi, M, prof)
+    rhs = (4 + M) * psi + op.hop(psi, prof) + op.clover(psi)
+    assert np.abs(lhs - rhs).max() < 1e-13
