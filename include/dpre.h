@@ -1,0 +1,291 @@
+/*
+ * dpre -- distance-preconditioned O(a)-improved Wilson-clover solves on one
+ * NVIDIA GB300 GPU (sm_103a).  C ABI of libdpre.so.
+ *
+ * The method (de Divitiis, Petronzio, Tantalo, arXiv 1006.4028):
+ *   Sec. I, eq. (linsysunprec): solve sum_y (D[U]+M)_{x,y} S(y) = eta(x) for a
+ *     source on one time slice, to a global residue r (eq. stopping).
+ *   Sec. II, eq. (redeft): factor a profile out of the propagator.  This
+ *     library takes the profile in the reciprocal orientation alpha_B = 1/alpha:
+ *     S'(y) = alpha_B(y) S(y), eta'(y) = alpha_B(y) eta(y), and solves
+ *     (D'+M) S' = eta' (eq. linsysprec) with D'+M = A (D+M) A^-1, A = diag(alpha_B).
+ *     Only the hopping terms change: the coefficient of U_mu(x) S'(x+mu) becomes
+ *     alpha_B(x_mu)/alpha_B(x_mu+1) and that of U_mu(x-mu)^dag S'(x-mu) becomes
+ *     alpha_B(x_mu)/alpha_B(x_mu-1) (Sec. II modified derivatives; Sec. III,
+ *     eq. redefcovs, for all four directions), with the antiperiodic time sign on
+ *     the hops across t = T-1 <-> 0 (eq. redeftbc).
+ *   Sec. II, eq. (backcorrection) and Sec. III: restore S = S'/alpha_B per site
+ *     before contracting C_PP(y0) = -sum_{y vec} tr[S^dag(y) S(y)].
+ *
+ * Operator convention (the paper names the O(a)-improved Wilson operator of
+ * Sec. II without writing it out; this is the standard form with r = 1):
+ *   (D+M) psi(x) = (4+M) psi(x)
+ *      - 1/2 sum_mu [ (1-gamma_mu) U_mu(x) psi(x+mu) + (1+gamma_mu) U_mu(x-mu)^dag psi(x-mu) ]
+ *      + c_sw (i/4) sum_{mu,nu} sigma_{mu nu} Fhat_{mu nu}(x) psi(x),
+ *   sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], Fhat = (Q - Q^dag)/8 (4-leaf clover).
+ *   Chiral gamma basis: gamma_mu = [[0, e_mu], [e_mu^dag, 0]], e_0 = -1,
+ *   e_k = -i sigma_k, gamma_5 = gamma_0 gamma_1 gamma_2 gamma_3 = diag(1,1,-1,-1).
+ *
+ * Host data layouts (all complex128 = two doubles, re then im):
+ *   dims = {T, Lx, Ly, Lz}; site index i = ((t*Lz + z)*Ly + y)*Lx + x;
+ *   direction mu = 0 (t), 1 (x), 2 (y), 3 (z).
+ *   links:   [V][4][3][3]       U_mu(x), row a, column b.
+ *   spinor:  [nrhs][V][4][3]    spin, colour.
+ *   prop:    [n_mass][12][V][4][3]  restored S for the 12 source components
+ *            k = 3*spin + colour (solution for source component k).
+ *   cpp:     [n_mass][T]        C_PP(y0), y0 = (t - t_src) mod T.
+ *
+ * Ownership: the caller owns every pointer it passes; the library copies what
+ * it needs during the call and keeps no caller pointer.  Handles (dp_ctx,
+ * dp_field, dp_ticket) belong to the library until released.
+ *
+ * Errors: every entry point returns a dp_status; nothing aborts or throws
+ * across the ABI.  dp_last_error() gives a thread-local message for the last
+ * failing call on the calling thread.  NaN/Inf inputs give DP_ERR_INVALID_ARG.
+ * Every extent must be even (the even-odd split needs neighbours across the
+ * periodic seams to have opposite parity), >= 2 and <= 256.
+ *
+ * Threading: a dp_ctx is used by one thread at a time, except dp_submit,
+ * dp_wait and dp_serve_stats, which may be called from any thread.
+ */
+#ifndef DPRE_H
+#define DPRE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dp_ctx dp_ctx;
+typedef uint64_t dp_field;
+typedef uint64_t dp_ticket;
+
+typedef enum {
+    DP_OK = 0,
+    DP_ERR_INVALID_ARG = 1,
+    DP_ERR_OOM = 2,
+    DP_ERR_NOT_CONVERGED = 3,
+    DP_ERR_BREAKDOWN = 4,
+    DP_ERR_NONFINITE = 5,
+    DP_ERR_TIMEOUT = 6,
+    DP_ERR_REJECTED = 7,
+    DP_ERR_CUDA = 8,
+    DP_ERR_NOT_FOUND = 9
+} dp_status;
+
+/* Profile kinds, all in the alpha_B orientation, coordinates relative to the
+ * source, rel_mu = (x_mu - src_mu) mod L_mu:
+ *   NONE     alpha_B = 1 (unpreconditioned)
+ *   EXP_T    alpha_B = exp(+alpha0 rel_t)                   (Sec. II, SF profile)
+ *   COSH_T   alpha_B = 1/cosh[alpha0 (rel_t - T/2)]          (Sec. II, eq. pbcalpha)
+ *   COSH_4D  alpha_B = prod_mu cosh[alpha0 (rel_mu - L_mu/2)] (Sec. III, eq. betaa)
+ *   TABLE    alpha_B = prod_mu table[mu][x_mu] (absolute coordinates, > 0)   */
+typedef enum {
+    DP_PROF_NONE = 0,
+    DP_PROF_EXP_T = 1,
+    DP_PROF_COSH_T = 2,
+    DP_PROF_COSH_4D = 3,
+    DP_PROF_TABLE = 4
+} dp_prof_kind;
+
+typedef struct {
+    int kind;               /* dp_prof_kind */
+    double alpha0;
+    const double *table[4]; /* TABLE only: alpha_B,mu per coordinate, length L_mu */
+} dp_profile;
+
+typedef enum {
+    DP_PREC_FP64 = 0,       /* FP64 Krylov solve ("FP64 plain" when unbatched)   */
+    DP_PREC_MIXED_FP32 = 1, /* FP32 inner BiCGStab, FP32 links, FP64 outer loop  */
+    DP_PREC_MIXED_FP16 = 2, /* FP32 inner with FP16 links (per-link scale)       */
+    DP_PREC_MIXED_BF16 = 3  /* FP32 inner with BF16 links (per-link scale)       */
+} dp_prec;
+
+typedef enum { DP_SOLVER_BICGSTAB = 0, DP_SOLVER_CGNE = 1 } dp_solver;
+
+typedef struct {
+    int max_iter;     /* total inner iterations allowed (0: 20000)                  */
+    int solver;       /* dp_solver                                                 */
+    int prec;         /* dp_prec                                                   */
+    int compress12;   /* FP32/16-bit links stored as 12 reals (row 2 rebuilt)        */
+    double inner_tol; /* relative reduction per inner solve (0: 1e-5 FP32)          */
+    int batched;      /* 1: all RHS in one multi-RHS solve; 0: one RHS at a time    */
+    int use_graph;    /* capture one solver iteration as a CUDA graph               */
+    int check_every;  /* iterations between convergence reads (0: automatic)        */
+} dp_solve_opts;
+
+typedef struct {
+    int iters_inner;         /* inner Krylov iterations (max over RHS)          */
+    int iters_outer;         /* FP64 true-residual corrections                  */
+    double true_rel_residue; /* max over RHS of |eta'-(D'+M)S'|/|eta'|, FP64, full lattice */
+    double seconds;          /* wall time of the call                           */
+    int n_rhs;               /* right-hand sides solved                         */
+    int status;              /* dp_status of this solve                         */
+} dp_solve_info;
+
+/* Optional device allocator.  alloc returns device memory of >= bytes, 256-byte
+ * aligned, usable on `stream`; free releases it.  NULL hooks: cudaMallocAsync
+ * / cudaFreeAsync on the context stream. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} dp_alloc_hooks;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t to run
+ * on (NULL: the library creates its own non-blocking stream). */
+dp_status dp_create(dp_ctx **out, int device, const dp_alloc_hooks *hooks, void *stream);
+void dp_destroy(dp_ctx *ctx);
+const char *dp_last_error(void);
+/* Device memory the library holds for this context, in bytes. */
+size_t dp_device_bytes(dp_ctx *ctx);
+
+/* ---- gauge fields (Sec. I: D[U]; Sec. II: O(a)-improved operator) -------- */
+
+/* Upload and pack a gauge field: lexicographic complex128 links (layout above)
+ * to even-odd, site-blocked SoA on the device in FP64 (18 reals), FP32 (12 and
+ * 18 reals) and 16-bit (12 reals + one FP32 scale per link) copies.
+ * bc_t = -1 antiperiodic time (the paper's case, Sec. II), +1 periodic. */
+dp_status dp_field_load(dp_ctx *ctx, const double *links, const int dims[4], int bc_t,
+                        dp_field *out);
+/* Build the clover term c_sw (i/4) sigma.Fhat for this field (FP64, two
+ * Hermitian 6x6 chiral blocks per site). */
+dp_status dp_field_set_csw(dp_ctx *ctx, dp_field field, double csw);
+dp_status dp_field_free(dp_ctx *ctx, dp_field field);
+
+/* ---- solves (Sec. I-III: source scaling, solve, restore, contract) ------- */
+
+/* Point source at src = {t, x, y, z} for all 12 spin-colour components, one
+ * mass M and profile.  Scales the source by alpha_B(x_src), solves the
+ * even-odd Schur system of (D'+M) to relative residue r (stopping on the
+ * preconditioned system, Sec. II), reconstructs the odd sites, restores
+ * S = S'/alpha_B per site and contracts C_PP.  cpp_out: host [T]; prop_out:
+ * NULL or host [12][V][4][3] restored propagator; info may be NULL.
+ * Returns DP_ERR_NOT_CONVERGED if max_iter ran out (results still written). */
+dp_status dp_solve_point(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
+                         const int src[4], double r, const dp_solve_opts *opts,
+                         double *cpp_out, double *prop_out, dp_solve_info *info);
+
+/* Several masses, each with its own profile, sharing one point source: all
+ * 12 x n_mass RHS run in one multi-RHS solve.  cpp_out: host [n_mass][T];
+ * prop_out NULL or host [n_mass][12][V][4][3]; info NULL or [n_mass]. */
+dp_status dp_solve_point_multi(dp_ctx *ctx, dp_field field, int n_mass, const double *M,
+                               const dp_profile *profiles, const int src[4], double r,
+                               const dp_solve_opts *opts, double *cpp_out, double *prop_out,
+                               dp_solve_info *info);
+
+/* As dp_solve_point_multi, but cpp_out is DEVICE memory ([n_mass][T] doubles)
+ * written on the context stream; nothing is copied to the host except the
+ * convergence flags the iteration loop reads. */
+dp_status dp_solve_point_dev(dp_ctx *ctx, dp_field field, int n_mass, const double *M,
+                             const dp_profile *profiles, const int src[4], double r,
+                             const dp_solve_opts *opts, double *cpp_out_dev,
+                             dp_solve_info *info);
+
+/* ---- operator application (host buffers; for checks and small jobs) ----- */
+
+typedef enum {
+    DP_APPLY_HOP = 0,       /* hopping part only (with profile factors)        */
+    DP_APPLY_CLOVER = 1,    /* clover term c_sw (i/4) sigma.Fhat only            */
+    DP_APPLY_FULL = 2,      /* (D'+M) psi                                        */
+    DP_APPLY_CLOVER_INV = 3 /* (4 + M + clover)^-1 psi                           */
+} dp_apply_kind;
+
+/* out = op(in) for nrhs host spinors [nrhs][V][4][3] (complex128), computed
+ * in precision `prec` (DP_PREC_FP64 or DP_PREC_MIXED_FP32: FP32 kernels with
+ * FP32-rounded inputs).  The profile is placed relative to src (NULL src: the
+ * origin).  compress12 selects 12-real FP32 links. */
+dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_profile *profile,
+                   const int src[4], int prec, int compress12, const double *in, double *out,
+                   int nrhs);
+
+/* Host-only (no GPU needed): the profile factors and hop coefficients the
+ * solver uses for this geometry, profile and source.  alpha_out: [4][Lmax]
+ * alpha_B,mu(x_mu); hop_out: [4][2][Lmax], [mu][0][x] = -1/2 alpha_B(x)/
+ * alpha_B(x+1) (forward), [mu][1][x] = -1/2 alpha_B(x)/alpha_B(x-1)
+ * (backward), with bc_t on the hops across t = T-1 <-> 0 (Sec. II modified
+ * derivatives, eq. redeftbc; Sec. III eq. redefcovs).  Lmax = max(dims);
+ * entries beyond L_mu are 1 (alpha) and 0 (hop). */
+dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profile,
+                            const int src[4], double *alpha_out, double *hop_out);
+
+/* ---- device-resident operator for benchmarks and the autotuner ---------- */
+
+/* One hopping application D_{p,1-p} with the fused clover-inverse epilogue
+ * (out = A_pp^-1 D_{p,1-p} in), on packed even-odd device spinors of nrhs
+ * right-hand sides: layout [chunk][V/2][nrhs] with chunk = float4 (6 per
+ * spinor, FP32) or double2 (12, FP64).  `in`/`out` are device pointers the
+ * caller allocated with dp_spinor_bytes().  Launch shape from the tuner
+ * unless block_threads > 0.  iters launches back to back; if ms_out is
+ * non-NULL it receives the average launch time measured with CUDA events on
+ * the context stream. */
+size_t dp_spinor_bytes(dp_ctx *ctx, dp_field field, int prec, int nrhs);
+dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
+                        int prec, int compress12, int out_parity, const void *in, void *out,
+                        int nrhs, int block_threads, int rhs_per_thread, int iters,
+                        float *ms_out);
+
+/* ---- autotuner ----------------------------------------------------------- */
+
+/* Time candidate launch shapes (threads per block, RHS per thread) of the
+ * multi-RHS dslash for this field, precision and nrhs, and keep the fastest
+ * for later launches.  best_* may be NULL. */
+dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int nrhs,
+                      int *best_block_threads, int *best_rhs_per_thread, float *best_ms);
+
+/* ---- per-kernel timing (CUDA events on the context stream) ---------------- */
+
+/* Enable (1) or disable (0) event timing around every kernel launch the
+ * solvers make; statistics accumulate per kernel name until reset. */
+dp_status dp_timing_enable(dp_ctx *ctx, int on);
+dp_status dp_timing_reset(dp_ctx *ctx);
+/* Statistics of kernel class `name` ("dslash_fp32", "dslash_fp64", "blas",
+ * "reduce", ...): launches and total milliseconds.  Synchronises the stream. */
+dp_status dp_timing_get(dp_ctx *ctx, const char *name, long *launches, double *total_ms);
+/* Kernel launches made by this context since creation. */
+long dp_launch_count(dp_ctx *ctx);
+
+/* ---- serving: continuous batching over resident fields -------------------- */
+
+typedef struct {
+    dp_field field;
+    double M;
+    dp_profile profile;   /* TABLE pointers are copied at submit time */
+    int src[4];
+    double r;
+    int prec;             /* dp_prec */
+} dp_request;
+
+typedef struct {
+    long submitted, completed, rejected, in_flight;
+    double p50_ms, p99_ms, mean_ms; /* submit -> completion latency */
+    double solves_per_s;            /* completions / (last - first completion) */
+    size_t hbm_budget, hbm_in_use;
+} dp_serve_stats;
+
+/* Start the scheduler thread.  hbm_budget: bytes of solver state the
+ * scheduler may hold for admitted requests (0: 80% of free memory);
+ * max_slots: RHS slots per field batch (multiple of 12, 0: 48). */
+dp_status dp_serve_start(dp_ctx *ctx, size_t hbm_budget, int max_slots);
+/* Queue a request; the library copies it.  DP_ERR_REJECTED if it can never fit
+ * the HBM budget or the scheduler is not running. */
+dp_status dp_submit(dp_ctx *ctx, const dp_request *req, dp_ticket *ticket);
+/* Wait up to timeout_s (< 0: forever) for a ticket; DP_ERR_TIMEOUT if not done.
+ * cpp_out: host [T] of the request's field; info may be NULL. */
+dp_status dp_wait(dp_ctx *ctx, dp_ticket ticket, double timeout_s, double *cpp_out,
+                  dp_solve_info *info);
+/* Cancel a queued (not yet admitted) request. */
+dp_status dp_cancel(dp_ctx *ctx, dp_ticket ticket);
+dp_status dp_serve_stats_get(dp_ctx *ctx, dp_serve_stats *out);
+/* Stop the scheduler after draining (drain=1) or cancelling (drain=0) queued work. */
+dp_status dp_serve_stop(dp_ctx *ctx, int drain);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPRE_H */

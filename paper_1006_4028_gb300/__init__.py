@@ -1,0 +1,400 @@
+"""Python binding of libdpre, the GB300 library for distance-preconditioned
+Wilson-clover solves (arXiv 1006.4028).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libdpre.so`` (built in-tree by :mod:`.build`).  The functions keep
+the names of the C ABI declared in ``include/dpre.h``.  There is no CPU
+fallback: if the library is missing or no GPU is present the calls raise.
+
+Host arrays use numpy complex128 in the lexicographic layouts of the header:
+links ``(T, Lz, Ly, Lx, 4, 3, 3)``, spinors ``(nrhs, T, Lz, Ly, Lx, 4, 3)``.
+Profiles are given as ``(kind, alpha0)`` or ``(kind, alpha0, tables)`` with
+kind one of ``"none", "exp_t", "cosh_t", "cosh_4d", "table"`` (alpha_B
+orientation: S' = alpha_B S, see the header).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "DpError", "load", "lib_path",
+    "dp_create", "dp_destroy", "dp_last_error", "dp_device_bytes",
+    "dp_field_load", "dp_field_set_csw", "dp_field_free",
+    "dp_solve_point", "dp_solve_point_multi", "dp_solve_point_dev",
+    "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_autotune",
+    "dp_timing_enable", "dp_timing_reset", "dp_timing_get", "dp_launch_count",
+    "dp_serve_start", "dp_submit", "dp_wait", "dp_cancel", "dp_serve_stats_get", "dp_serve_stop",
+    "PROFILE_KINDS", "PREC", "APPLY", "STATUS",
+]
+
+PROFILE_KINDS = {"none": 0, "exp_t": 1, "cosh_t": 2, "cosh_4d": 3, "table": 4}
+PREC = {"fp64": 0, "mixed_fp32": 1, "mixed_fp16": 2, "mixed_bf16": 3}
+APPLY = {"hop": 0, "clover": 1, "full": 2, "clover_inv": 3}
+STATUS = {0: "DP_OK", 1: "DP_ERR_INVALID_ARG", 2: "DP_ERR_OOM", 3: "DP_ERR_NOT_CONVERGED",
+          4: "DP_ERR_BREAKDOWN", 5: "DP_ERR_NONFINITE", 6: "DP_ERR_TIMEOUT", 7: "DP_ERR_REJECTED",
+          8: "DP_ERR_CUDA", 9: "DP_ERR_NOT_FOUND"}
+
+
+class DpError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+        self.message = message
+
+
+class Profile(C.Structure):
+    _fields_ = [("kind", C.c_int), ("alpha0", C.c_double), ("table", C.POINTER(C.c_double) * 4)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("max_iter", C.c_int), ("solver", C.c_int), ("prec", C.c_int),
+                ("compress12", C.c_int), ("inner_tol", C.c_double), ("batched", C.c_int),
+                ("use_graph", C.c_int), ("check_every", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters_inner", C.c_int), ("iters_outer", C.c_int),
+                ("true_rel_residue", C.c_double), ("seconds", C.c_double),
+                ("n_rhs", C.c_int), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(C.Structure):
+    _fields_ = [("field", C.c_uint64), ("M", C.c_double), ("profile", Profile),
+                ("src", C.c_int * 4), ("r", C.c_double), ("prec", C.c_int)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_long), ("completed", C.c_long), ("rejected", C.c_long),
+                ("in_flight", C.c_long), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("mean_ms", C.c_double), ("solves_per_s", C.c_double),
+                ("hbm_budget", C.c_size_t), ("hbm_in_use", C.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load libdpre.so (raises if it has not been built and building is off)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise ImportError("libdpre.so is not built (%s); run paper_1006_4028_gb300.build.build()"
+                              % _build.LIB)
+        _build.build()
+    lib = C.CDLL(_build.LIB)
+    vp, ip, dp, up, sz = C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_size_t
+    P = C.POINTER
+    sig = {
+        "dp_create": ([P(vp), ip, vp, vp], ip),
+        "dp_destroy": ([vp], None),
+        "dp_last_error": ([], C.c_char_p),
+        "dp_device_bytes": ([vp], sz),
+        "dp_field_load": ([vp, vp, P(C.c_int * 4), ip, P(up)], ip),
+        "dp_field_set_csw": ([vp, up, dp], ip),
+        "dp_field_free": ([vp, up], ip),
+        "dp_solve_point": ([vp, up, dp, P(Profile), P(C.c_int * 4), dp, P(SolveOpts), vp, vp,
+                            P(SolveInfo)], ip),
+        "dp_solve_point_multi": ([vp, up, ip, vp, vp, P(C.c_int * 4), dp, P(SolveOpts), vp, vp,
+                                  vp], ip),
+        "dp_solve_point_dev": ([vp, up, ip, vp, vp, P(C.c_int * 4), dp, P(SolveOpts), vp, vp], ip),
+        "dp_apply": ([vp, up, ip, dp, P(Profile), P(C.c_int * 4), ip, ip, vp, vp, ip], ip),
+        "dp_profile_tables": ([P(C.c_int * 4), ip, P(Profile), P(C.c_int * 4), vp, vp], ip),
+        "dp_spinor_bytes": ([vp, up, ip, ip], sz),
+        "dp_dslash_dev": ([vp, up, dp, P(Profile), ip, ip, ip, vp, vp, ip, ip, ip, ip,
+                           P(C.c_float)], ip),
+        "dp_autotune": ([vp, up, ip, ip, ip, P(C.c_int), P(C.c_int), P(C.c_float)], ip),
+        "dp_timing_enable": ([vp, ip], ip),
+        "dp_timing_reset": ([vp], ip),
+        "dp_timing_get": ([vp, C.c_char_p, P(C.c_long), P(C.c_double)], ip),
+        "dp_launch_count": ([vp], C.c_long),
+        "dp_serve_start": ([vp, sz, ip], ip),
+        "dp_submit": ([vp, P(Request), P(up)], ip),
+        "dp_wait": ([vp, up, dp, vp, P(SolveInfo)], ip),
+        "dp_cancel": ([vp, up], ip),
+        "dp_serve_stats_get": ([vp, P(ServeStats)], ip),
+        "dp_serve_stop": ([vp, ip], ip),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def dp_last_error():
+    return load().dp_last_error().decode(errors="replace")
+
+
+def _check(st, allow=()):
+    if st != 0 and st not in allow:
+        raise DpError(st, dp_last_error())
+    return st
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data)
+
+
+def _profile(p, dims=None):
+    """(kind, alpha0[, tables]) -> (Profile, keepalive)."""
+    pr = Profile()
+    keep = []
+    if p is None:
+        p = ("none", 0.0)
+    kind = p[0]
+    pr.kind = PROFILE_KINDS[kind] if isinstance(kind, str) else int(kind)
+    pr.alpha0 = float(p[1]) if len(p) > 1 else 0.0
+    if len(p) > 2 and p[2] is not None:
+        for mu in range(4):
+            t = np.ascontiguousarray(p[2][mu], dtype=np.float64)
+            keep.append(t)
+            pr.table[mu] = t.ctypes.data_as(C.POINTER(C.c_double))
+    return pr, keep
+
+
+def _opts(o):
+    s = SolveOpts()
+    o = dict(o or {})
+    s.max_iter = int(o.get("max_iter", 0))
+    s.solver = int(o.get("solver", 0))
+    prec = o.get("prec", "mixed_fp32")
+    s.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    s.compress12 = int(o.get("compress12", 1))
+    s.inner_tol = float(o.get("inner_tol", 0.0))
+    s.batched = int(o.get("batched", 1))
+    s.use_graph = int(o.get("use_graph", 1))
+    s.check_every = int(o.get("check_every", 0))
+    return s
+
+
+def _i4(v):
+    return (C.c_int * 4)(*[int(x) for x in v])
+
+
+# ---- context --------------------------------------------------------------
+def dp_create(device=0, stream=None):
+    """Create a context; `stream` is a cudaStream_t handle (int) or None."""
+    lib = load()
+    h = C.c_void_p()
+    _check(lib.dp_create(C.byref(h), int(device), None, C.c_void_p(stream) if stream else None))
+    return h
+
+
+def dp_destroy(ctx):
+    load().dp_destroy(ctx)
+
+
+def dp_device_bytes(ctx):
+    return int(load().dp_device_bytes(ctx))
+
+
+# ---- fields -----------------------------------------------------------------
+def dp_field_load(ctx, links, dims, bc_t=-1):
+    U = np.ascontiguousarray(links, dtype=np.complex128)
+    T, Lx, Ly, Lz = (int(d) for d in dims)
+    if U.size != T * Lx * Ly * Lz * 36:
+        raise ValueError("links must hold V*4*3*3 complex entries")
+    f = C.c_uint64()
+    _check(load().dp_field_load(ctx, _ptr(U), C.byref(_i4(dims)), int(bc_t), C.byref(f)))
+    return f.value
+
+
+def dp_field_set_csw(ctx, field, csw):
+    _check(load().dp_field_set_csw(ctx, int(field), float(csw)))
+
+
+def dp_field_free(ctx, field):
+    _check(load().dp_field_free(ctx, int(field)))
+
+
+# ---- solves -------------------------------------------------------------------
+def dp_solve_point(ctx, field, M, profile, src, r, opts=None, T=None, V=None, want_prop=False,
+                   allow=(3,)):
+    """Point-source solve for 12 spin-colour RHS.  Returns (cpp[T], prop, info).
+
+    `T` (and `V` if want_prop) give the lattice sizes of the field.
+    """
+    pr, keep = _profile(profile)
+    cpp = np.zeros(int(T))
+    prop = np.zeros((12, int(V), 4, 3), np.complex128) if want_prop else None
+    info = SolveInfo()
+    o = _opts(opts)
+    st = load().dp_solve_point(ctx, int(field), float(M), C.byref(pr), C.byref(_i4(src)), float(r),
+                               C.byref(o), _ptr(cpp), _ptr(prop) if want_prop else None,
+                               C.byref(info))
+    _check(st, allow)
+    return cpp, prop, info.as_dict()
+
+
+def dp_solve_point_multi(ctx, field, Ms, profiles, src, r, opts=None, T=None, V=None,
+                         want_prop=False, allow=(3,)):
+    """Several masses (each with its profile) for one point source, one batch.
+
+    Returns (cpp[n_mass, T], prop or None, [info dict per mass])."""
+    n = len(Ms)
+    Ma = np.ascontiguousarray(Ms, dtype=np.float64)
+    profs = (Profile * n)()
+    keep = []
+    for k, p in enumerate(profiles):
+        pr, kp = _profile(p)
+        profs[k] = pr
+        keep += kp
+    cpp = np.zeros((n, int(T)))
+    prop = np.zeros((n, 12, int(V), 4, 3), np.complex128) if want_prop else None
+    infos = (SolveInfo * n)()
+    o = _opts(opts)
+    st = load().dp_solve_point_multi(ctx, int(field), n, _ptr(Ma), C.cast(profs, C.c_void_p),
+                                     C.byref(_i4(src)), float(r), C.byref(o), _ptr(cpp),
+                                     _ptr(prop) if want_prop else None, C.cast(infos, C.c_void_p))
+    _check(st, allow)
+    return cpp, prop, [i.as_dict() for i in infos]
+
+
+def dp_solve_point_dev(ctx, field, Ms, profiles, src, r, cpp_out_dev, opts=None, allow=(3,)):
+    """As dp_solve_point_multi with C_PP written to device memory at address
+    `cpp_out_dev` (an int, e.g. a torch tensor's data_ptr()); returns infos."""
+    n = len(Ms)
+    Ma = np.ascontiguousarray(Ms, dtype=np.float64)
+    profs = (Profile * n)()
+    keep = []
+    for k, p in enumerate(profiles):
+        pr, kp = _profile(p)
+        profs[k] = pr
+        keep += kp
+    infos = (SolveInfo * n)()
+    o = _opts(opts)
+    st = load().dp_solve_point_dev(ctx, int(field), n, _ptr(Ma), C.cast(profs, C.c_void_p),
+                                   C.byref(_i4(src)), float(r), C.byref(o),
+                                   C.c_void_p(int(cpp_out_dev)), C.cast(infos, C.c_void_p))
+    _check(st, allow)
+    return [i.as_dict() for i in infos]
+
+
+# ---- operator application -------------------------------------------------------
+def dp_apply(ctx, field, kind, M, profile, src, prec, psi, compress12=1):
+    """out = op(psi) for host spinors (nrhs, T, Lz, Ly, Lx, 4, 3) complex128."""
+    x = np.ascontiguousarray(psi, dtype=np.complex128)
+    nrhs = x.shape[0]
+    out = np.empty_like(x)
+    pr, keep = _profile(profile)
+    k = APPLY[kind] if isinstance(kind, str) else int(kind)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check(load().dp_apply(ctx, int(field), k, float(M), C.byref(pr), C.byref(_i4(src or (0, 0, 0, 0))),
+                           p, int(compress12), _ptr(x), _ptr(out), int(nrhs)))
+    return out
+
+
+def dp_profile_tables(dims, bc_t, profile, src=(0, 0, 0, 0)):
+    """Host-side profile factors and hop coefficients: (alpha[4, Lmax], hop[4, 2, Lmax])."""
+    Lm = max(int(d) for d in dims)
+    alpha = np.zeros((4, Lm))
+    hop = np.zeros((4, 2, Lm))
+    pr, keep = _profile(profile)
+    _check(load().dp_profile_tables(C.byref(_i4(dims)), int(bc_t), C.byref(pr), C.byref(_i4(src)),
+                                    _ptr(alpha), _ptr(hop)))
+    return alpha, hop
+
+
+def dp_spinor_bytes(ctx, field, prec, nrhs):
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    return int(load().dp_spinor_bytes(ctx, int(field), p, int(nrhs)))
+
+
+def dp_dslash_dev(ctx, field, M, profile, prec, compress12, out_parity, in_ptr, out_ptr, nrhs,
+                  block_threads=0, rhs_per_thread=0, iters=1):
+    """Device-resident hopping application with the A^-1 epilogue; returns the
+    average launch time in ms (CUDA events on the context stream)."""
+    pr, keep = _profile(profile)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    ms = C.c_float()
+    _check(load().dp_dslash_dev(ctx, int(field), float(M), C.byref(pr), p, int(compress12),
+                                int(out_parity), C.c_void_p(int(in_ptr)), C.c_void_p(int(out_ptr)),
+                                int(nrhs), int(block_threads), int(rhs_per_thread), int(iters),
+                                C.byref(ms)))
+    return ms.value
+
+
+def dp_autotune(ctx, field, prec, compress12, nrhs):
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    b, rpt, ms = C.c_int(), C.c_int(), C.c_float()
+    _check(load().dp_autotune(ctx, int(field), p, int(compress12), int(nrhs), C.byref(b),
+                              C.byref(rpt), C.byref(ms)))
+    return b.value, rpt.value, ms.value
+
+
+# ---- timing ----------------------------------------------------------------------
+def dp_timing_enable(ctx, on=True):
+    _check(load().dp_timing_enable(ctx, 1 if on else 0))
+
+
+def dp_timing_reset(ctx):
+    _check(load().dp_timing_reset(ctx))
+
+
+def dp_timing_get(ctx, name):
+    n, ms = C.c_long(), C.c_double()
+    _check(load().dp_timing_get(ctx, name.encode(), C.byref(n), C.byref(ms)))
+    return n.value, ms.value
+
+
+def dp_launch_count(ctx):
+    return int(load().dp_launch_count(ctx))
+
+
+# ---- serving -------------------------------------------------------------------------
+def dp_serve_start(ctx, hbm_budget=0, max_slots=0):
+    _check(load().dp_serve_start(ctx, int(hbm_budget), int(max_slots)))
+
+
+def dp_submit(ctx, field, M, profile, src, r, prec="mixed_fp32"):
+    rq = Request()
+    rq.field = int(field)
+    rq.M = float(M)
+    pr, keep = _profile(profile)
+    rq.profile = pr
+    rq.src = _i4(src)
+    rq.r = float(r)
+    rq.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    t = C.c_uint64()
+    _check(load().dp_submit(ctx, C.byref(rq), C.byref(t)))
+    return t.value
+
+
+def dp_wait(ctx, ticket, T, timeout_s=-1.0, allow=(3,)):
+    cpp = np.zeros(int(T))
+    info = SolveInfo()
+    st = load().dp_wait(ctx, int(ticket), float(timeout_s), _ptr(cpp), C.byref(info))
+    _check(st, allow)
+    return cpp, info.as_dict()
+
+
+def dp_cancel(ctx, ticket):
+    _check(load().dp_cancel(ctx, int(ticket)))
+
+
+def dp_serve_stats_get(ctx):
+    s = ServeStats()
+    _check(load().dp_serve_stats_get(ctx, C.byref(s)))
+    return s.as_dict()
+
+
+def dp_serve_stop(ctx, drain=True):
+    _check(load().dp_serve_stop(ctx, 1 if drain else 0))

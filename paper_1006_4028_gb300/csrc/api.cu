@@ -1,0 +1,821 @@
+// C ABI of libdpre: contexts, gauge fields, operator application, the
+// device-resident dslash entry point, the launch tuner and kernel timing.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ctx.h"
+
+namespace dp {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+#define CUDA_OK(expr)                                                            \
+    do {                                                                         \
+        cudaError_t e_ = (expr);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            set_error("%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return DP_ERR_CUDA;                                                  \
+        }                                                                        \
+    } while (0)
+
+void *Ctx::alloc(size_t n)
+{
+    if (n == 0) n = 256;
+    void *p = nullptr;
+    if (has_hooks) {
+        p = hooks.alloc(n, (void *)stream, hooks.user);
+    } else if (cudaMallocAsync(&p, n, stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        std::lock_guard<std::mutex> lk(mu);
+        allocs[p] = n;
+        bytes += n;
+    }
+    return p;
+}
+
+void Ctx::release(void *p)
+{
+    if (!p) return;
+    size_t n = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = allocs.find(p);
+        if (it == allocs.end()) return;
+        n = it->second;
+        bytes -= n;
+        allocs.erase(it);
+    }
+    if (has_hooks)
+        hooks.free(p, n, (void *)stream, hooks.user);
+    else
+        cudaFreeAsync(p, stream);
+}
+
+cudaEvent_t Ctx::get_event()
+{
+    if (!event_pool.empty()) {
+        cudaEvent_t e = event_pool.back();
+        event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void Ctx::time_begin(const char *name, cudaEvent_t *a)
+{
+    (void)name;
+    *a = nullptr;
+    if (!timing) return;
+    *a = get_event();
+    cudaEventRecord(*a, stream);
+}
+
+void Ctx::time_end(const char *name, cudaEvent_t a)
+{
+    if (!timing || !a) return;
+    cudaEvent_t b = get_event();
+    cudaEventRecord(b, stream);
+    pending.push_back({name, a, b});
+    if (pending.size() > 4096) collect_timing();
+}
+
+void Ctx::collect_timing()
+{
+    if (pending.empty()) return;
+    cudaStreamSynchronize(stream);
+    for (auto &p : pending) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        Stat &s = stats[p.name];
+        s.launches++;
+        s.ms += ms;
+        event_pool.push_back(p.a);
+        event_pool.push_back(p.b);
+    }
+    pending.clear();
+}
+
+int Ctx::block_for(long long Vh, int prec, int link_fmt, int nrhs)
+{
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = tuned_block.find(TuneKey{Vh, prec, link_fmt, nrhs});
+    if (it != tuned_block.end()) return it->second;
+    return prec == 0 ? 128 : 256;
+}
+
+std::shared_ptr<Field> find_field(Ctx *c, dp_field f)
+{
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->fields.find(f);
+    if (it == c->fields.end()) return nullptr;
+    return it->second;
+}
+
+dp_status profile_tables(const dp_profile &p, const Geom &g, int bc_t, const int src[4],
+                         double *alpha, double *hop)
+{
+    const int L[4] = {g.T, g.Lx, g.Ly, g.Lz};
+    const int Lm = g.Lmax;
+    if (!std::isfinite(p.alpha0)) {
+        set_error("profile alpha0 is not finite");
+        return DP_ERR_INVALID_ARG;
+    }
+    for (int mu = 0; mu < 4; mu++) {
+        for (int x = 0; x < Lm; x++) alpha[mu * Lm + x] = 1.0;
+        for (int x = 0; x < L[mu]; x++) {
+            const int rel = ((x - src[mu]) % L[mu] + L[mu]) % L[mu];
+            const double h = 0.5 * L[mu];
+            double a = 1.0;
+            switch (p.kind) {
+            case DP_PROF_NONE: a = 1.0; break;
+            case DP_PROF_EXP_T: a = mu == 0 ? std::exp(p.alpha0 * rel) : 1.0; break;
+            case DP_PROF_COSH_T: a = mu == 0 ? 1.0 / std::cosh(p.alpha0 * (rel - h)) : 1.0; break;
+            case DP_PROF_COSH_4D: a = std::cosh(p.alpha0 * (rel - h)); break;
+            case DP_PROF_TABLE:
+                if (!p.table[mu]) {
+                    set_error("TABLE profile without table for direction %d", mu);
+                    return DP_ERR_INVALID_ARG;
+                }
+                a = p.table[mu][x];
+                break;
+            default: set_error("unknown profile kind %d", p.kind); return DP_ERR_INVALID_ARG;
+            }
+            if (!(a > 0) || !std::isfinite(a)) {
+                set_error("profile value not positive and finite (dir %d, x %d)", mu, x);
+                return DP_ERR_INVALID_ARG;
+            }
+            alpha[mu * Lm + x] = a;
+        }
+    }
+    for (int mu = 0; mu < 4; mu++) {
+        for (int x = 0; x < 2 * Lm; x++) hop[mu * 2 * Lm + x] = 0.0;
+        for (int x = 0; x < L[mu]; x++) {
+            const int xp = (x + 1) % L[mu], xm = (x + L[mu] - 1) % L[mu];
+            const double sf = (mu == 0 && x == L[mu] - 1) ? bc_t : 1.0;
+            const double sb = (mu == 0 && x == 0) ? bc_t : 1.0;
+            const double *a = alpha + mu * Lm;
+            hop[(mu * 2 + 0) * Lm + x] = -0.5 * sf * a[x] / a[xp];
+            hop[(mu * 2 + 1) * Lm + x] = -0.5 * sb * a[x] / a[xm];
+        }
+    }
+    return DP_OK;
+}
+
+CloverInv::~CloverInv()
+{
+    if (!owner) return;
+    for (int p = 0; p < 2; p++) {
+        owner->release(inv64[p]);
+        owner->release(inv32[p]);
+    }
+}
+
+dp_status get_clover_inv(Ctx *c, Field &f, double M, std::shared_ptr<CloverInv> *out)
+{
+    if (!f.has_clover) {
+        set_error("clover term not built: call dp_field_set_csw first");
+        return DP_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(f.inv_mu);
+    for (size_t k = 0; k < f.invs.size(); k++)
+        if (f.invs[k]->M == M) {
+            auto ci = f.invs[k];  // move to the most-recently-used end
+            f.invs.erase(f.invs.begin() + k);
+            f.invs.push_back(ci);
+            *out = ci;
+            return DP_OK;
+        }
+    auto ci = std::make_shared<CloverInv>();
+    ci->owner = c;
+    ci->M = M;
+    const long long Vh = f.g.Vh;
+    for (int p = 0; p < 2; p++) {
+        ci->inv64[p] = (double2 *)c->alloc(Vh * 36 * sizeof(double2));
+        ci->inv32[p] = (float4 *)c->alloc(Vh * 18 * sizeof(float4));
+        if (!ci->inv64[p] || !ci->inv32[p]) {
+            set_error("out of device memory (clover inverse)");
+            return DP_ERR_OOM;
+        }
+    }
+    int *flag = (int *)c->alloc(sizeof(int));
+    if (!flag) {
+        set_error("out of device memory (clover inverse)");
+        return DP_ERR_OOM;
+    }
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+    for (int p = 0; p < 2 && e == cudaSuccess; p++)
+        e = launch_clover_invert(f.clov[p], Vh, M, ci->inv64[p], ci->inv32[p], flag, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->release(flag);
+    c->launches += 2;
+    if (e != cudaSuccess) {
+        set_error("clover inverse: %s", cudaGetErrorString(e));
+        return DP_ERR_CUDA;
+    }
+    if (h) {
+        set_error("clover block (4+M)+clover is singular or non-finite at M=%g", M);
+        return DP_ERR_NONFINITE;
+    }
+    // the cache keeps the 16 most recently used masses per field
+    if (f.invs.size() >= 16) f.invs.erase(f.invs.begin());
+    f.invs.push_back(ci);
+    *out = ci;
+    return DP_OK;
+}
+
+dp_status check_opts(const dp_solve_opts *in, dp_solve_opts *out)
+{
+    dp_solve_opts o{};
+    if (in) o = *in;
+    if (o.max_iter <= 0) o.max_iter = 20000;
+    if (o.prec < DP_PREC_FP64 || o.prec > DP_PREC_MIXED_BF16) {
+        set_error("invalid precision %d", o.prec);
+        return DP_ERR_INVALID_ARG;
+    }
+    if (o.prec == DP_PREC_MIXED_FP16 || o.prec == DP_PREC_MIXED_BF16) {
+        set_error("16-bit link precision is not available in this build");
+        return DP_ERR_INVALID_ARG;
+    }
+    if (o.solver != DP_SOLVER_BICGSTAB) {
+        set_error("solver %d is not available in this build (BiCGStab only)", o.solver);
+        return DP_ERR_INVALID_ARG;
+    }
+    if (!(o.inner_tol >= 0) || o.inner_tol >= 1) {
+        set_error("inner_tol must be in [0, 1)");
+        return DP_ERR_INVALID_ARG;
+    }
+    if (o.inner_tol == 0) o.inner_tol = o.prec == DP_PREC_FP64 ? 0.0 : 1e-5;
+    if (o.check_every < 0) o.check_every = 0;
+    *out = o;
+    return DP_OK;
+}
+
+static bool geom_ok(const int dims[4], Geom &g)
+{
+    for (int k = 0; k < 4; k++)
+        if (dims[k] < 2 || dims[k] > kMaxL || (dims[k] % 2)) return false;
+    g.T = dims[0];
+    g.Lx = dims[1];
+    g.Ly = dims[2];
+    g.Lz = dims[3];
+    g.Lxh = g.Lx / 2;
+    g.Lmax = std::max(std::max(g.T, g.Lx), std::max(g.Ly, g.Lz));
+    g.V = (long long)g.T * g.Lx * g.Ly * g.Lz;
+    g.Vh = g.V / 2;
+    return true;
+}
+
+}  // namespace dp
+
+using namespace dp;
+
+#define CTX_CHECK(ctx)                                  \
+    do {                                                \
+        if (!(ctx)) {                                   \
+            set_error("null context");                  \
+            return DP_ERR_INVALID_ARG;                  \
+        }                                               \
+        if (cudaSetDevice((ctx)->c.device) != cudaSuccess) { \
+            set_error("cudaSetDevice(%d) failed", (ctx)->c.device); \
+            return DP_ERR_CUDA;                         \
+        }                                               \
+    } while (0)
+
+extern "C" {
+
+const char *dp_last_error(void) { return g_err.c_str(); }
+
+dp_status dp_create(dp_ctx **out, int device, const dp_alloc_hooks *hooks, void *stream)
+{
+    if (!out) {
+        set_error("out is null");
+        return DP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_error("no CUDA device %d (%d visible)", device, ndev);
+        return DP_ERR_CUDA;
+    }
+    CUDA_OK(cudaSetDevice(device));
+    dp_ctx *ctx = new dp_ctx();
+    Ctx &c = ctx->c;
+    c.device = device;
+    if (hooks) {
+        if (!hooks->alloc || !hooks->free) {
+            delete ctx;
+            set_error("allocation hooks need both alloc and free");
+            return DP_ERR_INVALID_ARG;
+        }
+        c.hooks = *hooks;
+        c.has_hooks = true;
+    }
+    if (stream) {
+        c.stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            set_error("cannot create stream");
+            return DP_ERR_CUDA;
+        }
+        c.own_stream = true;
+    }
+    c.bc.blocks = 1024;
+    c.bc.partials = (double *)c.alloc((size_t)c.bc.blocks * kMaxRhs * 4 * sizeof(double));
+    c.bc.counter = (unsigned int *)c.alloc(256);
+    c.bc.n_active = (int *)c.alloc(256);
+    if (!c.bc.partials || !c.bc.counter || !c.bc.n_active ||
+        cudaMallocHost(&c.h_nactive, sizeof(int)) != cudaSuccess) {
+        dp_destroy(ctx);
+        set_error("out of memory creating context");
+        return DP_ERR_OOM;
+    }
+    cudaMemsetAsync(c.bc.counter, 0, 256, c.stream);
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) {
+        dp_destroy(ctx);
+        set_error("stream error creating context");
+        return DP_ERR_CUDA;
+    }
+    *out = ctx;
+    return DP_OK;
+}
+
+void dp_serve_shutdown(dp_ctx *ctx);
+
+void dp_destroy(dp_ctx *ctx)
+{
+    if (!ctx) return;
+    Ctx &c = ctx->c;
+    cudaSetDevice(c.device);
+    dp_serve_shutdown(ctx);
+    cudaStreamSynchronize(c.stream);
+    c.pending.clear();
+    std::vector<void *> ps;
+    for (auto &kv : c.allocs) ps.push_back(kv.first);
+    for (void *p : ps) c.release(p);
+    cudaStreamSynchronize(c.stream);
+    for (auto e : c.event_pool) cudaEventDestroy(e);
+    if (c.h_nactive) cudaFreeHost(c.h_nactive);
+    if (c.own_stream) cudaStreamDestroy(c.stream);
+    delete ctx;
+}
+
+size_t dp_device_bytes(dp_ctx *ctx)
+{
+    if (!ctx) return 0;
+    std::lock_guard<std::mutex> lk(ctx->c.mu);
+    return ctx->c.bytes;
+}
+
+dp_status dp_field_load(dp_ctx *ctx, const double *links, const int dims[4], int bc_t,
+                        dp_field *out)
+{
+    CTX_CHECK(ctx);
+    Ctx &c = ctx->c;
+    if (!links || !dims || !out || (bc_t != 1 && bc_t != -1)) {
+        set_error("dp_field_load: null pointer or bc_t not +-1");
+        return DP_ERR_INVALID_ARG;
+    }
+    Geom g;
+    if (!geom_ok(dims, g)) {
+        set_error("dims must be even and in [2, %d]", kMaxL);
+        return DP_ERR_INVALID_ARG;
+    }
+    const size_t n = (size_t)g.V * 4 * 18;
+    for (size_t k = 0; k < n; k++)
+        if (!std::isfinite(links[k])) {
+            set_error("links contain NaN/Inf at element %zu", k);
+            return DP_ERR_INVALID_ARG;
+        }
+    auto f = std::make_shared<Field>();
+    f->g = g;
+    f->bc_t = bc_t;
+    double2 *lex = (double2 *)c.alloc(n * sizeof(double));
+    bool ok = lex != nullptr;
+    for (int p = 0; p < 2 && ok; p++) {
+        f->l64[p] = (double2 *)c.alloc(g.Vh * 4 * 9 * sizeof(double2));
+        f->l32f[p] = (float2 *)c.alloc(g.Vh * 4 * 9 * sizeof(float2));
+        f->l32c[p] = (float4 *)c.alloc(g.Vh * 4 * 3 * sizeof(float4));
+        ok = f->l64[p] && f->l32f[p] && f->l32c[p];
+    }
+    if (!ok) {
+        c.release(lex);
+        for (int p = 0; p < 2; p++) {
+            c.release(f->l64[p]);
+            c.release(f->l32f[p]);
+            c.release(f->l32c[p]);
+        }
+        set_error("out of device memory loading field");
+        return DP_ERR_OOM;
+    }
+    CUDA_OK(cudaMemcpyAsync(lex, links, n * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    CUDA_OK(launch_pack_links(lex, g, f->l64, f->l32f, f->l32c, c.stream));
+    c.launches++;
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    c.release(lex);
+    std::lock_guard<std::mutex> lk(c.mu);
+    const uint64_t id = c.next_field++;
+    c.fields[id] = f;
+    *out = id;
+    return DP_OK;
+}
+
+dp_status dp_field_set_csw(dp_ctx *ctx, dp_field field, double csw)
+{
+    CTX_CHECK(ctx);
+    Ctx &c = ctx->c;
+    auto f = find_field(&c, field);
+    if (!f) {
+        set_error("unknown field %llu", (unsigned long long)field);
+        return DP_ERR_NOT_FOUND;
+    }
+    if (!std::isfinite(csw)) {
+        set_error("c_sw is not finite");
+        return DP_ERR_INVALID_ARG;
+    }
+    const long long Vh = f->g.Vh;
+    for (int p = 0; p < 2; p++) {
+        if (!f->clov[p]) f->clov[p] = (double2 *)c.alloc(Vh * 36 * sizeof(double2));
+        if (!f->clov32[p]) f->clov32[p] = (float4 *)c.alloc(Vh * 18 * sizeof(float4));
+        if (!f->clov[p] || !f->clov32[p]) {
+            set_error("out of device memory (clover)");
+            return DP_ERR_OOM;
+        }
+    }
+    CUDA_OK(launch_clover_build(f->l64[0], f->l64[1], f->g, csw, f->clov[0], f->clov[1], c.stream));
+    c.launches++;
+    // FP32 copy of the clover term for the FP32 apply path
+    for (int p = 0; p < 2; p++) CUDA_OK(launch_clover_to_f32(f->clov[p], f->clov32[p], Vh, c.stream));
+    c.launches += 2;
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    {
+        std::lock_guard<std::mutex> lk(f->inv_mu);
+        f->invs.clear();
+    }
+    f->has_clover = true;
+    f->csw = csw;
+    return DP_OK;
+}
+
+dp_status dp_field_free(dp_ctx *ctx, dp_field field)
+{
+    CTX_CHECK(ctx);
+    Ctx &c = ctx->c;
+    std::shared_ptr<Field> f;
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        auto it = c.fields.find(field);
+        if (it == c.fields.end()) {
+            set_error("unknown field %llu", (unsigned long long)field);
+            return DP_ERR_NOT_FOUND;
+        }
+        if (it->second->users.load() > 0) {
+            set_error("field has requests in flight");
+            return DP_ERR_INVALID_ARG;
+        }
+        f = it->second;
+        c.fields.erase(it);
+    }
+    cudaStreamSynchronize(c.stream);
+    for (int p = 0; p < 2; p++) {
+        c.release(f->l64[p]);
+        c.release(f->l32f[p]);
+        c.release(f->l32c[p]);
+        c.release(f->clov[p]);
+        c.release(f->clov32[p]);
+    }
+    {
+        std::lock_guard<std::mutex> lk(f->inv_mu);
+        f->invs.clear();
+    }
+    cudaStreamSynchronize(c.stream);
+    return DP_OK;
+}
+
+dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_profile *profile,
+                   const int src[4], int prec, int compress12, const double *in, double *out,
+                   int nrhs)
+{
+    CTX_CHECK(ctx);
+    Ctx &c = ctx->c;
+    auto fp = find_field(&c, field);
+    if (!fp) {
+        set_error("unknown field");
+        return DP_ERR_NOT_FOUND;
+    }
+    Field &f = *fp;
+    if (!in || !out || nrhs < 1 || nrhs > kMaxRhs || kind < 0 || kind > 3 ||
+        (prec != DP_PREC_FP64 && prec != DP_PREC_MIXED_FP32) || !std::isfinite(M)) {
+        set_error("dp_apply: invalid argument");
+        return DP_ERR_INVALID_ARG;
+    }
+    if (kind != DP_APPLY_HOP && !f.has_clover) {
+        set_error("clover term not built");
+        return DP_ERR_INVALID_ARG;
+    }
+    const Geom &g = f.g;
+    const size_t nlex = (size_t)g.V * 24 * nrhs;
+    for (size_t k = 0; k < nlex; k++)
+        if (!std::isfinite(in[k])) {
+            set_error("input spinor has NaN/Inf");
+            return DP_ERR_INVALID_ARG;
+        }
+    const int pr = prec == DP_PREC_FP64 ? 0 : 1;
+    const int zero_src[4] = {0, 0, 0, 0};
+    dp_profile none{};
+    none.kind = DP_PROF_NONE;
+    std::vector<double> alpha(4 * g.Lmax), hop(8 * g.Lmax);
+    dp_status stt = profile_tables(profile ? *profile : none, g, f.bc_t, src ? src : zero_src,
+                                   alpha.data(), hop.data());
+    if (stt != DP_OK) return stt;
+    std::vector<float> hopf(hop.begin(), hop.end());
+
+    std::shared_ptr<CloverInv> ci;
+    if (kind == DP_APPLY_CLOVER_INV) {
+        stt = get_clover_inv(&c, f, M, &ci);
+        if (stt != DP_OK) return stt;
+    }
+    const size_t vb = (size_t)g.Vh * nrhs * 24 * (pr == 0 ? 8 : 4);
+    double2 *lex = (double2 *)c.alloc(nlex * sizeof(double));
+    void *ie = c.alloc(vb), *io = c.alloc(vb), *oe = c.alloc(vb), *oo = c.alloc(vb);
+    void *te = c.alloc(vb), *to = c.alloc(vb);
+    void *hopd = c.alloc(hop.size() * sizeof(double));
+    dp_status ret = DP_OK;
+    if (!lex || !ie || !io || !oe || !oo || !te || !to || !hopd) {
+        set_error("out of device memory (dp_apply)");
+        ret = DP_ERR_OOM;
+    } else {
+        auto run = [&]() -> dp_status {
+            CUDA_OK(cudaMemcpyAsync(lex, in, nlex * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+            CUDA_OK(launch_pack_spinor(lex, g, nrhs, pr, ie, io, c.stream));
+            if (pr == 0)
+                CUDA_OK(cudaMemcpyAsync(hopd, hop.data(), hop.size() * sizeof(double),
+                                        cudaMemcpyHostToDevice, c.stream));
+            else
+                CUDA_OK(cudaMemcpyAsync(hopd, hopf.data(), hopf.size() * sizeof(float),
+                                        cudaMemcpyHostToDevice, c.stream));
+            const int lf = pr == 0 ? LINK_F64_18 : (compress12 ? LINK_F32_12 : LINK_F32_18);
+            void *inp[2] = {ie, io}, *outp[2] = {oe, oo}, *tmp[2] = {te, to};
+            for (int p = 0; p < 2; p++) {
+                const void *mat;
+                if (kind == DP_APPLY_CLOVER_INV)
+                    mat = pr == 0 ? (const void *)ci->inv64[p] : (const void *)ci->inv32[p];
+                else
+                    mat = pr == 0 ? (const void *)f.clov[p] : (const void *)f.clov32[p];
+                CloverApplyParams cp{};
+                cp.mat[0] = mat;
+                cp.diag[0] = kind == DP_APPLY_FULL ? 4.0 + M : 0.0;
+                cp.Vh = g.Vh;
+                cp.nrhs = nrhs;
+                cp.in = inp[p];
+                cp.out = (kind == DP_APPLY_FULL) ? tmp[p] : outp[p];
+                if (kind == DP_APPLY_CLOVER || kind == DP_APPLY_CLOVER_INV) {
+                    CUDA_OK(launch_clover_apply(cp, pr, c.stream));
+                    continue;
+                }
+                DslashParams P{};
+                P.in = inp[1 - p];
+                P.out = outp[p];
+                P.links[0] = pr == 0 ? (const void *)f.l64[0]
+                                     : (compress12 ? (const void *)f.l32c[0] : (const void *)f.l32f[0]);
+                P.links[1] = pr == 0 ? (const void *)f.l64[1]
+                                     : (compress12 ? (const void *)f.l32c[1] : (const void *)f.l32f[1]);
+                P.hop = hopd;
+                P.g = g;
+                P.parity = p;
+                P.nrhs = nrhs;
+                int epi = EPI_HOP;
+                if (kind == DP_APPLY_FULL) {
+                    CUDA_OK(launch_clover_apply(cp, pr, c.stream));
+                    P.x = tmp[p];
+                    epi = EPI_XPY;
+                }
+                CUDA_OK(launch_dslash(P, pr, lf, epi, c.block_for(g.Vh, pr, lf, nrhs), c.stream));
+            }
+            CUDA_OK(launch_unpack_spinor(oe, oo, g, nrhs, pr, lex, c.stream));
+            CUDA_OK(cudaMemcpyAsync(out, lex, nlex * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            CUDA_OK(cudaStreamSynchronize(c.stream));
+            c.launches += 6;
+            return DP_OK;
+        };
+        ret = run();
+    }
+    c.release(lex);
+    c.release(ie);
+    c.release(io);
+    c.release(oe);
+    c.release(oo);
+    c.release(te);
+    c.release(to);
+    c.release(hopd);
+    cudaStreamSynchronize(c.stream);
+    return ret;
+}
+
+size_t dp_spinor_bytes(dp_ctx *ctx, dp_field field, int prec, int nrhs)
+{
+    if (!ctx) return 0;
+    auto f = find_field(&ctx->c, field);
+    if (!f) return 0;
+    return (size_t)f->g.Vh * nrhs * 24 * (prec == DP_PREC_FP64 ? 8 : 4);
+}
+
+dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
+                        int prec, int compress12, int out_parity, const void *in, void *out,
+                        int nrhs, int block_threads, int rhs_per_thread, int iters,
+                        float *ms_out)
+{
+    CTX_CHECK(ctx);
+    Ctx &c = ctx->c;
+    auto fp = find_field(&c, field);
+    if (!fp) {
+        set_error("unknown field");
+        return DP_ERR_NOT_FOUND;
+    }
+    Field &f = *fp;
+    if (!in || !out || nrhs < 1 || nrhs > kMaxRhs || iters < 1 || (out_parity & ~1) ||
+        (prec != DP_PREC_FP64 && prec != DP_PREC_MIXED_FP32) ||
+        (rhs_per_thread != 0 && rhs_per_thread != 1) ||
+        (block_threads != 0 && (block_threads < 32 || block_threads > 256 || block_threads % 32))) {
+        set_error("dp_dslash_dev: invalid argument");
+        return DP_ERR_INVALID_ARG;
+    }
+    const Geom &g = f.g;
+    const int pr = prec == DP_PREC_FP64 ? 0 : 1;
+    const int lf = pr == 0 ? LINK_F64_18 : (compress12 ? LINK_F32_12 : LINK_F32_18);
+    std::shared_ptr<CloverInv> ci;
+    dp_status stt = get_clover_inv(&c, f, M, &ci);
+    if (stt != DP_OK) return stt;
+    const int zero_src[4] = {0, 0, 0, 0};
+    dp_profile none{};
+    none.kind = DP_PROF_NONE;
+    std::vector<double> alpha(4 * g.Lmax), hop(8 * g.Lmax);
+    stt = profile_tables(profile ? *profile : none, g, f.bc_t, zero_src, alpha.data(), hop.data());
+    if (stt != DP_OK) return stt;
+    std::vector<float> hopf(hop.begin(), hop.end());
+    void *hopd = c.alloc(hop.size() * sizeof(double));
+    if (!hopd) {
+        set_error("out of device memory");
+        return DP_ERR_OOM;
+    }
+    if (pr == 0)
+        CUDA_OK(cudaMemcpyAsync(hopd, hop.data(), hop.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    else
+        CUDA_OK(cudaMemcpyAsync(hopd, hopf.data(), hopf.size() * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+    DslashParams P{};
+    P.in = in;
+    P.out = out;
+    P.links[0] = pr == 0 ? (const void *)f.l64[0] : (compress12 ? (const void *)f.l32c[0] : (const void *)f.l32f[0]);
+    P.links[1] = pr == 0 ? (const void *)f.l64[1] : (compress12 ? (const void *)f.l32c[1] : (const void *)f.l32f[1]);
+    P.clov[0] = pr == 0 ? (const void *)ci->inv64[out_parity] : (const void *)ci->inv32[out_parity];
+    P.hop = hopd;
+    P.g = g;
+    P.parity = out_parity;
+    P.nrhs = nrhs;
+    const int block = block_threads > 0 ? block_threads : c.block_for(g.Vh, pr, lf, nrhs);
+    cudaEvent_t a = c.get_event(), b = c.get_event();
+    CUDA_OK(cudaEventRecord(a, c.stream));
+    for (int k = 0; k < iters; k++) CUDA_OK(launch_dslash(P, pr, lf, EPI_AINV, block, c.stream));
+    CUDA_OK(cudaEventRecord(b, c.stream));
+    c.launches += iters;
+    CUDA_OK(cudaEventSynchronize(b));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    c.event_pool.push_back(a);
+    c.event_pool.push_back(b);
+    if (ms_out) *ms_out = ms / iters;
+    c.release(hopd);
+    return DP_OK;
+}
+
+dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int nrhs,
+                      int *best_block_threads, int *best_rhs_per_thread, float *best_ms)
+{
+    CTX_CHECK(ctx);
+    Ctx &c = ctx->c;
+    auto fp = find_field(&c, field);
+    if (!fp) {
+        set_error("unknown field");
+        return DP_ERR_NOT_FOUND;
+    }
+    if (nrhs < 1 || nrhs > kMaxRhs || (prec != DP_PREC_FP64 && prec != DP_PREC_MIXED_FP32)) {
+        set_error("dp_autotune: invalid argument");
+        return DP_ERR_INVALID_ARG;
+    }
+    const Geom &g = fp->g;
+    const int pr = prec == DP_PREC_FP64 ? 0 : 1;
+    const int lf = pr == 0 ? LINK_F64_18 : (compress12 ? LINK_F32_12 : LINK_F32_18);
+    const size_t vb = dp_spinor_bytes(ctx, field, prec, nrhs);
+    void *in = c.alloc(vb), *out = c.alloc(vb);
+    if (!in || !out) {
+        c.release(in);
+        c.release(out);
+        set_error("out of device memory (autotune)");
+        return DP_ERR_OOM;
+    }
+    cudaMemsetAsync(in, 0, vb, c.stream);
+    const int cands[] = {64, 128, 192, 256};
+    int best = 0;
+    float bms = 1e30f;
+    dp_status st = DP_OK;
+    for (int b : cands) {
+        float ms = 0;
+        // warm up once, then time a few launches
+        st = dp_dslash_dev(ctx, field, 0.1, nullptr, prec, compress12, 0, in, out, nrhs, b, 1, 1, &ms);
+        if (st != DP_OK) break;
+        st = dp_dslash_dev(ctx, field, 0.1, nullptr, prec, compress12, 0, in, out, nrhs, b, 1, 5, &ms);
+        if (st != DP_OK) break;
+        if (ms < bms) {
+            bms = ms;
+            best = b;
+        }
+    }
+    c.release(in);
+    c.release(out);
+    if (st != DP_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        c.tuned_block[TuneKey{g.Vh, pr, lf, nrhs}] = best;
+    }
+    if (best_block_threads) *best_block_threads = best;
+    if (best_rhs_per_thread) *best_rhs_per_thread = 1;
+    if (best_ms) *best_ms = bms;
+    return DP_OK;
+}
+
+dp_status dp_timing_enable(dp_ctx *ctx, int on)
+{
+    CTX_CHECK(ctx);
+    ctx->c.timing = on != 0;
+    return DP_OK;
+}
+
+dp_status dp_timing_reset(dp_ctx *ctx)
+{
+    CTX_CHECK(ctx);
+    ctx->c.collect_timing();
+    ctx->c.stats.clear();
+    return DP_OK;
+}
+
+dp_status dp_timing_get(dp_ctx *ctx, const char *name, long *launches, double *total_ms)
+{
+    CTX_CHECK(ctx);
+    if (!name) {
+        set_error("null name");
+        return DP_ERR_INVALID_ARG;
+    }
+    ctx->c.collect_timing();
+    auto it = ctx->c.stats.find(name);
+    if (launches) *launches = it == ctx->c.stats.end() ? 0 : it->second.launches;
+    if (total_ms) *total_ms = it == ctx->c.stats.end() ? 0 : it->second.ms;
+    return DP_OK;
+}
+
+long dp_launch_count(dp_ctx *ctx) { return ctx ? ctx->c.launches.load() : 0; }
+
+dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profile,
+                            const int src[4], double *alpha_out, double *hop_out)
+{
+    if (!dims || !profile || !alpha_out || !hop_out || (bc_t != 1 && bc_t != -1)) {
+        set_error("dp_profile_tables: invalid argument");
+        return DP_ERR_INVALID_ARG;
+    }
+    Geom g;
+    if (!geom_ok(dims, g)) {
+        set_error("dims must be even and in [2, %d]", kMaxL);
+        return DP_ERR_INVALID_ARG;
+    }
+    const int zero[4] = {0, 0, 0, 0};
+    const int *s = src ? src : zero;
+    const int L[4] = {g.T, g.Lx, g.Ly, g.Lz};
+    for (int mu = 0; mu < 4; mu++)
+        if (s[mu] < 0 || s[mu] >= L[mu]) {
+            set_error("source coordinate out of range");
+            return DP_ERR_INVALID_ARG;
+        }
+    return profile_tables(*profile, g, bc_t, s, alpha_out, hop_out);
+}
+
+}  // extern "C"

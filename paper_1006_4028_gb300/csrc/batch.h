@@ -1,0 +1,99 @@
+// Slot-based solver batch: see solver.cu.
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "ctx.h"
+
+namespace dp {
+
+// a point-source job: `ncomp` spin-colour components (from comp0) of one
+// (mass, profile, source) group
+struct Job {
+    Group grp;
+    int comp0 = 0, ncomp = 12;
+    double r = 1e-10;
+    double *cpp_dst = nullptr;   // device [T], written (or added to) on completion
+    int accumulate = 0;
+    double *cpp_host = nullptr;  // host [T], written on completion
+    double *prop_host = nullptr; // host [ncomp][V][12] complex128 or NULL
+    SolveResult res;
+    bool done = false;
+    // set by the batch
+    int tab = -1, slot0 = -1;
+    double src_scale = 1.0;
+    void *user = nullptr;
+};
+
+struct Op {
+    const Field *f = nullptr;
+    int pr = 0;  // 0 FP64, 1 FP32
+    int lf = 0;  // link format
+    const void *hop = nullptr;
+    const void *inv[2][kMaxGroups] = {};
+    int8_t grp_of[kMaxRhs] = {};
+    int nrhs = 0;
+    int block = 128;
+};
+
+struct InnerVecs {
+    void *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr,
+         *x = nullptr, *to = nullptr;
+};
+
+class Batch {
+  public:
+    Batch(Ctx *c, std::shared_ptr<Field> f, int nslots, const dp_solve_opts &o, int round_cap);
+    ~Batch();
+    Batch(const Batch &) = delete;
+    Batch &operator=(const Batch &) = delete;
+
+    static size_t bytes_needed(const Geom &g, int nslots, int prec);
+    dp_status init();
+    bool can_admit(int ncomp) const;
+    // set up the job's source, Schur right-hand side and outer state
+    dp_status admit(Job *j);
+    // one FP64 defect-correction round for every active RHS
+    dp_status round();
+    // finish jobs whose RHS are all done: odd sites, residual, restore, C_PP
+    dp_status harvest(std::vector<Job *> &finished);
+    int active_jobs() const;
+    size_t bytes() const { return total_bytes; }
+    const std::shared_ptr<Field> &field() const { return f; }
+
+  private:
+    void *get(size_t bytes);
+    dp_status upload_mask(const std::vector<int> &m);
+    dp_status bicgstab(int max_iter, int *iters_done);
+
+    Ctx *c;
+    std::shared_ptr<Field> f;
+    int n;
+    dp_solve_opts opts;
+    int round_iters;
+    int mixed = 1, ipr = 1, ilf = LINK_F32_12;
+    int check_every = 4;
+    size_t v64 = 0, vin = 0, total_bytes = 0;
+    std::vector<void *> owned;
+    double2 *bh = nullptr, *x = nullptr, *r64 = nullptr, *y64 = nullptr, *to64 = nullptr;
+    InnerVecs in;
+    RhsState *outer = nullptr, *inner = nullptr;
+    double *alpha_d = nullptr, *hop64_d = nullptr;
+    float *hop32_d = nullptr;
+    SlotInfo *slots_d = nullptr;
+    int *tsrc_d = nullptr, *mask_d = nullptr;
+    double *cpp_d = nullptr, *cpart = nullptr, *nrm_d = nullptr;
+    Op op64, opin;
+    cudaGraphExec_t graph = nullptr;
+    int graph_max_iter = 0;
+    Job *jobs[kMaxGroups] = {};
+    std::shared_ptr<CloverInv> invs[kMaxGroups];
+    std::vector<Job *> slot_job;
+    std::vector<int> slot_inner, slot_outer, slot_stall;
+    std::vector<double> slot_rr_prev;
+    std::vector<SlotInfo> slots;
+    std::vector<RhsState> hs, hin;
+};
+
+}  // namespace dp

@@ -1,0 +1,146 @@
+// Host-side state of a dpre context: device memory, resident gauge fields
+// with their clover terms and clover inverses, reduction scratch, the launch
+// tuner, per-kernel timing and the request scheduler.
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/dpre.h"
+#include "dp_internal.h"
+
+namespace dp {
+
+void set_error(const char *fmt, ...);
+
+struct Ctx;
+
+// clover inverse for one mass; device memory is returned to the context when
+// the last holder (field cache or running batch) lets go
+struct CloverInv {
+    Ctx *owner = nullptr;
+    double M = 0;
+    double2 *inv64[2] = {nullptr, nullptr};
+    float4 *inv32[2] = {nullptr, nullptr};
+    ~CloverInv();
+};
+
+struct Field {
+    Geom g;
+    int bc_t;
+    double2 *l64[2] = {nullptr, nullptr};
+    float2 *l32f[2] = {nullptr, nullptr};
+    float4 *l32c[2] = {nullptr, nullptr};
+    double2 *clov[2] = {nullptr, nullptr};  // clover term, FP64 (no mass)
+    float4 *clov32[2] = {nullptr, nullptr}; // clover term, FP32 copy
+    bool has_clover = false;
+    double csw = 0;
+    std::vector<std::shared_ptr<CloverInv>> invs;  // per mass, least recently used first
+    std::mutex inv_mu;
+    std::atomic<int> users{0};    // requests in flight on this field
+};
+
+// one point-source group = 12 RHS sharing (mass, profile, source)
+struct Group {
+    double M;
+    dp_profile prof;
+    std::vector<double> table[4];  // copies of TABLE profiles
+    int src[4];
+};
+
+struct TimingRec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+
+struct Stat {
+    long launches = 0;
+    double ms = 0;
+};
+
+struct TuneKey {
+    long long Vh;
+    int prec, link_fmt, nrhs;
+    bool operator<(const TuneKey &o) const
+    {
+        if (Vh != o.Vh) return Vh < o.Vh;
+        if (prec != o.prec) return prec < o.prec;
+        if (link_fmt != o.link_fmt) return link_fmt < o.link_fmt;
+        return nrhs < o.nrhs;
+    }
+};
+
+struct Scheduler;
+struct SchedDeleter {
+    void operator()(Scheduler *s) const;  // defined with the scheduler (serve.cu)
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    dp_alloc_hooks hooks{};
+    bool has_hooks = false;
+
+    std::mutex mu;  // fields, allocations, tuner
+    std::map<uint64_t, std::shared_ptr<Field>> fields;
+    uint64_t next_field = 1;
+    std::map<void *, size_t> allocs;
+    size_t bytes = 0;
+
+    BlasCtx bc{};
+    int *h_nactive = nullptr;  // pinned
+
+    bool timing = false;
+    std::vector<TimingRec> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::map<std::string, Stat> stats;
+    std::atomic<long> launches{0};
+
+    std::map<TuneKey, int> tuned_block;
+
+    std::unique_ptr<Scheduler, SchedDeleter> sched;
+
+    void *alloc(size_t n);
+    void release(void *p);
+    cudaEvent_t get_event();
+    // record a timed launch region: call before(name) / after()
+    void time_begin(const char *name, cudaEvent_t *a);
+    void time_end(const char *name, cudaEvent_t a);
+    void collect_timing();
+    int block_for(long long Vh, int prec, int link_fmt, int nrhs);
+};
+
+std::shared_ptr<Field> find_field(Ctx *c, dp_field f);
+// clover inverse of (4+M) + clover for both parities, cached per mass
+dp_status get_clover_inv(Ctx *c, Field &f, double M, std::shared_ptr<CloverInv> *out);
+// FP64 alpha_B tables [4][Lmax] and hop tables [4][2][Lmax] (with the -1/2)
+dp_status profile_tables(const dp_profile &p, const Geom &g, int bc_t, const int src[4],
+                         double *alpha, double *hop);
+
+struct SolveResult {
+    int iters_inner = 0, iters_outer = 0;
+    double true_rel_residue = 0;
+    int status = 0;
+};
+
+// the method for a set of point-source groups on one field (solver.cu)
+dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group> &groups, double r_target,
+                       const dp_solve_opts &opts, double *cpp_dev, double *prop_host,
+                       std::vector<SolveResult> &res);
+
+dp_status check_opts(const dp_solve_opts *in, dp_solve_opts *out);
+
+}  // namespace dp
+
+struct dp_ctx {
+    dp::Ctx c;
+};

@@ -1,0 +1,191 @@
+// Internal definitions shared by the library's translation units.
+//
+// Device data layout (even-odd, site-blocked SoA; V/2 = Vh sites per parity):
+//   half-site index s of a site of parity p = (t+x+y+z)&1 is i>>1 with
+//   i = ((t*Lz + z)*Ly + y)*Lx + x (Lx even, so each x-row holds Lx/2 sites of
+//   each parity).
+//   spinor field of one parity, n RHS: [chunk][s][rhs] with chunk = float4
+//     (6 per spinor, FP32) or double2 (12 per spinor, FP64); the 24 reals of a
+//     spinor are (spin, colour, re/im) in that order, spin-major.
+//   links of one parity: [mu][chunk][s]; FP64: 9 double2 (18 reals);
+//     FP32: 9 float2 (18 reals) or 3 float4 (12 reals: rows 0 and 1).
+//   clover (and its inverse) of one parity: [slot][chunk][s]; 72 reals per
+//     site = two Hermitian 6x6 chiral blocks (spins 0,1 and spins 2,3), each
+//     packed as 6 real diagonal entries then the 15 upper-triangle entries
+//     (i<j, row-major) as (re, im); FP64: 36 double2, FP32: 18 float4.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dp {
+
+constexpr int kMaxRhs = 64;
+constexpr int kMaxL = 256;
+
+struct Geom {
+    int T, Lx, Ly, Lz, Lxh, Lmax;
+    long long V, Vh;
+};
+
+// dslash epilogues: D = hopping term D_{p,1-p}, A = clover(+mass) of parity p
+enum Epi {
+    EPI_HOP = 0,      // out = D in
+    EPI_AINV = 1,     // out = A^-1 D in
+    EPI_XMY_AINV = 2, // out = x - A^-1 D in
+    EPI_AINV_XMY = 3, // out = A^-1 (x - D in)
+    EPI_XPY = 4       // out = x + D in
+};
+
+enum LinkFmt { LINK_F64_18 = 0, LINK_F32_18 = 1, LINK_F32_12 = 2 };
+
+constexpr int kMaxGroups = 8;  // point-source groups (12 RHS each) per batch
+
+// per-RHS slot of a batch: which group (mass/profile/source) it belongs to and
+// which spin-colour component of the point source it carries
+struct SlotInfo {
+    int group;      // index into the per-group arrays
+    int comp;       // source component k = 3*spin + colour
+    int t, x, y, z; // source site
+    double scale;   // alpha_B(x_src): the source scaling eta' = alpha_B eta
+};
+
+struct DslashParams {
+    const void *in;         // spinor, parity 1-p
+    void *out;              // spinor, parity p
+    const void *x;          // spinor, parity p (epilogues 2-4)
+    const void *links[2];   // by parity
+    const void *clov[kMaxGroups]; // parity p clover inverse per group
+    const void *hop;        // [group][mu][2][Lmax] hop factors incl. the -1/2
+    const int *active;      // NULL or per-RHS flags at active[r * active_stride]
+    int active_stride;
+    Geom g;
+    int parity;             // output parity
+    int nrhs;
+    int8_t grp_of[kMaxRhs]; // RHS -> group
+};
+
+// ---- launch wrappers (dslash.cu) ----
+// prec: 0 = FP64 (links LINK_F64_18), 1 = FP32 (links LINK_F32_18 / LINK_F32_12)
+cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi, int block,
+                          cudaStream_t st);
+
+// ---- clover (clover.cu) ----
+// clover term (no mass) for all sites of both parities, FP64, layout above
+cudaError_t launch_clover_build(const double2 *links64_e, const double2 *links64_o,
+                                const Geom &g, double csw, double2 *clov_e, double2 *clov_o,
+                                cudaStream_t st);
+// inverse of (4+M) + clover for one parity; writes FP64 and FP32 copies;
+// flag[0] set to 1 if a block is singular or non-finite
+cudaError_t launch_clover_invert(const double2 *clov, long long Vh, double M, double2 *inv64,
+                                 float4 *inv32, int *flag, cudaStream_t st);
+cudaError_t launch_clover_to_f32(const double2 *in, float4 *out, long long Vh, cudaStream_t st);
+// out = (diag_g + C_g) in per RHS group g, one parity: C_g a packed clover
+// matrix (clover term, or an inverse with diag_g = 0), FP64 or FP32 spinors
+struct CloverApplyParams {
+    const void *mat[kMaxGroups];
+    double diag[kMaxGroups];
+    int8_t grp_of[kMaxRhs];
+    const int *mask;  // NULL or per-RHS flags: RHS with mask[r] == 0 are skipped
+    const void *in;
+    void *out;        // may alias `in`
+    long long Vh;
+    int nrhs;
+};
+cudaError_t launch_clover_apply(const CloverApplyParams &p, int prec, cudaStream_t st);
+
+// ---- field packing, sources, restore/contract (field.cu) ----
+cudaError_t launch_pack_links(const double2 *lex, const Geom &g, double2 *l64[2], float2 *l32f[2],
+                              float4 *l32c[2], cudaStream_t st);
+// lexicographic complex128 spinors [nrhs][V][12] <-> packed parity halves
+cudaError_t launch_pack_spinor(const double2 *lex, const Geom &g, int nrhs, int prec,
+                               void *even, void *odd, cudaStream_t st);
+cudaError_t launch_unpack_spinor(const void *even, const void *odd, const Geom &g, int nrhs,
+                                 int prec, double2 *lex, cudaStream_t st);
+// point source for every slot: RHS k = slots[k].scale at its source site for
+// component slots[k].comp, FP64, both parities (zeroed by the caller)
+cudaError_t launch_point_source(const Geom &g, const SlotInfo *slots_dev, int nrhs,
+                                const int *mask, double2 *even, double2 *odd, cudaStream_t st);
+// restore S = S'/alpha_B per site and contract C_PP per group:
+// cpp[group][(t - t_src[group]) mod T] (+)= -sum_{slice t} |S|^2.
+// alpha: [group][mu][Lmax] FP64 alpha_B per coordinate; partials: T*P*ngroups
+// doubles with P = contract_blocks_per_slice(g); prop_lex: NULL or
+// [nrhs][V][12] complex128 of the restored propagator
+int contract_blocks_per_slice(const Geom &g);
+// only RHS with mask[r] != 0 contribute (mask NULL: all)
+cudaError_t launch_restore_contract(const double2 *xe, const double2 *xo, const Geom &g, int nrhs,
+                                    const double *alpha, const SlotInfo *slots_dev, int ngroups,
+                                    const int *t_src_dev, const int *mask, double *cpp_dev,
+                                    double *partials, double2 *prop_lex, cudaStream_t st);
+// dst[k] (+)= src[k], k < T (accumulate != 0: add)
+cudaError_t launch_cpp_commit(const double *src, double *dst, int T, int accumulate, cudaStream_t st);
+
+// ---- BLAS-1 and reductions (blas.cu) ----
+struct RhsState {        // per RHS, device resident
+    double2 rho, alpha, omega, beta;
+    double rr, bb, tol2;  // |r|^2, |b|^2, stop threshold on |r|^2
+    double scale;         // FP64 outer loop: |r| used to normalise the inner source
+    int active;           // 1 while iterating
+    int iters;
+    int status;           // 0 running, 1 converged, 2 breakdown, 3 non-finite, 4 max-iter
+    int fresh;            // 1: x = 0, next residual call sets |b|^2 and tol2
+};
+
+struct BlasCtx {
+    double *partials;     // [max_blocks][kMaxRhs][4]
+    unsigned int *counter;
+    int *n_active;        // device counter of active RHS
+    int blocks;
+};
+
+// all vectors one parity, n RHS, layout above; prec 0 = FP64, 1 = FP32
+cudaError_t blas_bicg_init(BlasCtx &bc, int prec, const void *b, void *r, void *rhat, void *p,
+                           void *v, void *x, long long Vh, int nrhs, RhsState *st, double tol,
+                           cudaStream_t s);
+cudaError_t blas_bicg_p(BlasCtx &bc, int prec, const void *r, void *p, const void *v,
+                        long long Vh, int nrhs, const RhsState *st, int first, cudaStream_t s);
+cudaError_t blas_bicg_alpha(BlasCtx &bc, int prec, const void *rhat, const void *v,
+                            long long Vh, int nrhs, RhsState *st, cudaStream_t s);
+cudaError_t blas_bicg_s(BlasCtx &bc, int prec, const void *r, const void *v, void *sv,
+                        long long Vh, int nrhs, const RhsState *st, cudaStream_t s);
+cudaError_t blas_bicg_omega(BlasCtx &bc, int prec, const void *t, const void *sv,
+                            long long Vh, int nrhs, RhsState *st, cudaStream_t s);
+cudaError_t blas_bicg_update(BlasCtx &bc, int prec, void *x, void *r, const void *p,
+                             const void *sv, const void *t, const void *rhat, long long Vh,
+                             int nrhs, RhsState *st, int max_iter, cudaStream_t s);
+// FP64 outer loop helpers
+// r = b - y (r = b for `fresh` RHS); |r|^2 -> st.rr; st.scale = |r|;
+// convergence vs st.tol2 -> active
+// (mask: NULL or per-RHS flags restricting the update further)
+cudaError_t blas_residual64(BlasCtx &bc, const double2 *b, const double2 *y, double2 *r,
+                            long long Vh, int nrhs, RhsState *st, const int *mask,
+                            cudaStream_t s);
+// zero the FP64 vector entries of the RHS with mask[r] != 0
+cudaError_t blas_zero_masked(double2 *v, long long Vh, int nrhs, const int *mask, cudaStream_t s);
+// r32 = r64 / scale (active RHS); zero for inactive
+cudaError_t blas_to_f32_scaled(const double2 *r64, float4 *r32, long long Vh, int nrhs,
+                               const RhsState *st, cudaStream_t s);
+// x64 += scale * e32 (active RHS)
+cudaError_t blas_acc_f32(double2 *x64, const float4 *e32, long long Vh, int nrhs,
+                         const RhsState *st, cudaStream_t s);
+cudaError_t blas_zero(void *v, size_t bytes, cudaStream_t s);
+// per-RHS squared norms (FP64 accumulate) into out_dev[nrhs]
+cudaError_t blas_norm2(BlasCtx &bc, int prec, const void *v, long long Vh, int nrhs,
+                       double *out_dev, cudaStream_t s);
+// inner-solve state from the outer one: same active set; per-RHS inner
+// tolerance max(inner_tol, 0.5 target |b|/|r|) (squared into tol2)
+cudaError_t blas_inner_setup(const RhsState *outer, RhsState *inner, int nrhs,
+                             double inner_tol, double target, cudaStream_t s);
+// FP64 normalised copy out = v / scale (active RHS, zero otherwise)
+cudaError_t blas_scale64(const double2 *v, double2 *out, long long Vh, int nrhs,
+                         const RhsState *st, cudaStream_t s);
+// x64 += scale * e64 (active RHS)
+cudaError_t blas_acc64(double2 *x64, const double2 *e64, long long Vh, int nrhs,
+                       const RhsState *st, cudaStream_t s);
+// per-RHS |a - b|^2 (FP64) into out_dev[nrhs]
+cudaError_t blas_diff_norm2(BlasCtx &bc, const double2 *a, const double2 *b, long long Vh,
+                            int nrhs, double *out_dev, cudaStream_t s);
+// count active RHS into bc.n_active
+cudaError_t blas_count_active(BlasCtx &bc, const RhsState *st, int nrhs, cudaStream_t s);
+
+}  // namespace dp

@@ -1,0 +1,280 @@
+// Gauge-field packing, spinor packing, the point source and the
+// restore-and-contract step of the method.
+//
+//  * links: lexicographic complex128 -> even-odd site-blocked SoA per parity
+//    and direction, FP64 (18 reals), FP32 (18 reals) and FP32 12-real (rows 0
+//    and 1 only; row 2 is rebuilt in the dslash from unitarity).
+//  * point source (Sec. I, eq. linsysunprec with a source on one time slice;
+//    Sec. II eq. redeft): eta' = alpha_B(x_src) delta_{x,x_src} e_k.
+//  * restore and contract (Sec. II eq. backcorrection, Sec. III): S = S'/alpha_B
+//    per site, C_PP(y0) = -sum_{y vec} sum_k |S_k(y)|^2, y0 relative to the
+//    source, reduced per time slice in a fixed order (deterministic).
+#include "cplx.cuh"
+#include "dp_internal.h"
+
+namespace dp {
+namespace {
+
+__device__ __forceinline__ void coords_full(const Geom &g, long long i, int &t, int &x, int &y,
+                                            int &z)
+{
+    x = (int)(i % g.Lx);
+    i /= g.Lx;
+    y = (int)(i % g.Ly);
+    i /= g.Ly;
+    z = (int)(i % g.Lz);
+    t = (int)(i / g.Lz);
+}
+
+__global__ void k_pack_links(const double2 *lex, Geom g, double2 *l64e, double2 *l64o,
+                             float2 *l32fe, float2 *l32fo, float4 *l32ce, float4 *l32co)
+{
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= g.V * 4) return;
+    const long long i = gid >> 2;
+    const int mu = (int)(gid & 3);
+    int t, x, y, z;
+    coords_full(g, i, t, x, y, z);
+    const int par = (t + x + y + z) & 1;
+    const long long s = i >> 1;
+    const double2 *u = lex + (i * 4 + mu) * 9;
+    double2 *o64 = (par ? l64o : l64e) + (long long)mu * 9 * g.Vh + s;
+    float2 *o32 = (par ? l32fo : l32fe) + (long long)mu * 9 * g.Vh + s;
+    float4 *oc = (par ? l32co : l32ce) + (long long)mu * 3 * g.Vh + s;
+    double2 v[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) v[k] = u[k];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        o64[k * g.Vh] = v[k];
+        o32[k * g.Vh] = make_float2((float)v[k].x, (float)v[k].y);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        oc[k * g.Vh] = make_float4((float)v[2 * k].x, (float)v[2 * k].y, (float)v[2 * k + 1].x,
+                                   (float)v[2 * k + 1].y);
+}
+
+// one thread per (full site, rhs)
+__global__ void k_pack_spinor(const double2 *lex, Geom g, int n, int prec, void *ev, void *od)
+{
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= g.V * n) return;
+    const long long i = gid % g.V;
+    const int r = (int)(gid / g.V);
+    int t, x, y, z;
+    coords_full(g, i, t, x, y, z);
+    const int par = (t + x + y + z) & 1;
+    const long long s = i >> 1;
+    const double2 *src = lex + ((long long)r * g.V + i) * 12;
+    const long long cs = g.Vh * n, me = s * n + r;
+    if (prec == 0) {
+        double2 *o = static_cast<double2 *>(par ? od : ev) + me;
+#pragma unroll
+        for (int k = 0; k < 12; k++) o[k * cs] = src[k];
+    } else {
+        float4 *o = static_cast<float4 *>(par ? od : ev) + me;
+#pragma unroll
+        for (int k = 0; k < 6; k++)
+            o[k * cs] = make_float4((float)src[2 * k].x, (float)src[2 * k].y,
+                                    (float)src[2 * k + 1].x, (float)src[2 * k + 1].y);
+    }
+}
+
+__global__ void k_unpack_spinor(const void *ev, const void *od, Geom g, int n, int prec,
+                                double2 *lex)
+{
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= g.V * n) return;
+    const long long i = gid % g.V;
+    const int r = (int)(gid / g.V);
+    int t, x, y, z;
+    coords_full(g, i, t, x, y, z);
+    const int par = (t + x + y + z) & 1;
+    const long long s = i >> 1;
+    double2 *dst = lex + ((long long)r * g.V + i) * 12;
+    const long long cs = g.Vh * n, me = s * n + r;
+    if (prec == 0) {
+        const double2 *o = static_cast<const double2 *>(par ? od : ev) + me;
+#pragma unroll
+        for (int k = 0; k < 12; k++) dst[k] = o[k * cs];
+    } else {
+        const float4 *o = static_cast<const float4 *>(par ? od : ev) + me;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            const float4 v = o[k * cs];
+            dst[2 * k] = make_double2(v.x, v.y);
+            dst[2 * k + 1] = make_double2(v.z, v.w);
+        }
+    }
+}
+
+__global__ void k_point_source(Geom g, const SlotInfo *slots, int n, const int *mask, double2 *ev,
+                               double2 *od)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    if (mask && !mask[k]) return;
+    const SlotInfo sl = slots[k];
+    const int par = (sl.t + sl.x + sl.y + sl.z) & 1;
+    const long long s = ((((long long)sl.t * g.Lz + sl.z) * g.Ly + sl.y) * g.Lx + sl.x) >> 1;
+    double2 *b = par ? od : ev;
+    b[((long long)sl.comp * g.Vh + s) * n + k] = make_double2(sl.scale, 0.0);
+}
+
+constexpr int kContractBlock = 256;
+
+// grid (P, T): block (p, t) sums |S'|^2/alpha_B^2 over its share of slice t,
+// per group; partials[(t*P + p)*ng + grp]
+__global__ void __launch_bounds__(kContractBlock)
+    k_contract(const double2 *xe, const double2 *xo, Geom g, int n, const double *alpha,
+               const SlotInfo *slots, const int *mask, int ng, double *partials, double2 *prop)
+{
+    const int P = gridDim.x, p = blockIdx.x, t = blockIdx.y;
+    const long long Vs = g.Vh / g.T;  // half-sites per slice per parity
+    const long long chunk = (Vs + P - 1) / P;
+    const long long j0 = p * chunk, j1 = min(Vs, j0 + chunk);
+    const int nm = ng;
+    const long long cs = g.Vh * n;
+    double loc[kMaxGroups];
+    for (int m = 0; m < kMaxGroups; m++) loc[m] = 0;
+    const long long work = (j1 > j0 ? j1 - j0 : 0) * n;
+    for (long long e = threadIdx.x; e < work; e += blockDim.x) {
+        const long long s = (long long)t * Vs + j0 + e / n;
+        const int r = (int)(e % n);
+        if (mask && !mask[r]) continue;
+        const int xh = (int)(s % g.Lxh);
+        long long q = s / g.Lxh;
+        const int y = (int)(q % g.Ly);
+        q /= g.Ly;
+        const int z = (int)(q % g.Lz);
+        const int grp = slots[r].group;
+        const double *al = alpha + (long long)grp * 4 * g.Lmax;
+        const double base = al[0 * g.Lmax + t] * al[2 * g.Lmax + y] * al[3 * g.Lmax + z];
+        double acc = 0;
+        for (int par = 0; par < 2; par++) {
+            const int x = 2 * xh + ((t + y + z + par) & 1);
+            const double inv = 1.0 / (base * al[1 * g.Lmax + x]);
+            const double2 *v = (par ? xo : xe) + s * n + r;
+            double2 *pd = prop ? prop + ((long long)r * g.V + 2 * s + (x & 1)) * 12 : nullptr;
+            double sp = 0;
+            for (int k = 0; k < 12; k++) {
+                double2 c = v[k * cs];
+                c.x *= inv;
+                c.y *= inv;
+                sp = fmx(c.x, c.x, sp);
+                sp = fmx(c.y, c.y, sp);
+                if (pd) pd[k] = c;
+            }
+            acc += sp;
+        }
+#pragma unroll
+        for (int m = 0; m < kMaxGroups; m++)
+            if (m == grp) loc[m] += acc;
+    }
+    __shared__ double sh[kContractBlock];
+    for (int m = 0; m < nm; m++) {
+        sh[threadIdx.x] = loc[m];
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partials[((long long)t * P + p) * nm + m] = sh[0];
+        __syncthreads();
+    }
+}
+
+// cpp[m][(t - t_src[m]) mod T] = -sum_p partials[t][p][m], summed in p order
+__global__ void k_contract_final(const double *partials, int P, int T, int nm, const int *t_src,
+                                 double *cpp)
+{
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= T * nm) return;
+    const int t = id / nm, m = id % nm;
+    double s = 0;
+    for (int p = 0; p < P; p++) s += partials[((long long)t * P + p) * nm + m];
+    const int rel = ((t - t_src[m]) % T + T) % T;
+    cpp[m * T + rel] = -s;
+}
+
+__global__ void k_cpp_commit(const double *src, double *dst, int T, int accumulate)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= T) return;
+    dst[k] = accumulate ? dst[k] + src[k] : src[k];
+}
+
+}  // namespace
+
+cudaError_t launch_pack_links(const double2 *lex, const Geom &g, double2 *l64[2], float2 *l32f[2],
+                              float4 *l32c[2], cudaStream_t st)
+{
+    const int block = 128;
+    const long long n = g.V * 4;
+    k_pack_links<<<(unsigned)((n + block - 1) / block), block, 0, st>>>(
+        lex, g, l64[0], l64[1], l32f[0], l32f[1], l32c[0], l32c[1]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_spinor(const double2 *lex, const Geom &g, int nrhs, int prec,
+                               void *even, void *odd, cudaStream_t st)
+{
+    const int block = 128;
+    const long long n = g.V * nrhs;
+    k_pack_spinor<<<(unsigned)((n + block - 1) / block), block, 0, st>>>(lex, g, nrhs, prec, even,
+                                                                         odd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_spinor(const void *even, const void *odd, const Geom &g, int nrhs,
+                                 int prec, double2 *lex, cudaStream_t st)
+{
+    const int block = 128;
+    const long long n = g.V * nrhs;
+    k_unpack_spinor<<<(unsigned)((n + block - 1) / block), block, 0, st>>>(even, odd, g, nrhs,
+                                                                           prec, lex);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_point_source(const Geom &g, const SlotInfo *slots_dev, int nrhs,
+                                const int *mask, double2 *even, double2 *odd, cudaStream_t st)
+{
+    k_point_source<<<1, kMaxRhs, 0, st>>>(g, slots_dev, nrhs, mask, even, odd);
+    return cudaGetLastError();
+}
+
+// partials must hold T * P * n_mass doubles, P = contract_blocks_per_slice(g)
+int contract_blocks_per_slice(const Geom &g)
+{
+    const long long Vs = g.Vh / g.T;
+    long long P = (Vs + 1023) / 1024;
+    if (P < 1) P = 1;
+    if (P > 64) P = 64;
+    return (int)P;
+}
+
+cudaError_t launch_restore_contract(const double2 *xe, const double2 *xo, const Geom &g, int nrhs,
+                                    const double *alpha, const SlotInfo *slots_dev, int ngroups,
+                                    const int *t_src_dev, const int *mask, double *cpp_dev,
+                                    double *partials, double2 *prop_lex, cudaStream_t st)
+{
+    if (ngroups < 1 || ngroups > kMaxGroups) return cudaErrorInvalidValue;
+    const int P = contract_blocks_per_slice(g);
+    dim3 grid(P, g.T);
+    k_contract<<<grid, kContractBlock, 0, st>>>(xe, xo, g, nrhs, alpha, slots_dev, mask, ngroups,
+                                                partials, prop_lex);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int tot = g.T * ngroups;
+    k_contract_final<<<(tot + 127) / 128, 128, 0, st>>>(partials, P, g.T, ngroups, t_src_dev, cpp_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cpp_commit(const double *src, double *dst, int T, int accumulate, cudaStream_t st)
+{
+    k_cpp_commit<<<(T + 127) / 128, 128, 0, st>>>(src, dst, T, accumulate);
+    return cudaGetLastError();
+}
+
+}  // namespace dp

@@ -1,0 +1,731 @@
+// The method for point-source jobs on one gauge field, as a slot-based batch:
+//
+//   1. profile tables and source scaling eta' = alpha_B(x_src) eta
+//      (Sec. II eq. redeft; Sec. III eq. redefa);
+//   2. even-odd Schur form of (D'+M) S' = eta' (eq. linsysprec):
+//        Mhat = 1 - A_ee^-1 D_eo A_oo^-1 D_oe,
+//        bhat = A_ee^-1 (eta'_e - D_eo A_oo^-1 eta'_o);
+//   3. Krylov solve of Mhat x_e = bhat to relative residue r (eq. stopping,
+//      read as a relative L2 norm on the preconditioned system): an FP64
+//      defect-correction loop (true Schur residual in FP64 every round) around
+//      an inner BiCGStab in FP32 (mixed precision) or FP64 (plain);
+//   4. x_o = A_oo^-1 (eta'_o - D_oe x_e);
+//   5. restore S = S'/alpha_B per site and contract C_PP(y0) (Sec. II eq.
+//      backcorrection; Sec. III: restore before contracting).
+//
+// A batch holds n RHS slots.  A job (one mass, profile and source; 12
+// spin-colour components, or one component for the unbatched FP64 baseline)
+// occupies contiguous slots.  Jobs are admitted and completed between rounds,
+// which is what the request scheduler uses for continuous batching.  Every
+// decision (convergence, breakdown, iteration cap) is per RHS on the device
+// and converged or empty slots are masked out of every kernel, so a job's
+// arithmetic does not depend on the other slots.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "batch.h"
+
+namespace dp {
+
+#define CK(expr)                                                                 \
+    do {                                                                         \
+        cudaError_t e_ = (expr);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            set_error("%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return DP_ERR_CUDA;                                                  \
+        }                                                                        \
+    } while (0)
+
+namespace {
+
+dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void *out,
+                 const void *x, const int *mask, int mask_stride)
+{
+    DslashParams P{};
+    P.in = in;
+    P.out = out;
+    P.x = x;
+    const Field &f = *op.f;
+    if (op.pr == 0) {
+        P.links[0] = f.l64[0];
+        P.links[1] = f.l64[1];
+    } else if (op.lf == LINK_F32_12) {
+        P.links[0] = f.l32c[0];
+        P.links[1] = f.l32c[1];
+    } else {
+        P.links[0] = f.l32f[0];
+        P.links[1] = f.l32f[1];
+    }
+    for (int k = 0; k < kMaxGroups; k++) P.clov[k] = op.inv[parity][k];
+    P.hop = op.hop;
+    P.active = mask;
+    P.active_stride = mask_stride;
+    P.g = f.g;
+    P.parity = parity;
+    P.nrhs = op.nrhs;
+    memcpy(P.grp_of, op.grp_of, sizeof P.grp_of);
+    const char *name = op.pr == 0 ? "dslash_fp64" : "dslash_fp32";
+    cudaEvent_t ev;
+    c->time_begin(name, &ev);
+    CK(launch_dslash(P, op.pr, op.lf, epi, op.block, c->stream));
+    c->time_end(name, ev);
+    c->launches++;
+    return DP_OK;
+}
+
+constexpr int kStateStride = (int)(sizeof(RhsState) / sizeof(int));
+
+const int *state_mask(const RhsState *st) { return st ? &st[0].active : nullptr; }
+
+// y = Mhat x = x - A_ee^-1 D_eo A_oo^-1 D_oe x ; tmp: odd-parity vector
+dp_status apply_mhat(Ctx *c, const Op &op, const void *x, void *y, void *tmp,
+                     const RhsState *mask)
+{
+    dp_status s = dslash(c, op, 1, EPI_AINV, x, tmp, nullptr, state_mask(mask), kStateStride);
+    if (s != DP_OK) return s;
+    return dslash(c, op, 0, EPI_XMY_AINV, tmp, y, x, state_mask(mask), kStateStride);
+}
+
+}  // namespace
+
+Batch::Batch(Ctx *cc, std::shared_ptr<Field> ff, int nslots, const dp_solve_opts &o, int round_cap)
+    : c(cc), f(std::move(ff)), n(nslots), opts(o), round_iters(round_cap)
+{
+}
+
+Batch::~Batch()
+{
+    if (graph) cudaGraphExecDestroy(graph);
+    for (void *p : owned) c->release(p);
+}
+
+void *Batch::get(size_t bytes)
+{
+    void *p = c->alloc(bytes);
+    if (p) {
+        owned.push_back(p);
+        total_bytes += bytes;
+    }
+    return p;
+}
+
+size_t Batch::bytes_needed(const Geom &g, int nslots, int prec)
+{
+    const size_t v64 = (size_t)g.Vh * nslots * 24 * sizeof(double);
+    const size_t vin = (size_t)g.Vh * nslots * 24 * (prec == DP_PREC_FP64 ? 8 : 4);
+    return 5 * v64 + 8 * vin + ((size_t)1 << 20);
+}
+
+dp_status Batch::init()
+{
+    const Geom &g = f->g;
+    mixed = opts.prec != DP_PREC_FP64;
+    ipr = mixed ? 1 : 0;
+    ilf = mixed ? (opts.compress12 ? LINK_F32_12 : LINK_F32_18) : LINK_F64_18;
+    const long long Vh = g.Vh;
+    const int Lm = g.Lmax;
+    v64 = (size_t)Vh * n * 24 * sizeof(double);
+    vin = (size_t)Vh * n * 24 * (ipr == 0 ? 8 : 4);
+    bh = (double2 *)get(v64);
+    x = (double2 *)get(v64);
+    r64 = (double2 *)get(v64);
+    y64 = (double2 *)get(v64);
+    to64 = (double2 *)get(v64);
+    bool ok = bh && x && r64 && y64 && to64;
+    void **iv[8] = {&in.r, &in.rh, &in.p, &in.v, &in.s, &in.t, &in.x, &in.to};
+    for (auto pp : iv) {
+        *pp = get(vin);
+        ok = ok && *pp;
+    }
+    outer = (RhsState *)get(sizeof(RhsState) * kMaxRhs);
+    inner = (RhsState *)get(sizeof(RhsState) * kMaxRhs);
+    alpha_d = (double *)get(sizeof(double) * kMaxGroups * 4 * Lm);
+    hop64_d = (double *)get(sizeof(double) * kMaxGroups * 8 * Lm);
+    hop32_d = (float *)get(sizeof(float) * kMaxGroups * 8 * Lm);
+    slots_d = (SlotInfo *)get(sizeof(SlotInfo) * kMaxRhs);
+    tsrc_d = (int *)get(sizeof(int) * kMaxGroups);
+    mask_d = (int *)get(sizeof(int) * kMaxRhs);
+    cpp_d = (double *)get(sizeof(double) * kMaxGroups * g.T);
+    cpart = (double *)get(sizeof(double) * (size_t)g.T * contract_blocks_per_slice(g) * kMaxGroups);
+    nrm_d = (double *)get(sizeof(double) * kMaxRhs);
+    ok = ok && outer && inner && alpha_d && hop64_d && hop32_d && slots_d && tsrc_d && mask_d &&
+         cpp_d && cpart && nrm_d;
+    if (!ok) {
+        set_error("out of device memory for a %d-slot solver batch (%zu bytes per FP64 vector)", n, v64);
+        return DP_ERR_OOM;
+    }
+    hs.assign(kMaxRhs, RhsState{});
+    hin.assign(kMaxRhs, RhsState{});
+    slot_job.assign(n, nullptr);
+    slot_inner.assign(n, 0);
+    slot_outer.assign(n, 0);
+    slot_rr_prev.assign(n, 0.0);
+    slot_stall.assign(n, 0);
+    slots.assign(kMaxRhs, SlotInfo{});
+    CK(cudaMemsetAsync(outer, 0, sizeof(RhsState) * kMaxRhs, c->stream));
+    CK(cudaMemsetAsync(inner, 0, sizeof(RhsState) * kMaxRhs, c->stream));
+    CK(cudaMemsetAsync(alpha_d, 0, sizeof(double) * kMaxGroups * 4 * Lm, c->stream));
+    CK(cudaMemsetAsync(hop64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, c->stream));
+    CK(cudaMemsetAsync(hop32_d, 0, sizeof(float) * kMaxGroups * 8 * Lm, c->stream));
+
+    op64 = Op{};
+    op64.f = f.get();
+    op64.pr = 0;
+    op64.lf = LINK_F64_18;
+    op64.hop = hop64_d;
+    op64.nrhs = n;
+    op64.block = c->block_for(Vh, 0, LINK_F64_18, n);
+    opin = op64;
+    opin.pr = ipr;
+    opin.lf = ilf;
+    opin.hop = ipr == 0 ? (const void *)hop64_d : (const void *)hop32_d;
+    opin.block = c->block_for(Vh, ipr, ilf, n);
+    check_every = opts.check_every > 0 ? opts.check_every : (Vh * n >= (1 << 20) ? 2 : 8);
+    return DP_OK;
+}
+
+int Batch::active_jobs() const
+{
+    int k = 0;
+    for (auto *j : jobs)
+        if (j) k++;
+    return k;
+}
+
+bool Batch::can_admit(int ncomp) const
+{
+    int free_tab = -1;
+    for (int k = 0; k < kMaxGroups; k++)
+        if (!jobs[k]) {
+            free_tab = k;
+            break;
+        }
+    if (free_tab < 0) return false;
+    for (int s0 = 0; s0 + ncomp <= n; s0 += ncomp) {
+        bool fr = true;
+        for (int k = 0; k < ncomp; k++)
+            if (slot_job[s0 + k]) fr = false;
+        if (fr) return true;
+    }
+    return false;
+}
+
+dp_status Batch::upload_mask(const std::vector<int> &m)
+{
+    CK(cudaMemcpyAsync(mask_d, m.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+    // the host vector may go away: make the copy complete before returning
+    CK(cudaStreamSynchronize(c->stream));
+    return DP_OK;
+}
+
+dp_status Batch::admit(Job *j)
+{
+    const Geom &g = f->g;
+    const int Lm = g.Lmax;
+    int tab = -1, s0 = -1;
+    for (int k = 0; k < kMaxGroups; k++)
+        if (!jobs[k]) {
+            tab = k;
+            break;
+        }
+    for (int b = 0; b + j->ncomp <= n && tab >= 0; b += j->ncomp) {
+        bool fr = true;
+        for (int k = 0; k < j->ncomp; k++)
+            if (slot_job[b + k]) fr = false;
+        if (fr) {
+            s0 = b;
+            break;
+        }
+    }
+    if (tab < 0 || s0 < 0) {
+        set_error("no free slots in the batch");
+        return DP_ERR_REJECTED;
+    }
+    // tables and clover inverse of the job
+    std::vector<double> alpha(4 * Lm), hop(8 * Lm);
+    dp_profile pf = j->grp.prof;
+    for (int mu = 0; mu < 4; mu++)
+        if (pf.kind == DP_PROF_TABLE) pf.table[mu] = j->grp.table[mu].data();
+    dp_status s = profile_tables(pf, g, f->bc_t, j->grp.src, alpha.data(), hop.data());
+    if (s != DP_OK) return s;
+    double scale = 1.0;
+    for (int mu = 0; mu < 4; mu++) scale *= alpha[mu * Lm + j->grp.src[mu]];
+    std::shared_ptr<CloverInv> ci;
+    s = get_clover_inv(c, *f, j->grp.M, &ci);
+    if (s != DP_OK) return s;
+    std::vector<float> hopf(hop.begin(), hop.end());
+    CK(cudaMemcpyAsync(alpha_d + (size_t)tab * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(hop64_d + (size_t)tab * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(hop32_d + (size_t)tab * 8 * Lm, hopf.data(), sizeof(float) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
+    const int ts = j->grp.src[0];
+    CK(cudaMemcpyAsync(tsrc_d + tab, &ts, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    invs[tab] = ci;
+    for (int p = 0; p < 2; p++) {
+        op64.inv[p][tab] = ci->inv64[p];
+        opin.inv[p][tab] = ipr == 0 ? (const void *)ci->inv64[p] : (const void *)ci->inv32[p];
+    }
+    for (int k = 0; k < j->ncomp; k++) {
+        SlotInfo &sl = slots[s0 + k];
+        sl.group = tab;
+        sl.comp = j->comp0 + k;
+        sl.t = j->grp.src[0];
+        sl.x = j->grp.src[1];
+        sl.y = j->grp.src[2];
+        sl.z = j->grp.src[3];
+        sl.scale = scale;
+        op64.grp_of[s0 + k] = opin.grp_of[s0 + k] = (int8_t)tab;
+        slot_job[s0 + k] = j;
+        slot_inner[s0 + k] = 0;
+        slot_outer[s0 + k] = 0;
+        slot_rr_prev[s0 + k] = 0;
+        slot_stall[s0 + k] = 0;
+    }
+    CK(cudaMemcpyAsync(slots_d + s0, &slots[s0], sizeof(SlotInfo) * j->ncomp, cudaMemcpyHostToDevice, c->stream));
+    j->tab = tab;
+    j->slot0 = s0;
+    j->src_scale = scale;
+    jobs[tab] = j;
+    if (graph) {  // kernel parameters (clover pointers, groups) changed
+        cudaGraphExecDestroy(graph);
+        graph = nullptr;
+    }
+    std::vector<int> m(n, 0);
+    for (int k = 0; k < j->ncomp; k++) m[s0 + k] = 1;
+    s = upload_mask(m);
+    if (s != DP_OK) return s;
+    const long long Vh = g.Vh;
+    // eta'_e -> y64, eta'_o -> to64 (only this job's slots are non-zero)
+    CK(cudaMemsetAsync(y64, 0, v64, c->stream));
+    CK(cudaMemsetAsync(to64, 0, v64, c->stream));
+    CK(launch_point_source(g, slots_d, n, mask_d, y64, to64, c->stream));
+    // to64 <- A_oo^-1 eta'_o (in place), bhat = A_ee^-1 (eta'_e - D_eo to64)
+    CloverApplyParams cp{};
+    for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[1][k];
+    memcpy(cp.grp_of, op64.grp_of, sizeof cp.grp_of);
+    cp.mask = mask_d;
+    cp.in = to64;
+    cp.out = to64;
+    cp.Vh = Vh;
+    cp.nrhs = n;
+    CK(launch_clover_apply(cp, 0, c->stream));
+    s = dslash(c, op64, 0, EPI_AINV_XMY, to64, bh, y64, mask_d, 1);
+    if (s != DP_OK) return s;
+    CK(blas_zero_masked(x, Vh, n, mask_d, c->stream));
+    // outer state rows: active, fresh (r = bhat, |bhat|^2 sets the threshold)
+    for (int k = 0; k < j->ncomp; k++) {
+        RhsState st{};
+        st.active = 1;
+        st.fresh = 1;
+        st.tol2 = j->r * j->r;
+        hs[s0 + k] = st;
+    }
+    CK(cudaMemcpyAsync(outer + s0, &hs[s0], sizeof(RhsState) * j->ncomp, cudaMemcpyHostToDevice, c->stream));
+    CK(blas_residual64(c->bc, bh, y64, r64, Vh, n, outer, mask_d, c->stream));
+    c->launches += 5;
+    CK(cudaStreamSynchronize(c->stream));
+    return DP_OK;
+}
+
+dp_status Batch::bicgstab(int max_iter, int *iters_done)
+{
+    BlasCtx &bc = c->bc;
+    const int pr = opin.pr;
+    const long long Vh = f->g.Vh;
+    CK(blas_bicg_init(bc, pr, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, c->stream));
+    c->launches += 2;
+    CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int it = 0;
+    if (*c->h_nactive == 0) {
+        *iters_done = 0;
+        return DP_OK;
+    }
+    auto body = [&](int first) -> dp_status {
+        CK(blas_bicg_p(bc, pr, in.r, in.p, in.v, Vh, n, inner, first, c->stream));
+        dp_status s = apply_mhat(c, opin, in.p, in.v, in.to, inner);
+        if (s != DP_OK) return s;
+        CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, c->stream));
+        CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, c->stream));
+        s = apply_mhat(c, opin, in.s, in.t, in.to, inner);
+        if (s != DP_OK) return s;
+        CK(blas_bicg_omega(bc, pr, in.t, in.s, Vh, n, inner, c->stream));
+        CK(blas_bicg_update(bc, pr, in.x, in.r, in.p, in.s, in.t, in.rh, Vh, n, inner, max_iter, c->stream));
+        c->launches += 6;
+        return DP_OK;
+    };
+    const bool graphs = opts.use_graph && !c->timing;
+    while (true) {
+        if (it == 0 || !graphs) {
+            dp_status s = body(it == 0);
+            if (s != DP_OK) return s;
+        } else {
+            if (!graph) {
+                cudaGraph_t gr;
+                CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                const long before = c->launches.load();
+                dp_status s = body(0);
+                cudaError_t ce = cudaStreamEndCapture(c->stream, &gr);
+                c->launches = before;
+                if (s != DP_OK) return s;
+                CK(ce);
+                CK(cudaGraphInstantiate(&graph, gr, 0));
+                cudaGraphDestroy(gr);
+                graph_max_iter = max_iter;
+            }
+            CK(cudaGraphLaunch(graph, c->stream));
+            c->launches += 10;
+        }
+        it++;
+        if (it >= max_iter) break;
+        if (it % check_every == 0) {
+            CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (*c->h_nactive == 0) break;
+        }
+    }
+    *iters_done = it;
+    return DP_OK;
+}
+
+dp_status Batch::round()
+{
+    const long long Vh = f->g.Vh;
+    const int max_outer = 200;
+    // per-RHS stop rules on the host: stagnation of the true residual, round
+    // and iteration caps
+    CK(cudaMemcpyAsync(hs.data(), outer, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int nact = 0;
+    bool changed = false;
+    for (int k = 0; k < n; k++) {
+        if (!slot_job[k] || !hs[k].active) continue;
+        if (slot_outer[k] > 0 && hs[k].rr >= slot_rr_prev[k]) slot_stall[k]++;
+        else slot_stall[k] = 0;
+        slot_rr_prev[k] = hs[k].rr;
+        if (slot_stall[k] >= 3 || slot_outer[k] >= max_outer || slot_inner[k] >= opts.max_iter) {
+            hs[k].active = 0;
+            hs[k].status = 4;
+            changed = true;
+        } else {
+            nact++;
+        }
+    }
+    if (changed) CK(cudaMemcpyAsync(outer, hs.data(), sizeof(RhsState) * n, cudaMemcpyHostToDevice, c->stream));
+    if (nact == 0) return DP_OK;
+    for (int k = 0; k < n; k++)
+        if (slot_job[k] && hs[k].active) slot_outer[k]++;
+    CK(blas_inner_setup(outer, inner, n, opts.inner_tol, 0.0, c->stream));
+    if (mixed)
+        CK(blas_to_f32_scaled(r64, (float4 *)in.rh, Vh, n, outer, c->stream));
+    else
+        CK(blas_scale64(r64, (double2 *)in.rh, Vh, n, outer, c->stream));
+    c->launches += 2;
+    // inner budget of this round
+    int budget = round_iters > 0 ? round_iters : opts.max_iter;
+    int done = 0;
+    dp_status s = bicgstab(budget, &done);
+    if (s != DP_OK) return s;
+    CK(cudaMemcpyAsync(hin.data(), inner, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    bool bad = false;
+    for (int k = 0; k < n; k++) {
+        if (!slot_job[k] || !hs[k].active) continue;
+        slot_inner[k] += hin[k].iters;
+        if (hin[k].status == 3) {
+            hs[k].active = 0;
+            hs[k].status = 3;
+            bad = true;
+        }
+    }
+    if (bad) CK(cudaMemcpyAsync(outer, hs.data(), sizeof(RhsState) * n, cudaMemcpyHostToDevice, c->stream));
+    if (mixed)
+        CK(blas_acc_f32(x, (const float4 *)in.x, Vh, n, outer, c->stream));
+    else
+        CK(blas_acc64(x, (const double2 *)in.x, Vh, n, outer, c->stream));
+    s = apply_mhat(c, op64, x, y64, to64, outer);
+    if (s != DP_OK) return s;
+    CK(blas_residual64(c->bc, bh, y64, r64, Vh, n, outer, nullptr, c->stream));
+    c->launches += 3;
+    return DP_OK;
+}
+
+dp_status Batch::harvest(std::vector<Job *> &finished)
+{
+    const Geom &g = f->g;
+    const long long Vh = g.Vh;
+    CK(cudaMemcpyAsync(hs.data(), outer, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int tab = 0; tab < kMaxGroups; tab++) {
+        Job *j = jobs[tab];
+        if (!j) continue;
+        bool all = true;
+        for (int k = 0; k < j->ncomp; k++)
+            if (hs[j->slot0 + k].active) all = false;
+        if (!all) continue;
+        std::vector<int> m(n, 0);
+        for (int k = 0; k < j->ncomp; k++) m[j->slot0 + k] = 1;
+        dp_status s = upload_mask(m);
+        if (s != DP_OK) return s;
+        // eta'_o again (to64; y64 takes the even part), then x_o -> y64
+        CK(cudaMemsetAsync(y64, 0, v64, c->stream));
+        CK(cudaMemsetAsync(to64, 0, v64, c->stream));
+        CK(launch_point_source(g, slots_d, n, mask_d, y64, to64, c->stream));
+        s = dslash(c, op64, 1, EPI_AINV_XMY, x, y64, to64, mask_d, 1);
+        if (s != DP_OK) return s;
+        // residual report: the full residual of (D'+M)S' = eta' is (A_ee rhat, 0)
+        // with x_o rebuilt from x_e, so |A_ee rhat| / |eta'|
+        CloverApplyParams cp{};
+        for (int k = 0; k < kMaxGroups; k++) {
+            cp.mat[k] = f->clov[0];
+            cp.diag[k] = jobs[k] ? 4.0 + jobs[k]->grp.M : 0.0;
+        }
+        memcpy(cp.grp_of, op64.grp_of, sizeof cp.grp_of);
+        cp.mask = mask_d;
+        cp.in = r64;
+        cp.out = to64;
+        cp.Vh = Vh;
+        cp.nrhs = n;
+        CK(launch_clover_apply(cp, 0, c->stream));
+        CK(blas_norm2(c->bc, 0, to64, Vh, n, nrm_d, c->stream));
+        double2 *prop_d = nullptr;
+        void *prop_tmp = nullptr;
+        if (j->prop_host) {
+            prop_tmp = c->alloc((size_t)g.V * 24 * sizeof(double) * n);
+            if (!prop_tmp) {
+                set_error("out of device memory for the propagator");
+                return DP_ERR_OOM;
+            }
+            prop_d = (double2 *)prop_tmp;
+        }
+        CK(launch_restore_contract(x, y64, g, n, alpha_d, slots_d, kMaxGroups, tsrc_d, mask_d, cpp_d,
+                                   cpart, prop_d, c->stream));
+        if (j->cpp_dst) CK(launch_cpp_commit(cpp_d + (size_t)tab * g.T, j->cpp_dst, g.T, j->accumulate, c->stream));
+        if (j->cpp_host) CK(cudaMemcpyAsync(j->cpp_host, cpp_d + (size_t)tab * g.T, sizeof(double) * g.T, cudaMemcpyDeviceToHost, c->stream));
+        if (prop_d)
+            CK(cudaMemcpyAsync(j->prop_host, prop_d + (size_t)j->slot0 * g.V * 12,
+                               sizeof(double) * 24 * g.V * j->ncomp, cudaMemcpyDeviceToHost, c->stream));
+        std::vector<double> nr(n);
+        CK(cudaMemcpyAsync(nr.data(), nrm_d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (prop_tmp) c->release(prop_tmp);
+        c->launches += 6;
+        SolveResult &R = j->res;
+        R = SolveResult{};
+        R.status = DP_OK;
+        for (int k = 0; k < j->ncomp; k++) {
+            const int sl = j->slot0 + k;
+            R.iters_inner = std::max(R.iters_inner, slot_inner[sl]);
+            R.iters_outer = std::max(R.iters_outer, slot_outer[sl]);
+            R.true_rel_residue = std::max(R.true_rel_residue, std::sqrt(nr[sl]) / j->src_scale);
+            const int st = hs[sl].status;
+            if (st == 3) R.status = DP_ERR_NONFINITE;
+            else if (st == 2 && R.status == DP_OK) R.status = DP_ERR_BREAKDOWN;
+            else if (st != 1 && R.status == DP_OK) R.status = DP_ERR_NOT_CONVERGED;
+            slot_job[sl] = nullptr;
+        }
+        jobs[tab] = nullptr;
+        invs[tab].reset();
+        j->done = true;
+        finished.push_back(j);
+    }
+    return DP_OK;
+}
+
+dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group> &groups,
+                       double r_target, const dp_solve_opts &o, double *cpp_dev, double *prop_host,
+                       std::vector<SolveResult> &res)
+{
+    const Geom &g = f->g;
+    const int ng = (int)groups.size();
+    if (ng < 1 || 12 * ng > kMaxRhs) {
+        set_error("between 1 and %d point-source groups per batch", kMaxRhs / 12);
+        return DP_ERR_INVALID_ARG;
+    }
+    if (!(r_target > 0) || !(r_target < 1)) {
+        set_error("residue r must be in (0, 1)");
+        return DP_ERR_INVALID_ARG;
+    }
+    const int L[4] = {g.T, g.Lx, g.Ly, g.Lz};
+    for (const Group &gr : groups) {
+        if (!std::isfinite(gr.M)) {
+            set_error("mass is not finite");
+            return DP_ERR_INVALID_ARG;
+        }
+        for (int mu = 0; mu < 4; mu++)
+            if (gr.src[mu] < 0 || gr.src[mu] >= L[mu]) {
+                set_error("source coordinate %d out of range", mu);
+                return DP_ERR_INVALID_ARG;
+            }
+    }
+    res.assign(ng, SolveResult());
+    const bool batched = o.batched != 0;
+    Batch B(c, f, batched ? 12 * ng : 1, o, 0);
+    dp_status s = B.init();
+    if (s != DP_OK) return s;
+    std::vector<Job> jobs(batched ? ng : 12 * ng);
+    for (size_t k = 0; k < jobs.size(); k++) {
+        Job &j = jobs[k];
+        const int gi = batched ? (int)k : (int)k / 12;
+        j.grp = groups[gi];
+        j.comp0 = batched ? 0 : (int)k % 12;
+        j.ncomp = batched ? 12 : 1;
+        j.r = r_target;
+        j.cpp_dst = cpp_dev + (size_t)gi * g.T;
+        j.accumulate = batched ? 0 : (j.comp0 > 0);
+        if (prop_host) j.prop_host = prop_host + ((size_t)gi * 12 + j.comp0) * g.V * 24;
+    }
+    // batched: all jobs at once; unbatched: one RHS after the other
+    size_t next = 0;
+    std::vector<Job *> fin;
+    while (true) {
+        while (next < jobs.size() && B.can_admit(jobs[next].ncomp)) {
+            s = B.admit(&jobs[next]);
+            if (s != DP_OK) return s;
+            next++;
+        }
+        if (B.active_jobs() == 0) break;
+        s = B.round();
+        if (s != DP_OK) return s;
+        s = B.harvest(fin);
+        if (s != DP_OK) return s;
+    }
+    dp_status ret = DP_OK;
+    for (int gi = 0; gi < ng; gi++) {
+        SolveResult &R = res[gi];
+        R.status = DP_OK;
+        for (size_t k = 0; k < jobs.size(); k++) {
+            const int jg = batched ? (int)k : (int)k / 12;
+            if (jg != gi) continue;
+            const SolveResult &J = jobs[k].res;
+            if (batched) {
+                R = J;
+            } else {
+                R.iters_inner = std::max(R.iters_inner, J.iters_inner);
+                R.iters_outer = std::max(R.iters_outer, J.iters_outer);
+                R.true_rel_residue = std::max(R.true_rel_residue, J.true_rel_residue);
+                if (J.status != DP_OK && R.status == DP_OK) R.status = J.status;
+            }
+        }
+        if (R.status != DP_OK && ret == DP_OK) ret = (dp_status)R.status;
+    }
+    if (ret != DP_OK) set_error("solve finished with status %d (see per-mass info)", ret);
+    return ret;
+}
+
+}  // namespace dp
+
+using namespace dp;
+
+static dp_status solve_common(dp_ctx *ctx, dp_field field, int n_mass, const double *M,
+                              const dp_profile *profiles, const int src[4], double r,
+                              const dp_solve_opts *opts, double *cpp_out, int cpp_on_device,
+                              double *prop_out, dp_solve_info *info)
+{
+    if (!ctx) {
+        set_error("null context");
+        return DP_ERR_INVALID_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    Ctx &c = ctx->c;
+    if (cudaSetDevice(c.device) != cudaSuccess) {
+        set_error("cudaSetDevice failed");
+        return DP_ERR_CUDA;
+    }
+    auto fp = find_field(&c, field);
+    if (!fp) {
+        set_error("unknown field");
+        return DP_ERR_NOT_FOUND;
+    }
+    if (n_mass < 1 || n_mass > kMaxRhs / 12 || !M || !profiles || !src || !cpp_out) {
+        set_error("invalid argument (n_mass in [1, %d], non-null M, profiles, src, cpp_out)", kMaxRhs / 12);
+        return DP_ERR_INVALID_ARG;
+    }
+    dp_solve_opts o;
+    dp_status s = check_opts(opts, &o);
+    if (s != DP_OK) return s;
+    if (!opts) o.batched = 1;
+    const int L[4] = {fp->g.T, fp->g.Lx, fp->g.Ly, fp->g.Lz};
+    std::vector<Group> groups(n_mass);
+    for (int k = 0; k < n_mass; k++) {
+        groups[k].M = M[k];
+        groups[k].prof = profiles[k];
+        for (int mu = 0; mu < 4; mu++) {
+            groups[k].src[mu] = src[mu];
+            if (profiles[k].kind == DP_PROF_TABLE) {
+                if (!profiles[k].table[mu]) {
+                    set_error("TABLE profile without table for direction %d", mu);
+                    return DP_ERR_INVALID_ARG;
+                }
+                groups[k].table[mu].assign(profiles[k].table[mu], profiles[k].table[mu] + L[mu]);
+            }
+        }
+    }
+    fp->users++;
+    double *cpp_dev = cpp_out;
+    void *tmp = nullptr;
+    if (!cpp_on_device) {
+        tmp = c.alloc(sizeof(double) * n_mass * fp->g.T);
+        cpp_dev = (double *)tmp;
+    }
+    std::vector<SolveResult> res;
+    if (!cpp_dev) {
+        fp->users--;
+        set_error("out of device memory");
+        return DP_ERR_OOM;
+    }
+    s = solve_groups(&c, fp, groups, r, o, cpp_dev, prop_out, res);
+    if (!cpp_on_device && (s == DP_OK || s == DP_ERR_NOT_CONVERGED || s == DP_ERR_BREAKDOWN)) {
+        cudaMemcpyAsync(cpp_out, cpp_dev, sizeof(double) * n_mass * fp->g.T, cudaMemcpyDeviceToHost, c.stream);
+    }
+    cudaStreamSynchronize(c.stream);
+    if (tmp) c.release(tmp);
+    fp->users--;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info)
+        for (int k = 0; k < n_mass; k++) {
+            info[k] = dp_solve_info{};
+            if (k < (int)res.size()) {
+                info[k].iters_inner = res[k].iters_inner;
+                info[k].iters_outer = res[k].iters_outer;
+                info[k].true_rel_residue = res[k].true_rel_residue;
+                info[k].status = res[k].status;
+            } else {
+                info[k].status = s;
+            }
+            info[k].seconds = secs;
+            info[k].n_rhs = 12;
+        }
+    return s;
+}
+
+extern "C" {
+
+dp_status dp_solve_point(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
+                         const int src[4], double r, const dp_solve_opts *opts, double *cpp_out,
+                         double *prop_out, dp_solve_info *info)
+{
+    dp_profile none{};
+    none.kind = DP_PROF_NONE;
+    return solve_common(ctx, field, 1, &M, profile ? profile : &none, src, r, opts, cpp_out, 0,
+                        prop_out, info);
+}
+
+dp_status dp_solve_point_multi(dp_ctx *ctx, dp_field field, int n_mass, const double *M,
+                               const dp_profile *profiles, const int src[4], double r,
+                               const dp_solve_opts *opts, double *cpp_out, double *prop_out,
+                               dp_solve_info *info)
+{
+    return solve_common(ctx, field, n_mass, M, profiles, src, r, opts, cpp_out, 0, prop_out, info);
+}
+
+dp_status dp_solve_point_dev(dp_ctx *ctx, dp_field field, int n_mass, const double *M,
+                             const dp_profile *profiles, const int src[4], double r,
+                             const dp_solve_opts *opts, double *cpp_out_dev, dp_solve_info *info)
+{
+    return solve_common(ctx, field, n_mass, M, profiles, src, r, opts, cpp_out_dev, 1, nullptr, info);
+}
+
+}  // extern "C"

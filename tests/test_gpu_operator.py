@@ -1,0 +1,144 @@
+"""GPU parity of the operator kernels against the CPU oracle, through the C ABI.
+
+Tolerances (per site, |GPU(x) - oracle(x)|_2 / |oracle(x)|_2, max over sites):
+FP64 1e-13, FP32 1e-6 (the FP32 path is fed the FP32-rounded spinor and links,
+the oracle the FP64 ones).
+"""
+import numpy as np
+import pytest
+
+import lattice_inputs as li
+import oracle
+import paper_1006_4028_gb300 as dp
+from gpu_common import field, per_site_rel, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+PROFILES = [("none", 0.0, (0, 0, 0, 0)), ("cosh_t", 0.4, (3, 1, 2, 0)),
+            ("exp_t", 0.4, (0, 0, 0, 0)), ("cosh_4d", 0.2, (5, 3, 0, 1))]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    c = dp.dp_create(0)
+    yield c
+    dp.dp_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def setup(ctx):
+    dims = (8, 4, 6, 4)
+    U = field(dims, 0.5, 11)
+    f = dp.dp_field_load(ctx, U, dims, -1)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    op = oracle.WilsonClover(U, dims, 1.7, -1)
+    psi = li.random_spinor(dims, 3, 12)
+    return dims, f, op, psi
+
+
+@pytest.mark.parametrize("prof", PROFILES)
+def test_hop_fp64(ctx, setup, prof):
+    dims, f, op, psi = setup
+    kind, a0, src = prof
+    got = dp.dp_apply(ctx, f, "hop", 0.0, (kind, a0), src, "fp64", psi)
+    ref = op.hop(psi, (kind, a0, src))
+    assert per_site_rel(got, ref) < 1e-13
+
+
+@pytest.mark.parametrize("prof", PROFILES)
+@pytest.mark.parametrize("c12", [0, 1])
+def test_hop_fp32(ctx, setup, prof, c12):
+    dims, f, op, psi = setup
+    kind, a0, src = prof
+    got = dp.dp_apply(ctx, f, "hop", 0.0, (kind, a0), src, "mixed_fp32", psi, compress12=c12)
+    ref = op.hop(psi, (kind, a0, src))
+    assert per_site_rel(got, ref) < 1e-6
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("mixed_fp32", 1e-6)])
+def test_clover_and_full_operator(ctx, setup, prec, tol):
+    dims, f, op, psi = setup
+    got = dp.dp_apply(ctx, f, "clover", 0.0, None, None, prec, psi)
+    assert per_site_rel(got, op.clover(psi)) < tol
+    M = 0.3
+    prof = ("cosh_4d", 0.3, (1, 2, 3, 0))
+    got = dp.dp_apply(ctx, f, "full", M, prof[:2], prof[2], prec, psi)
+    assert per_site_rel(got, op.apply(psi, M, prof)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed_fp32", 2e-6)])
+def test_clover_inverse(ctx, setup, prec, tol):
+    dims, f, op, psi = setup
+    M = 0.05
+    y = dp.dp_apply(ctx, f, "clover_inv", M, None, None, prec, psi)
+    back = (4 + M) * y + op.clover(y)
+    assert per_site_rel(back, psi) < tol
+
+
+def test_free_field_clover_vanishes_and_unit_links(ctx):
+    dims = (4, 4, 4, 4)
+    U = li.unit_links(dims)
+    f = dp.dp_field_load(ctx, U, dims, -1)
+    dp.dp_field_set_csw(ctx, f, 1.9)
+    psi = li.random_spinor(dims, 1, 3)
+    assert np.abs(dp.dp_apply(ctx, f, "clover", 0.0, None, None, "fp64", psi)).max() == 0.0
+    op = oracle.WilsonClover(U, dims, 1.9, -1)
+    got = dp.dp_apply(ctx, f, "full", 0.5, None, None, "fp64", psi)
+    assert per_site_rel(got, op.apply(psi, 0.5)) < 1e-13
+    dp.dp_field_free(ctx, f)
+
+
+def test_periodic_time_and_many_rhs(ctx):
+    dims = (4, 6, 4, 2)
+    U = field(dims, 0.3, 5)
+    f = dp.dp_field_load(ctx, U, dims, +1)
+    dp.dp_field_set_csw(ctx, f, 1.0)
+    op = oracle.WilsonClover(U, dims, 1.0, +1)
+    psi = li.random_spinor(dims, 13, 6)  # ragged: 13 RHS
+    got = dp.dp_apply(ctx, f, "full", 0.1, ("exp_t", 0.3), (1, 0, 0, 0), "fp64", psi)
+    assert per_site_rel(got, op.apply(psi, 0.1, ("exp_t", 0.3, (1, 0, 0, 0)))) < 1e-13
+    dp.dp_field_free(ctx, f)
+
+
+def test_invalid_arguments_are_errors(ctx):
+    dims = (4, 4, 4, 4)
+    U = li.unit_links(dims)
+    with pytest.raises(dp.DpError) as e:
+        dp.dp_field_load(ctx, U, (4, 3, 4, 4), -1)
+    assert e.value.status == 1
+    bad = U.copy()
+    bad[0, 0, 0, 0, 0, 0, 0] = np.nan
+    with pytest.raises(dp.DpError) as e:
+        dp.dp_field_load(ctx, bad, dims, -1)
+    assert e.value.status == 1
+    with pytest.raises(dp.DpError) as e:
+        dp.dp_field_set_csw(ctx, 987654, 1.0)
+    assert e.value.status == 9
+    f = dp.dp_field_load(ctx, U, dims, -1)
+    psi = li.random_spinor(dims, 1, 1)
+    with pytest.raises(dp.DpError):  # clover not built yet
+        dp.dp_apply(ctx, f, "full", 0.1, None, None, "fp64", psi)
+    psi[0, 0, 0, 0, 0, 0, 0] = np.inf
+    with pytest.raises(dp.DpError):
+        dp.dp_apply(ctx, f, "hop", 0.1, None, None, "fp64", psi)
+    dp.dp_field_free(ctx, f)
+    with pytest.raises(dp.DpError):
+        dp.dp_field_free(ctx, f)
+
+
+def test_full_size_48x24_fp32_hop(ctx):
+    """One multi-RHS FP32 hopping application on the 48x24^3 heavy-quark
+    lattice (eps = 0.3, seed 1), all sites compared with the oracle."""
+    dims = (48, 24, 24, 24)
+    U = li.su3_links(dims, 0.3, 1)
+    f = dp.dp_field_load(ctx, U, dims, -1)
+    psi = li.random_spinor(dims, 2, 21)
+    prof = ("cosh_t", 0.4)
+    got = dp.dp_apply(ctx, f, "hop", 0.0, prof, (0, 0, 0, 0), "mixed_fp32", psi, compress12=1)
+    op = oracle.WilsonClover(U, dims, 0.0, -1)
+    ref = op.hop(psi, ("cosh_t", 0.4, (0, 0, 0, 0)))
+    assert per_site_rel(got, ref) < 1e-6
+    got64 = dp.dp_apply(ctx, f, "hop", 0.0, prof, (0, 0, 0, 0), "fp64", psi[:1])
+    assert per_site_rel(got64, ref[:1]) < 1e-13
+    dp.dp_field_free(ctx, f)

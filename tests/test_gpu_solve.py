@@ -1,0 +1,158 @@
+"""GPU solves (source scaling, Schur solve, restore, contraction) against the
+oracle, through the C ABI.
+
+Tolerance: per-time-slice relative deviation of C_PP(y0) <= 1e-6 out to
+y0 = T/2, against the oracle's tight-residue (1e-13) solve or, in the free
+theory, the exact momentum-space propagator.
+"""
+import numpy as np
+import pytest
+
+import lattice_inputs as li
+import oracle
+import paper_1006_4028_gb300 as dp
+from gpu_common import field, per_site_rel, require_gpu, slice_rel
+
+pytestmark = pytest.mark.gpu
+
+MIXED = {"prec": "mixed_fp32", "compress12": 1, "batched": 1, "use_graph": 1}
+MIXED_NOGRAPH = {"prec": "mixed_fp32", "compress12": 0, "batched": 1, "use_graph": 0}
+PLAIN = {"prec": "fp64", "batched": 0, "use_graph": 0}
+FP64_BATCHED = {"prec": "fp64", "batched": 1, "use_graph": 1}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    c = dp.dp_create(0)
+    yield c
+    dp.dp_destroy(c)
+
+
+@pytest.mark.parametrize("opts", [MIXED, PLAIN, FP64_BATCHED])
+def test_free_16x8_exp_profile_matches_momentum_space(ctx, opts):
+    """Free field 16x8^3, antiperiodic time, M = 0.5, exp(alpha0 y0) with
+    alpha0 = 0.4, point source at the origin, r = 1e-11."""
+    dims = (16, 8, 8, 8)
+    f = dp.dp_field_load(ctx, li.unit_links(dims), dims, -1)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    cpp, _, info = dp.dp_solve_point(ctx, f, 0.5, ("exp_t", 0.4), (0, 0, 0, 0), 1e-11, opts, T=16)
+    exact = oracle.free_cpp(dims, 0.5)
+    assert info["status"] == 0
+    assert info["true_rel_residue"] < 1e-10
+    assert slice_rel(cpp, exact, 8) < 1e-6
+    if opts["prec"] == "fp64":
+        assert slice_rel(cpp, exact, 15) < 1e-9
+    dp.dp_field_free(ctx, f)
+
+
+@pytest.fixture(scope="module")
+def inter(ctx):
+    dims = (12, 4, 4, 6)
+    U = field(dims, 0.3, 1)
+    f = dp.dp_field_load(ctx, U, dims, -1)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    op = oracle.WilsonClover(U, dims, 1.7, -1)
+    return dims, f, op
+
+
+CASES = [(0.5, ("cosh_t", 0.4), (0, 0, 0, 0)), (0.8, ("cosh_t", 0.5), (3, 1, 2, 0)),
+         (0.1, ("cosh_4d", 0.2), (5, 2, 1, 3)), (0.5, ("none", 0.0), (1, 0, 0, 1)),
+         (0.5, ("exp_t", 0.3), (2, 3, 3, 5))]
+
+
+@pytest.mark.parametrize("M,prof,src", CASES)
+@pytest.mark.parametrize("opts", [MIXED, MIXED_NOGRAPH, PLAIN])
+def test_interacting_solve_matches_oracle(ctx, inter, M, prof, src, opts):
+    dims, f, op = inter
+    T, V = dims[0], int(np.prod(dims))
+    ref, Sref, oinfo = oracle.solve_point(op, M, prof[0], prof[1], src, tol=1e-13)
+    assert oinfo["converged"]
+    cpp, prop, info = dp.dp_solve_point(ctx, f, M, prof, src, 1e-11, opts, T=T, V=V, want_prop=True)
+    assert info["status"] == 0
+    assert slice_rel(cpp, ref, T // 2) < 1e-6
+    # the restored propagator itself
+    got = prop.reshape((12,) + oracle.array_shape(dims) + (4, 3))
+    assert per_site_rel(got, Sref) < 1e-5
+
+
+def test_multi_mass_batch_equals_single_solves(ctx, inter):
+    dims, f, op = inter
+    T = dims[0]
+    Ms = [0.1, 0.5, 0.8]
+    profs = [("cosh_4d", 0.2), ("cosh_t", 0.4), ("cosh_t", 0.5)]
+    src = (2, 1, 0, 3)
+    multi, _, infos = dp.dp_solve_point_multi(ctx, f, Ms, profs, src, 1e-11, MIXED, T=T)
+    for k in range(3):
+        single, _, _ = dp.dp_solve_point(ctx, f, Ms[k], profs[k], src, 1e-11, MIXED, T=T)
+        assert slice_rel(multi[k], single, T // 2) < 1e-8
+        ref, _, _ = oracle.solve_point(op, Ms[k], profs[k][0], profs[k][1], src, tol=1e-13)
+        assert slice_rel(multi[k], ref, T // 2) < 1e-6
+        assert infos[k]["status"] == 0
+
+
+def test_restored_independent_of_profile(ctx, inter):
+    """Exact similarity transform: every profile restores the same C_PP."""
+    dims, f, op = inter
+    T = dims[0]
+    base, _, _ = dp.dp_solve_point(ctx, f, 0.5, ("none", 0.0), (0, 0, 0, 0), 1e-12, MIXED, T=T)
+    for prof in [("cosh_t", 0.3), ("cosh_t", 0.5), ("exp_t", 0.4), ("cosh_4d", 0.2)]:
+        c, _, _ = dp.dp_solve_point(ctx, f, 0.5, prof, (0, 0, 0, 0), 1e-12, MIXED, T=T)
+        assert slice_rel(c, base, T // 2) < 1e-7
+
+
+def test_loose_residue_heavy_quark_effect(ctx):
+    """Sec. II: at r = 1e-6 the unpreconditioned far slices drift; with the
+    cosh profile (alpha0 = 0.4) the restored correlator stays accurate."""
+    dims = (48, 4, 4, 4)
+    f = dp.dp_field_load(ctx, li.unit_links(dims), dims, -1)
+    dp.dp_field_set_csw(ctx, f, 0.0)
+    exact = oracle.free_cpp(dims, 0.5)
+    loose, _, _ = dp.dp_solve_point(ctx, f, 0.5, ("none", 0.0), (0, 0, 0, 0), 1e-6, PLAIN, T=48)
+    prec, _, _ = dp.dp_solve_point(ctx, f, 0.5, ("cosh_t", 0.4), (0, 0, 0, 0), 1e-6, PLAIN, T=48)
+    e_loose = np.abs(loose / exact - 1)[:25]
+    e_prec = np.abs(prec / exact - 1)[:25]
+    assert e_loose.max() > 1e-2
+    assert e_prec.max() < 1e-4
+    dp.dp_field_free(ctx, f)
+
+
+def test_not_converged_and_bad_arguments(ctx, inter):
+    dims, f, op = inter
+    T = dims[0]
+    o = dict(MIXED, max_iter=3)
+    with pytest.raises(dp.DpError) as e:
+        dp.dp_solve_point(ctx, f, 0.05, ("none", 0.0), (0, 0, 0, 0), 1e-12, o, T=T, allow=())
+    assert e.value.status == 3
+    cpp, _, info = dp.dp_solve_point(ctx, f, 0.05, ("none", 0.0), (0, 0, 0, 0), 1e-12, o, T=T)
+    assert info["status"] == 3 and info["iters_inner"] <= 3 * 40
+    for bad in [dict(src=(12, 0, 0, 0)), dict(r=0.0), dict(r=1.5), dict(M=float("nan"))]:
+        args = dict(M=0.5, src=(0, 0, 0, 0), r=1e-8)
+        args.update(bad)
+        with pytest.raises(dp.DpError) as e:
+            dp.dp_solve_point(ctx, f, args["M"], ("none", 0.0), args["src"], args["r"], MIXED, T=T)
+        assert e.value.status == 1
+    with pytest.raises(dp.DpError):
+        dp.dp_solve_point(ctx, f, 0.5, ("none", 0.0), (0, 0, 0, 0), 1e-8,
+                          dict(MIXED, prec="mixed_bf16"), T=T)
+
+
+def test_device_output_and_timing(ctx, inter):
+    torch = pytest.importorskip("torch")
+    dims, f, op = inter
+    T = dims[0]
+    out = torch.zeros(2 * T, dtype=torch.float64, device="cuda")
+    dp.dp_timing_enable(ctx, True)
+    dp.dp_timing_reset(ctx)
+    n0 = dp.dp_launch_count(ctx)
+    infos = dp.dp_solve_point_dev(ctx, f, [0.5, 0.8], [("cosh_t", 0.4), ("cosh_t", 0.5)],
+                                  (0, 0, 0, 0), 1e-10, out.data_ptr(), MIXED)
+    torch.cuda.synchronize()
+    launches, ms = dp.dp_timing_get(ctx, "dslash_fp32")
+    dp.dp_timing_enable(ctx, False)
+    assert launches > 0 and ms > 0
+    assert dp.dp_launch_count(ctx) - n0 > launches
+    host, _, _ = dp.dp_solve_point_multi(ctx, f, [0.5, 0.8], [("cosh_t", 0.4), ("cosh_t", 0.5)],
+                                         (0, 0, 0, 0), 1e-10, MIXED, T=T)
+    np.testing.assert_array_equal(out.cpu().numpy().reshape(2, T), host)
+    assert all(i["status"] == 0 for i in infos)

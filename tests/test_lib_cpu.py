@@ -1,0 +1,93 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry point
+the header declares, and its host-side profile/hop tables agree with the
+oracle's independent implementation.  No GPU compute is called here."""
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1006_4028_gb300 as dp
+from paper_1006_4028_gb300 import build as dpbuild
+
+
+@pytest.fixture(scope="module")
+def lib():
+    dpbuild.build()
+    return dp.load()
+
+
+def declared_functions():
+    src = open(dpbuild.INCLUDE + "/dpre.h").read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(dp_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["dp_create", "dp_destroy", "dp_last_error", "dp_field_load", "dp_field_set_csw",
+                 "dp_field_free", "dp_solve_point", "dp_submit", "dp_wait"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+KINDS = [("none", 0.0), ("exp_t", 0.4), ("cosh_t", 0.3), ("cosh_4d", 0.2)]
+
+
+@pytest.mark.parametrize("kind,alpha0", KINDS)
+@pytest.mark.parametrize("src", [(0, 0, 0, 0), (5, 3, 1, 2)])
+@pytest.mark.parametrize("bc_t", [-1, 1])
+def test_host_profile_tables_match_oracle(lib, kind, alpha0, src, bc_t):
+    dims = (16, 8, 4, 6)
+    alpha, hop = dp.dp_profile_tables(dims, bc_t, (kind, alpha0), src)
+    ref_al = oracle.profile_alpha(kind, alpha0, dims, src)
+    fwd, bwd, _ = oracle.hop_tables(ref_al, dims, bc_t)
+    for mu in range(4):
+        L = dims[mu]
+        np.testing.assert_allclose(alpha[mu, :L], ref_al[mu], rtol=1e-15, atol=0)
+        np.testing.assert_allclose(hop[mu, 0, :L], -0.5 * fwd[mu, :L], rtol=1e-14, atol=0)
+        np.testing.assert_allclose(hop[mu, 1, :L], -0.5 * bwd[mu, :L], rtol=1e-14, atol=0)
+
+
+def test_host_profile_table_kind(lib):
+    dims = (8, 4, 4, 4)
+    rng = np.random.default_rng(1)
+    tabs = [rng.uniform(0.5, 2.0, size=d) for d in dims]
+    alpha, hop = dp.dp_profile_tables(dims, -1, ("table", 0.0, tabs))
+    fwd, bwd, _ = oracle.hop_tables(tabs, dims, -1)
+    for mu in range(4):
+        np.testing.assert_allclose(alpha[mu, :dims[mu]], tabs[mu], rtol=0)
+        np.testing.assert_allclose(hop[mu, 0, :dims[mu]], -0.5 * fwd[mu, :dims[mu]], rtol=1e-15)
+
+
+@pytest.mark.parametrize("dims", [(7, 4, 4, 4), (8, 3, 4, 4), (8, 4, 4, 1), (300, 4, 4, 4)])
+def test_host_rejects_bad_geometry(lib, dims):
+    with pytest.raises(dp.DpError) as e:
+        dp.dp_profile_tables(dims, -1, ("none", 0.0))
+    assert e.value.status == 1
+
+
+def test_host_rejects_bad_profiles(lib):
+    with pytest.raises(dp.DpError):
+        dp.dp_profile_tables((8, 4, 4, 4), -1, ("exp_t", float("nan")))
+    with pytest.raises(dp.DpError):
+        dp.dp_profile_tables((8, 4, 4, 4), -1, ("table", 0.0, [np.zeros(8)] + [np.ones(4)] * 3))
+    with pytest.raises(dp.DpError):
+        dp.dp_profile_tables((8, 4, 4, 4), 0, ("none", 0.0))
+    with pytest.raises(dp.DpError):
+        dp.dp_profile_tables((8, 4, 4, 4), -1, ("none", 0.0), (8, 0, 0, 0))
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(dp.DpError) as e:
+        dp.dp_create(0)
+    assert e.value.status == 8
+    assert "device" in e.value.message
