@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark: distance-preconditioned Wilson-clover point-source solves on GB300.
+
+Workload (the interacting heavy-quark case): 48x24^3 lattice, antiperiodic
+time, synthetic SU(3) links U = exp(i eps H) with eps = 0.3 (seed 1), c_sw =
+1.7, M = 0.5, cosh profile alpha_B = 1/cosh[alpha0 (y0 - T/2)] with alpha0 =
+0.4, residue r = 1e-11.  One step = one point-source solve: the 12
+spin-colour right-hand sides batched in the multi-RHS FP32 inner BiCGStab
+inside the FP64 defect-correction loop, then odd-site reconstruction, 1/alpha
+restore and the C_PP contraction.  Each step uses a new seeded random source
+site.  Metric: solves/s (higher is better).
+
+Also reported: the dslash roofline (HBM) of the dominant kernel measured with
+CUDA events inside the timed region, the plain single-RHS FP64 GPU solver on
+the same workload, the end-to-end number through the host-buffer C-ABI call,
+the CPU oracle baseline, and the SM clocks seen during the timed region.
+
+--impl reference times the CPU oracle (the plain FP64 reference of the
+method) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "heavy-quark point-source solve 48x24^3",
+    "lattice": [48, 24, 24, 24],
+    "bc_t": -1,
+    "links": "exp(i eps H), eps=0.3, seed 1 (synthetic; CLS ensembles not available)",
+    "csw": 1.7,
+    "M": 0.5,
+    "profile": "cosh_t alpha0=0.4 (alpha_B = 1/cosh[alpha0 (y0 - T/2)])",
+    "residue": 1e-11,
+    "rhs_per_solve": 12,
+}
+DIMS = (48, 24, 24, 24)
+EPS, SEED, CSW, MASS, ALPHA0, RES = 0.3, 1, 1.7, 0.5, 0.4, 1e-11
+METRIC = "Precond. Wilson-clover solves/s & dslash HBM GB/s vs FP64 plain; p99 latency"
+UNIT = "solves/s"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample(seconds_target=15.0):
+    """Time the CPU oracle on a bounded sample of the workload: full-lattice
+    applications of (D'+M) on one RHS (the oracle BiCGStab spends its time
+    there, two per iteration).  Returns (sec_per_apply, threads, n_apply)."""
+    import lattice_inputs as li
+    import oracle
+
+    U = li.su3_links(DIMS, EPS, SEED)
+    op = oracle.WilsonClover(U, DIMS, CSW, -1)
+    psi = li.random_spinor(DIMS, 1, 5)
+    prof = ("cosh_t", ALPHA0, (0, 0, 0, 0))
+    t0 = time.perf_counter()
+    op.apply(psi, MASS, prof)
+    first = time.perf_counter() - t0
+    n = max(1, min(30, int(seconds_target / max(first, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        op.apply(psi, MASS, prof)
+    dt = (time.perf_counter() - t0) / n
+    return dt, oracle.num_threads(), n
+
+
+def oracle_iters_per_rhs():
+    """Oracle BiCGStab iterations per RHS on this workload, from the stored
+    oracle run under tests/golden (written by the oracle only)."""
+    p = os.path.join(ROOT, "tests", "golden", "cpp_48x24_M0.5_cosh0.4.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        it = d.get("oracle_iters")
+        if it:
+            return float(np.mean(it)), "tests/golden oracle run (tol %g)" % d.get("tol", 0)
+    return None, None
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    iters, src = oracle_iters_per_rhs()
+    if iters is None:
+        iters, src = 100.0, "assumed 100 iterations per RHS (no stored oracle run)"
+    # warm-up (also builds the clover matrices)
+    import lattice_inputs as li
+
+    U = li.su3_links(DIMS, EPS, SEED)
+    op = oracle.WilsonClover(U, DIMS, CSW, -1)
+    psi = li.random_spinor(DIMS, 1, 5)
+    prof = ("cosh_t", ALPHA0, (0, 0, 0, 0))
+    for _ in range(args.warmup):
+        op.apply(psi, MASS, prof)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        op.apply(psi, MASS, prof)
+    dt = (time.perf_counter() - t0) / args.steps
+    per_solve = dt * 2 * iters * 12
+    value = 1.0 / per_solve
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": dict(WORKLOAD),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": "one full-lattice (D'+M) application on 1 RHS per step; "
+                                   "a solve = 12 RHS x 2 applications x %.0f BiCGStab "
+                                   "iterations (%s)" % (iters, src)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-plain", action="store_true")
+    ap.add_argument("--graphs", type=int, default=0,
+                    help="capture solver iterations as CUDA graphs in the timed region "
+                         "(per-kernel event timing needs them off)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    ws, rank, local = dist_env()
+    import torch
+
+    import lattice_inputs as li
+    import paper_1006_4028_gb300 as dp
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl")
+        pg = tdist
+    dp.load()
+    stream = torch.cuda.current_stream()
+    ctx = dp.dp_create(local, stream.cuda_stream)
+    U = li.su3_links(DIMS, EPS, SEED)
+    field = dp.dp_field_load(ctx, U, DIMS, -1)
+    dp.dp_field_set_csw(ctx, field, CSW)
+    del U
+    T, V = DIMS[0], int(np.prod(DIMS))
+    opts = {"prec": "mixed_fp32", "compress12": 1, "batched": 1, "use_graph": args.graphs}
+    prof = ("cosh_t", ALPHA0)
+    rng = np.random.default_rng(1000 + rank)
+
+    def rand_src():
+        return tuple(int(rng.integers(0, d)) for d in DIMS)
+
+    # tune the launch shapes of the dslash for this volume and batch
+    tuned = {}
+    for prec, c12 in (("mixed_fp32", 1), ("fp64", 0)):
+        for nr in (12, 1):
+            tuned["%s_n%d" % (prec, nr)] = dp.dp_autotune(ctx, field, prec, c12, nr)
+
+    cpp_dev = torch.zeros(T, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        dp.dp_solve_point_dev(ctx, field, [MASS], [prof], rand_src(), RES, cpp_dev.data_ptr(), opts)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, inputs resident in HBM ----
+    dp.dp_timing_reset(ctx)
+    dp.dp_timing_enable(ctx, True)
+    clk = Clocks(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    n0 = dp.dp_launch_count(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        infos += dp.dp_solve_point_dev(ctx, field, [MASS], [prof], rand_src(), RES,
+                                       cpp_dev.data_ptr(), opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = clk.stop()
+    launches = dp.dp_launch_count(ctx) - n0
+    ms = e0.elapsed_time(e1)
+    d32_n, d32_ms = dp.dp_timing_get(ctx, "dslash_fp32")
+    d64_n, d64_ms = dp.dp_timing_get(ctx, "dslash_fp64")
+    dp.dp_timing_enable(ctx, False)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    total = args.steps * ws
+    value = total / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (multi-RHS FP32 dslash) ----
+    Vh = V // 2
+    n = 12
+    # algorithmic bytes per half-site: spinor in/out n*(24+24)*4, 8 links of
+    # 12 FP32 reals, the FP32 clover inverse (72 reals); the second Schur
+    # launch also reads x (n*24*4): average of the two launch kinds
+    b_ainv = n * 48 * 4 + 8 * 12 * 4 + 72 * 4
+    b_xmy = b_ainv + n * 24 * 4
+    bytes_per_launch = Vh * (b_ainv + b_xmy) / 2
+    avg_ms = d32_ms / max(d32_n, 1)
+    hbm_peak, peak_src = peaks()
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    # cross-check: the same kernel with all 12 RHS active, timed in isolation
+    buf_in = torch.zeros(dp.dp_spinor_bytes(ctx, field, "mixed_fp32", 12) // 4, dtype=torch.float32,
+                         device="cuda")
+    buf_in.normal_()
+    buf_out = torch.empty_like(buf_in)
+    iso_ms = dp.dp_dslash_dev(ctx, field, MASS, prof, "mixed_fp32", 1, 0, buf_in.data_ptr(),
+                              buf_out.data_ptr(), 12, 0, 0, 20)
+    del buf_in, buf_out
+    iso_gbs = Vh * b_ainv / (iso_ms / 1e3) / 1e9
+
+    # ---- end to end: host-buffer C-ABI call per solve (wall clock) ----
+    e2e_steps = max(3, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cpp_h = None
+    for _ in range(e2e_steps):
+        cpp_h, _, info_h = dp.dp_solve_point(ctx, field, MASS, prof, rand_src(), RES, opts, T=T)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    Lm = max(DIMS)
+    h2d = 4 * Lm * 8 + 8 * Lm * 8 + 8 * Lm * 4 + 4 + 12 * 40 + 12 * 88 + 12 * 4
+    d2h = T * 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer",
+        "data": "synthetic",
+        "config": dict(WORKLOAD, parallelism="replicas" if ws > 1 else "single",
+                       l2="working set ~%.1f GB >> 129 MB L2 (no flush needed)"
+                          % (dp.dp_device_bytes(ctx) / 1e9),
+                       solver="BiCGStab FP32 inner (12-real links) in FP64 defect correction",
+                       graphs=bool(args.graphs), tuned_launch=tuned),
+        "gpu_launches": launches,
+        "iterations": {"inner_mean": float(np.mean([i["iters_inner"] for i in infos])),
+                       "outer_mean": float(np.mean([i["iters_outer"] for i in infos])),
+                       "true_rel_residue_max": float(max(i["true_rel_residue"] for i in infos))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "kernel": "dslash_fp32 (12 RHS, 12-real links, fused A^-1 epilogue)",
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+                     "launches": d32_n, "peak_source": peak_src,
+                     "isolated_all_active": {"avg_launch_ms": iso_ms, "achieved": iso_gbs,
+                                             "frac": iso_gbs / hbm_peak}},
+        "kernel_time_share": {"dslash_fp32": d32_ms / ms, "dslash_fp64": d64_ms / ms},
+        "clocks": clocks,
+        "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "note": "dp_solve_point with host buffers; request parameters and profile "
+                        "tables up, C_PP down"},
+    }
+
+    if rank == 0 and not args.no_fp64_plain:
+        o64 = {"prec": "fp64", "batched": 0, "use_graph": 0}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, i64 = dp.dp_solve_point(ctx, field, MASS, prof, rand_src(), RES, o64, T=T)
+        s64 = time.perf_counter() - t0
+        line["fp64_plain"] = {"solves_per_s": 1.0 / s64, "ms_per_solve": s64 * 1e3,
+                              "iters_inner": i64["iters_inner"],
+                              "speedup_of_value": value / ws * s64}
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, thr, napp = cpu_sample()
+        iters, src = oracle_iters_per_rhs()
+        if iters is None:
+            iters, src = 100.0, "assumed 100 iterations per RHS (no stored oracle run)"
+        line["cpu_baseline"] = {
+            "value": 1.0 / (dt * 2 * iters * 12), "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": "%d full-lattice (D'+M) applications on 1 RHS (%.2f s each); a solve = "
+                      "12 RHS x 2 applications x %.0f BiCGStab iterations (%s)"
+                      % (napp, dt, iters, src)}
+    # parity of one solve at the origin source against the stored oracle result
+    gold = os.path.join(ROOT, "tests", "golden", "cpp_48x24_M0.5_cosh0.4.json")
+    if rank == 0 and os.path.exists(gold):
+        g = json.load(open(gold))
+        c, _, _ = dp.dp_solve_point(ctx, field, MASS, prof, (0, 0, 0, 0), RES, opts, T=T)
+        ref = np.asarray(g["cpp"])
+        line["per_slice_rel_err_vs_oracle_max"] = float(np.max(np.abs(c[:T // 2 + 1] /
+                                                                      ref[:T // 2 + 1] - 1)))
+    dp.dp_field_free(ctx, field)
+    dp.dp_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

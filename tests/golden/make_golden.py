@@ -1,0 +1,50 @@
+"""Write stored oracle results used by the GPU tests and the benchmark.
+
+Calls only the CPU oracle (and the seeded input generators).  Each output is
+a JSON file in this directory with the inputs that produced it.
+
+  cpp_48x24_M0.5_cosh0.4.json : C_PP(y0) of the point source at the origin on
+      the 48x24^3 heavy-quark workload (eps = 0.3, seed 1, c_sw = 1.7,
+      antiperiodic time, M = 0.5, cosh profile alpha0 = 0.4), solved by the
+      oracle's full-lattice FP64 BiCGStab to relative residue 1e-13, restored
+      (Sec. II eq. backcorrection), plus the oracle's iteration counts.
+
+Run:  python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import lattice_inputs as li  # noqa: E402
+import oracle  # noqa: E402
+
+
+def heavy_48x24():
+    dims = (48, 24, 24, 24)
+    eps, seed, csw, M, alpha0, tol = 0.3, 1, 1.7, 0.5, 0.4, 1e-13
+    t0 = time.time()
+    U = li.su3_links(dims, eps, seed)
+    op = oracle.WilsonClover(U, dims, csw, -1)
+    cpp, _, info = oracle.solve_point(op, M, "cosh_t", alpha0, (0, 0, 0, 0), tol=tol)
+    out = {
+        "what": "oracle C_PP(y0), point source at the origin, restored",
+        "dims": list(dims), "eps": eps, "seed": seed, "csw": csw, "bc_t": -1, "M": M,
+        "profile": "cosh_t", "alpha0": alpha0, "src": [0, 0, 0, 0], "tol": tol,
+        "cpp": [float(v) for v in cpp],
+        "oracle_iters": [int(v) for v in info["iters"]],
+        "oracle_relres": [float(v) for v in info["relres"]],
+        "converged": bool(info["converged"]),
+        "oracle_threads": oracle.num_threads(),
+        "seconds": time.time() - t0,
+    }
+    with open(os.path.join(HERE, "cpp_48x24_M0.5_cosh0.4.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
+if __name__ == "__main__":
+    heavy_48x24()

@@ -104,8 +104,11 @@ def test_periodic_time_and_many_rhs(ctx):
 def test_invalid_arguments_are_errors(ctx):
     dims = (4, 4, 4, 4)
     U = li.unit_links(dims)
+    with pytest.raises(dp.DpError) as e:  # odd extent: no even-odd split
+        dp.dp_field_load(ctx, li.unit_links((4, 3, 4, 4)), (4, 3, 4, 4), -1)
+    assert e.value.status == 1
     with pytest.raises(dp.DpError) as e:
-        dp.dp_field_load(ctx, U, (4, 3, 4, 4), -1)
+        dp.dp_field_load(ctx, U, dims, 0)
     assert e.value.status == 1
     bad = U.copy()
     bad[0, 0, 0, 0, 0, 0, 0] = np.nan
