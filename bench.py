@@ -199,11 +199,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
+    ap.add_argument("--dims", default=None,
+                    help="T,Lx,Ly,Lz of a smaller lattice for profiling runs (not the headline)")
     ap.add_argument("--graphs", type=int, default=0,
                     help="capture solver iterations as CUDA graphs in the timed region "
                          "(per-kernel event timing needs them off)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.dims:
+        global DIMS
+        DIMS = tuple(int(v) for v in args.dims.split(","))
+        WORKLOAD["lattice"] = list(DIMS)
+        WORKLOAD["workload"] = "heavy-quark point-source solve %dx%d^3 (profiling size)" % (
+            DIMS[0], DIMS[1])
+        args.no_cpu_baseline = True
     if args.impl == "reference":
         return run_reference(args)
 
@@ -364,7 +373,7 @@ def main():
                       % (napp, dt, iters, src)}
     # parity of one solve at the origin source against the stored oracle result
     gold = os.path.join(ROOT, "tests", "golden", "cpp_48x24_M0.5_cosh0.4.json")
-    if rank == 0 and os.path.exists(gold):
+    if rank == 0 and os.path.exists(gold) and DIMS == (48, 24, 24, 24):
         g = json.load(open(gold))
         c, _, _ = dp.dp_solve_point(ctx, field, MASS, prof, (0, 0, 0, 0), RES, opts, T=T)
         ref = np.asarray(g["cpp"])

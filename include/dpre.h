@@ -186,6 +186,21 @@ dp_status dp_solve_point_dev(dp_ctx *ctx, dp_field field, int n_mass, const doub
                              const dp_solve_opts *opts, double *cpp_out_dev,
                              dp_solve_info *info);
 
+/* Restore and contract a preconditioned propagator already on the device
+ * (Sec. II eq. backcorrection; Sec. III, restore before contracting):
+ * S = S'/alpha_B per site, C_PP(y0) = -sum_{y vec} sum |S|^2 with
+ * y0 = (t - src_t) mod T.  xe/xo: device FP64 S' of the even/odd sites in the
+ * packed layout [12 components][V/2 sites][n_groups*12 RHS] of complex128
+ * (site s of parity p is the half index i>>1 of a site with (t+x+y+z)&1 = p);
+ * RHS 12g..12g+11 belong to group g, whose profile and source are
+ * profiles[g] and src[4g..4g+3].  cpp_dev: device [n_groups][T].  Device
+ * scratch (tables and per-slice partial sums, a few hundred KB) comes from the
+ * context allocator.  Runs on the context stream; returns after the stream
+ * work is queued. */
+dp_status dp_restore_contract_dev(dp_ctx *ctx, dp_field field, int n_groups,
+                                  const dp_profile *profiles, const int *src, const double *xe,
+                                  const double *xo, double *cpp_dev);
+
 /* ---- operator application (host buffers; for checks and small jobs) ----- */
 
 typedef enum {

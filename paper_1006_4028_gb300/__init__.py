@@ -116,6 +116,7 @@ def load(build_if_missing=False):
         "dp_solve_point_dev": ([vp, up, ip, vp, vp, P(C.c_int * 4), dp, P(SolveOpts), vp, vp], ip),
         "dp_apply": ([vp, up, ip, dp, P(Profile), P(C.c_int * 4), ip, ip, vp, vp, ip], ip),
         "dp_profile_tables": ([P(C.c_int * 4), ip, P(Profile), P(C.c_int * 4), vp, vp], ip),
+        "dp_restore_contract_dev": ([vp, up, ip, vp, vp, vp, vp, vp], ip),
         "dp_spinor_bytes": ([vp, up, ip, ip], sz),
         "dp_dslash_dev": ([vp, up, dp, P(Profile), ip, ip, ip, vp, vp, ip, ip, ip, ip,
                            P(C.c_float)], ip),
@@ -311,6 +312,47 @@ def dp_profile_tables(dims, bc_t, profile, src=(0, 0, 0, 0)):
     _check(load().dp_profile_tables(C.byref(_i4(dims)), int(bc_t), C.byref(pr), C.byref(_i4(src)),
                                     _ptr(alpha), _ptr(hop)))
     return alpha, hop
+
+
+def pack_half_spinors(S, dims):
+    """Host marshalling of lexicographic spinors S (n, T, Lz, Ly, Lx, 4, 3) into
+    the packed even/odd device layout [12][V/2][n] (complex128): returns
+    (even, odd) numpy arrays of shape (12, V/2, n)."""
+    T, Lx, Ly, Lz = (int(d) for d in dims)
+    S = np.asarray(S, dtype=np.complex128)
+    n = S.shape[0]
+    flat = S.reshape(n, T * Lz * Ly * Lx, 12)
+    t, z, y, x = np.indices((T, Lz, Ly, Lx)).reshape(4, -1)
+    par = (t + x + y + z) & 1
+    idx = np.arange(T * Lz * Ly * Lx)
+    out = []
+    for p in (0, 1):
+        sel = idx[par == p]
+        half = sel >> 1
+        a = np.zeros((12, T * Lx * Ly * Lz // 2, n), np.complex128)
+        a[:, half, :] = flat[:, sel, :].transpose(2, 1, 0)
+        out.append(a)
+    return out[0], out[1]
+
+
+def _groups(profiles, srcs):
+    n = len(profiles)
+    profs = (Profile * n)()
+    keep = []
+    for k, p in enumerate(profiles):
+        pr, kp = _profile(p)
+        profs[k] = pr
+        keep += kp
+    s = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32).reshape(n, 4))
+    return n, profs, s, keep
+
+
+def dp_restore_contract_dev(ctx, field, profiles, srcs, xe_ptr, xo_ptr, cpp_ptr):
+    """Restore and contract device S' halves (packed layout) into device C_PP."""
+    n, profs, s, keep = _groups(profiles, srcs)
+    _check(load().dp_restore_contract_dev(ctx, int(field), n, C.cast(profs, C.c_void_p), _ptr(s),
+                                          C.c_void_p(int(xe_ptr)), C.c_void_p(int(xo_ptr)),
+                                          C.c_void_p(int(cpp_ptr))))
 
 
 def dp_spinor_bytes(ctx, field, prec, nrhs):

@@ -795,6 +795,83 @@ dp_status dp_timing_get(dp_ctx *ctx, const char *name, long *launches, double *t
 
 long dp_launch_count(dp_ctx *ctx) { return ctx ? ctx->c.launches.load() : 0; }
 
+dp_status dp_restore_contract_dev(dp_ctx *ctx, dp_field field, int n_groups,
+                                  const dp_profile *profiles, const int *src, const double *xe,
+                                  const double *xo, double *cpp_dev)
+{
+    CTX_CHECK(ctx);
+    Ctx &c = ctx->c;
+    auto fp = find_field(&c, field);
+    if (!fp) {
+        set_error("unknown field");
+        return DP_ERR_NOT_FOUND;
+    }
+    if (n_groups < 1 || n_groups > kMaxGroups || 12 * n_groups > kMaxRhs || !profiles || !src ||
+        !xe || !xo || !cpp_dev) {
+        set_error("dp_restore_contract_dev: invalid argument (n_groups in [1, %d])", kMaxRhs / 12);
+        return DP_ERR_INVALID_ARG;
+    }
+    const Geom &g = fp->g;
+    const int Lm = g.Lmax, n = 12 * n_groups;
+    const int L[4] = {g.T, g.Lx, g.Ly, g.Lz};
+    std::vector<double> alpha((size_t)n_groups * 4 * Lm), hop(8 * Lm);
+    std::vector<SlotInfo> slots(n);
+    std::vector<int> tsrc(n_groups);
+    for (int k = 0; k < n_groups; k++) {
+        for (int mu = 0; mu < 4; mu++)
+            if (src[4 * k + mu] < 0 || src[4 * k + mu] >= L[mu]) {
+                set_error("source coordinate out of range");
+                return DP_ERR_INVALID_ARG;
+            }
+        dp_status s = profile_tables(profiles[k], g, fp->bc_t, src + 4 * k,
+                                     &alpha[(size_t)k * 4 * Lm], hop.data());
+        if (s != DP_OK) return s;
+        tsrc[k] = src[4 * k];
+        for (int j = 0; j < 12; j++) {
+            SlotInfo &sl = slots[12 * k + j];
+            sl.group = k;
+            sl.comp = j;
+            sl.t = src[4 * k];
+            sl.x = src[4 * k + 1];
+            sl.y = src[4 * k + 2];
+            sl.z = src[4 * k + 3];
+            sl.scale = 1.0;
+        }
+    }
+    const size_t npart = (size_t)g.T * contract_blocks_per_slice(g) * n_groups;
+    double *alpha_d = (double *)c.alloc(alpha.size() * sizeof(double));
+    SlotInfo *slots_d = (SlotInfo *)c.alloc(sizeof(SlotInfo) * n);
+    int *tsrc_d = (int *)c.alloc(sizeof(int) * n_groups);
+    double *part = (double *)c.alloc(npart * sizeof(double));
+    dp_status ret = DP_OK;
+    if (!alpha_d || !slots_d || !tsrc_d || !part) {
+        set_error("out of device memory (restore/contract scratch)");
+        ret = DP_ERR_OOM;
+    } else {
+        cudaError_t e = cudaMemcpyAsync(alpha_d, alpha.data(), alpha.size() * sizeof(double),
+                                        cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(slots_d, slots.data(), sizeof(SlotInfo) * n, cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tsrc_d, tsrc.data(), sizeof(int) * n_groups, cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess)
+            e = launch_restore_contract((const double2 *)xe, (const double2 *)xo, g, n, alpha_d, slots_d,
+                                        n_groups, tsrc_d, nullptr, cpp_dev, part, nullptr, c.stream);
+        // the host tables are pageable: make sure the copies are done before they go
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+        if (e != cudaSuccess) {
+            set_error("restore/contract: %s", cudaGetErrorString(e));
+            ret = DP_ERR_CUDA;
+        }
+        c.launches += 2;
+    }
+    c.release(alpha_d);
+    c.release(slots_d);
+    c.release(tsrc_d);
+    c.release(part);
+    return ret;
+}
+
 dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profile,
                             const int src[4], double *alpha_out, double *hop_out)
 {

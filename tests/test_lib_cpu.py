@@ -83,6 +83,27 @@ def test_host_rejects_bad_profiles(lib):
         dp.dp_profile_tables((8, 4, 4, 4), -1, ("none", 0.0), (8, 0, 0, 0))
 
 
+def test_pack_half_spinors_layout():
+    """Host marshalling into the packed even/odd layout [12][V/2][n]."""
+    import lattice_inputs as li
+
+    dims = (4, 2, 4, 2)
+    S = li.random_spinor(dims, 3, 1)
+    ev, od = dp.pack_half_spinors(S, dims)
+    T, Lx, Ly, Lz = dims
+    seen = 0
+    for t in range(T):
+        for z in range(Lz):
+            for y in range(Ly):
+                for x in range(Lx):
+                    i = ((t * Lz + z) * Ly + y) * Lx + x
+                    half = ev if (t + x + y + z) % 2 == 0 else od
+                    np.testing.assert_array_equal(half[:, i >> 1, :],
+                                                  S[:, t, z, y, x].reshape(3, 12).T)
+                    seen += 1
+    assert seen == 64 and ev.shape == (12, 32, 3)
+
+
 def test_create_without_gpu_fails_cleanly(lib):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
