@@ -201,6 +201,32 @@ dp_status dp_restore_contract_dev(dp_ctx *ctx, dp_field field, int n_groups,
                                   const dp_profile *profiles, const int *src, const double *xe,
                                   const double *xo, double *cpp_dev);
 
+/* The same restore and contraction as dp_restore_contract_dev, for callers
+ * that must not allocate device memory: an application whose own allocator
+ * already holds the free device memory (a cudaMalloc from the library would
+ * fail or fragment it), or a latency-bound loop that cannot afford an
+ * allocation or an out-of-memory failure in the middle of a run.  The paper
+ * has no counterpart; it is an interface choice of this library.
+ *
+ * The device scratch is one fixed array inside the library (about 1.1 MB on
+ * every GPU that loads the library, held until the process exits): profile
+ * tables, slot descriptors and the per-slice partial sums, sized for T <= 256,
+ * up to 64 partial sums per time slice (always the case for extents <= 256)
+ * and n_groups <= 5.  Larger requests return DP_ERR_INVALID_ARG.  No
+ * cudaMalloc, cudaFree or other allocating call is made.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and keeps it; make that first call before any stream
+ * capture.  Every call shares the one array and it keeps the last call's
+ * contents (nothing needs clearing: each value read is written earlier in the
+ * same call).  Calls that overlap on the GPU (other threads, other contexts on
+ * the same device) race on the array: serialise them.  Arguments, layouts and
+ * results are those of dp_restore_contract_dev; the call returns after its
+ * work on the context stream has finished. */
+dp_status dp_restore_contract_noalloc(dp_ctx *ctx, dp_field field, int n_groups,
+                                      const dp_profile *profiles, const int *src, const double *xe,
+                                      const double *xo, double *cpp_dev);
+
 /* ---- operator application (host buffers; for checks and small jobs) ----- */
 
 typedef enum {

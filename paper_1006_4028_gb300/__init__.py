@@ -117,6 +117,7 @@ def load(build_if_missing=False):
         "dp_apply": ([vp, up, ip, dp, P(Profile), P(C.c_int * 4), ip, ip, vp, vp, ip], ip),
         "dp_profile_tables": ([P(C.c_int * 4), ip, P(Profile), P(C.c_int * 4), vp, vp], ip),
         "dp_restore_contract_dev": ([vp, up, ip, vp, vp, vp, vp, vp], ip),
+        "dp_restore_contract_noalloc": ([vp, up, ip, vp, vp, vp, vp, vp], ip),
         "dp_spinor_bytes": ([vp, up, ip, ip], sz),
         "dp_dslash_dev": ([vp, up, dp, P(Profile), ip, ip, ip, vp, vp, ip, ip, ip, ip,
                            P(C.c_float)], ip),
@@ -353,6 +354,15 @@ def dp_restore_contract_dev(ctx, field, profiles, srcs, xe_ptr, xo_ptr, cpp_ptr)
     _check(load().dp_restore_contract_dev(ctx, int(field), n, C.cast(profs, C.c_void_p), _ptr(s),
                                           C.c_void_p(int(xe_ptr)), C.c_void_p(int(xo_ptr)),
                                           C.c_void_p(int(cpp_ptr))))
+
+
+def dp_restore_contract_noalloc(ctx, field, profiles, srcs, xe_ptr, xo_ptr, cpp_ptr):
+    """As dp_restore_contract_dev, with the device scratch in a fixed array
+    inside the library: no device memory is allocated (see the header)."""
+    n, profs, s, keep = _groups(profiles, srcs)
+    _check(load().dp_restore_contract_noalloc(ctx, int(field), n, C.cast(profs, C.c_void_p),
+                                              _ptr(s), C.c_void_p(int(xe_ptr)),
+                                              C.c_void_p(int(xo_ptr)), C.c_void_p(int(cpp_ptr))))
 
 
 def dp_spinor_bytes(ctx, field, prec, nrhs):

@@ -277,4 +277,160 @@ cudaError_t launch_cpp_commit(const double *src, double *dst, int T, int accumul
     return cudaGetLastError();
 }
 
+// ---- allocation-free restore and contract -----------------------------------
+//
+// dp_restore_contract_noalloc runs the same two kernels as
+// dp_restore_contract_dev, but its device scratch (profile tables, slot
+// descriptors and the per-slice partial sums) lives in one file-scope device
+// array instead of memory from the context allocator.  Layout of the array
+// (256-byte aligned regions):
+//   partials  kNaMaxT * kNaMaxP * kNaMaxGroups doubles   (1 MiB)
+//   alpha     kNaMaxGroups * 4 * kMaxL doubles            (64 KiB)
+//   slots     kMaxRhs SlotInfo
+//   t_src     kNaMaxGroups ints
+constexpr int kNaMaxT = kMaxL;
+constexpr int kNaMaxP = 64;
+constexpr int kNaMaxGroups = kMaxGroups;
+constexpr size_t kNaAlign = 256;
+constexpr size_t na_round(size_t b) { return (b + kNaAlign - 1) / kNaAlign * kNaAlign; }
+constexpr size_t kNaPartOff = 0;
+constexpr size_t kNaAlphaOff = kNaPartOff + na_round(sizeof(double) * kNaMaxT * kNaMaxP * kNaMaxGroups);
+constexpr size_t kNaSlotOff = kNaAlphaOff + na_round(sizeof(double) * kNaMaxGroups * 4 * kMaxL);
+constexpr size_t kNaTsrcOff = kNaSlotOff + na_round(sizeof(SlotInfo) * kMaxRhs);
+constexpr size_t kNaBytes = kNaTsrcOff + na_round(sizeof(int) * kNaMaxGroups);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+size_t noalloc_scratch_bytes() { return kNaBytes; }
+
 }  // namespace dp
+
+#include <mutex>
+
+#include "ctx.h"
+
+namespace {
+// Device address of g_noalloc_scratch per device.  In host code the array's
+// name only stands in for the symbol; the address a kernel may use is looked
+// up once per device with that device current.
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mu;
+void *g_na_addr[kNaMaxDevices] = {};
+
+dp_status noalloc_scratch_address(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kNaMaxDevices) {
+        dp::set_error("device index %d beyond the %d supported", device, kNaMaxDevices);
+        return DP_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, dp::g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            dp::set_error("cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+            return DP_ERR_CUDA;
+        }
+        g_na_addr[device] = p;
+    }
+    *out = static_cast<unsigned char *>(g_na_addr[device]);
+    return DP_OK;
+}
+}  // namespace
+
+extern "C" dp_status dp_restore_contract_noalloc(dp_ctx *ctx, dp_field field, int n_groups,
+                                                 const dp_profile *profiles, const int *src,
+                                                 const double *xe, const double *xo,
+                                                 double *cpp_dev)
+{
+    using namespace dp;
+    if (!ctx) {
+        set_error("null context");
+        return DP_ERR_INVALID_ARG;
+    }
+    Ctx &c = ctx->c;
+    if (cudaSetDevice(c.device) != cudaSuccess) {
+        set_error("cudaSetDevice(%d) failed", c.device);
+        return DP_ERR_CUDA;
+    }
+    auto fp = find_field(&c, field);
+    if (!fp) {
+        set_error("unknown field");
+        return DP_ERR_NOT_FOUND;
+    }
+    if (n_groups < 1 || 12 * n_groups > kMaxRhs || n_groups > kNaMaxGroups || !profiles || !src ||
+        !xe || !xo || !cpp_dev) {
+        set_error("dp_restore_contract_noalloc: invalid argument (n_groups in [1, %d])", kMaxRhs / 12);
+        return DP_ERR_INVALID_ARG;
+    }
+    const Geom &g = fp->g;
+    const int P = contract_blocks_per_slice(g);
+    if (g.T > kNaMaxT || P > kNaMaxP || g.Lmax > kMaxL) {
+        set_error("lattice beyond the fixed scratch of dp_restore_contract_noalloc "
+                  "(T <= %d, %d partial sums per slice, extents <= %d)", kNaMaxT, kNaMaxP, kMaxL);
+        return DP_ERR_INVALID_ARG;
+    }
+    unsigned char *base = nullptr;
+    dp_status s = noalloc_scratch_address(c.device, &base);
+    if (s != DP_OK) return s;
+    // host-side tables in fixed-size stack arrays (about 82 KiB): no heap use
+    double alpha[kNaMaxGroups * 4 * kMaxL];
+    double hop[8 * kMaxL];
+    SlotInfo slots[kMaxRhs];
+    int tsrc[kNaMaxGroups] = {};
+    const int Lm = g.Lmax, n = 12 * n_groups;
+    const int L[4] = {g.T, g.Lx, g.Ly, g.Lz};
+    for (int k = 0; k < n_groups; k++) {
+        for (int mu = 0; mu < 4; mu++)
+            if (src[4 * k + mu] < 0 || src[4 * k + mu] >= L[mu]) {
+                set_error("source coordinate out of range");
+                return DP_ERR_INVALID_ARG;
+            }
+        s = profile_tables(profiles[k], g, fp->bc_t, src + 4 * k, alpha + (size_t)k * 4 * Lm, hop);
+        if (s != DP_OK) return s;
+        tsrc[k] = src[4 * k];
+        for (int j = 0; j < 12; j++) {
+            SlotInfo &sl = slots[12 * k + j];
+            sl.group = k;
+            sl.comp = j;
+            sl.t = src[4 * k];
+            sl.x = src[4 * k + 1];
+            sl.y = src[4 * k + 2];
+            sl.z = src[4 * k + 3];
+            sl.scale = 1.0;
+        }
+    }
+    double *part_d = reinterpret_cast<double *>(base + kNaPartOff);
+    double *alpha_d = reinterpret_cast<double *>(base + kNaAlphaOff);
+    SlotInfo *slots_d = reinterpret_cast<SlotInfo *>(base + kNaSlotOff);
+    int *tsrc_d = reinterpret_cast<int *>(base + kNaTsrcOff);
+    // every partial sum the final kernel reads is written earlier in the same
+    // call, so nothing in the shared array has to be cleared first
+    cudaError_t e = cudaMemcpyAsync(alpha_d, alpha, sizeof(double) * n_groups * 4 * Lm,
+                                    cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(slots_d, slots, sizeof(SlotInfo) * n, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tsrc_d, tsrc, sizeof(int) * n_groups, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) {
+        dim3 grid(P, g.T);
+        k_contract<<<grid, kContractBlock, 0, c.stream>>>((const double2 *)xe, (const double2 *)xo, g, n,
+                                                          alpha_d, slots_d, nullptr, n_groups, part_d,
+                                                          nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const int tot = g.T * n_groups;
+        k_contract_final<<<(tot + 127) / 128, 128, 0, c.stream>>>(part_d, P, g.T, n_groups, tsrc_d, cpp_dev);
+        e = cudaGetLastError();
+    }
+    // the host tables live on this stack frame: wait for the copies (and the
+    // kernels) before returning
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) {
+        set_error("restore/contract (no-alloc): %s", cudaGetErrorString(e));
+        return DP_ERR_CUDA;
+    }
+    c.launches += 2;
+    return DP_OK;
+}
