@@ -261,9 +261,12 @@ dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profi
  * right-hand sides: layout [chunk][V/2][nrhs] with chunk = float4 (6 per
  * spinor, FP32) or double2 (12, FP64).  `in`/`out` are device pointers the
  * caller allocated with dp_spinor_bytes().  Launch shape from the tuner
- * unless block_threads > 0.  iters launches back to back; if ms_out is
- * non-NULL it receives the average launch time measured with CUDA events on
- * the context stream. */
+ * unless given: block_threads > 0 sets the block; rhs_per_thread 1-4 selects
+ * the register kernel with that many RHS per thread (2-4: FP32 only, nrhs a
+ * multiple and 12 divisible by it), -1 the shared-memory staged kernel (FP32,
+ * 12-real links, nrhs dividing 96), 0 the tuned or default shape.  iters
+ * launches back to back; if ms_out is non-NULL it receives the average launch
+ * time measured with CUDA events on the context stream. */
 size_t dp_spinor_bytes(dp_ctx *ctx, dp_field field, int prec, int nrhs);
 dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
                         int prec, int compress12, int out_parity, const void *in, void *out,
@@ -272,9 +275,11 @@ dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile 
 
 /* ---- autotuner ----------------------------------------------------------- */
 
-/* Time candidate launch shapes (threads per block, RHS per thread) of the
- * multi-RHS dslash for this field, precision and nrhs, and keep the fastest
- * for later launches.  best_* may be NULL. */
+/* Time candidate launch shapes of the multi-RHS dslash for this field,
+ * precision and nrhs (register kernel: 64-256 threads per block x 1-4 RHS per
+ * thread; shared-memory staged kernel), and keep the fastest for the solver's
+ * later launches.  best_rhs_per_thread returns -1 for the staged kernel.
+ * best_* may be NULL. */
 dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int nrhs,
                       int *best_block_threads, int *best_rhs_per_thread, float *best_ms);
 

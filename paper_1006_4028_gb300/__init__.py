@@ -336,6 +336,21 @@ def pack_half_spinors(S, dims):
     return out[0], out[1]
 
 
+def unpack_half_spinors(even, odd, dims):
+    """Inverse of pack_half_spinors: (12, V/2, n) halves -> (n, T, Lz, Ly, Lx, 4, 3)."""
+    T, Lx, Ly, Lz = (int(d) for d in dims)
+    n = even.shape[2]
+    V = T * Lz * Ly * Lx
+    t, z, y, x = np.indices((T, Lz, Ly, Lx)).reshape(4, -1)
+    par = (t + x + y + z) & 1
+    idx = np.arange(V)
+    flat = np.zeros((n, V, 12), np.complex128)
+    for p, half in ((0, even), (1, odd)):
+        sel = idx[par == p]
+        flat[:, sel, :] = np.asarray(half)[:, sel >> 1, :].transpose(2, 1, 0)
+    return flat.reshape(n, T, Lz, Ly, Lx, 4, 3)
+
+
 def _groups(profiles, srcs):
     n = len(profiles)
     profs = (Profile * n)()

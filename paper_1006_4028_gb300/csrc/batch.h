@@ -35,6 +35,7 @@ struct Op {
     int8_t grp_of[kMaxRhs] = {};
     int nrhs = 0;
     int block = 128;
+    int rpt = 1;  // RHS per thread of the Schur launches
 };
 
 struct InnerVecs {
@@ -44,7 +45,10 @@ struct InnerVecs {
 
 class Batch {
   public:
-    Batch(Ctx *c, std::shared_ptr<Field> f, int nslots, const dp_solve_opts &o, int round_cap);
+    // schur_parity: the parity p whose Schur system is solved; a job whose
+    // source sits on parity p needs no dslash to set up its right-hand side
+    Batch(Ctx *c, std::shared_ptr<Field> f, int nslots, const dp_solve_opts &o, int round_cap,
+          int schur_parity = 0);
     ~Batch();
     Batch(const Batch &) = delete;
     Batch &operator=(const Batch &) = delete;
@@ -72,11 +76,13 @@ class Batch {
     int n;
     dp_solve_opts opts;
     int round_iters;
+    int sp = 0;
     int mixed = 1, ipr = 1, ilf = LINK_F32_12;
     int check_every = 4;
     size_t v64 = 0, vin = 0, total_bytes = 0;
     std::vector<void *> owned;
-    double2 *bh = nullptr, *x = nullptr, *r64 = nullptr, *y64 = nullptr, *to64 = nullptr;
+    double2 *bh = nullptr, *x = nullptr, *r64 = nullptr, *y64 = nullptr, *to64 = nullptr,
+            *t64 = nullptr;
     InnerVecs in;
     RhsState *outer = nullptr, *inner = nullptr;
     double *alpha_d = nullptr, *hop64_d = nullptr;

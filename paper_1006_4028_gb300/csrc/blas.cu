@@ -10,6 +10,10 @@
 // block partials in a fixed order and applies the scalar recurrences (alpha,
 // omega, rho, beta) per RHS on the device, so the iteration loop needs no
 // host round trip.  Per-RHS results do not depend on the other RHS.
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include "cplx.cuh"
 #include "dp_internal.h"
 
@@ -473,16 +477,51 @@ __global__ void k_inner_setup(const RhsState *outer, RhsState *inner, int n, dou
 
 }  // namespace
 
+// Grid of a grid-stride reduction: one full wave (resident blocks per SM x
+// SMs, from the occupancy calculator), so no partial second wave idles the
+// machine at the end; never more blocks than the scratch holds.
+template <typename K>
+static int one_wave(K kernel, int block, int cap)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair((const void *)kernel, block);
+    auto it = cache.find(key);
+    if (it != cache.end()) return std::min(it->second, cap);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, 0) != cudaSuccess || per < 1)
+        per = 1;
+    cudaGetLastError();
+    const int w = std::max(1, per * std::max(1, sms));
+    cache[key] = w;
+    return std::min(w, cap);
+}
+
 static Cfg cfg(const BlasCtx &bc, long long Vh, int n) { return cfg_for(Vh, n, bc.blocks); }
+
+template <typename K>
+static Cfg cfg_wave(const BlasCtx &bc, K kernel, long long Vh, int n)
+{
+    Cfg c = cfg_for(Vh, n, bc.blocks);
+    c.grid = std::min(c.grid, one_wave(kernel, c.block, bc.blocks));
+    return c;
+}
 
 cudaError_t blas_zero(void *v, size_t bytes, cudaStream_t s) { return cudaMemsetAsync(v, 0, bytes, s); }
 
 #define DISPATCH(prec, KERNEL, ...)                                              \
     do {                                                                         \
-        if ((prec) == 0)                                                         \
-            KERNEL<double><<<c.grid, c.block, 0, s>>>(c, __VA_ARGS__);           \
-        else                                                                     \
-            KERNEL<float><<<c.grid, c.block, 0, s>>>(c, __VA_ARGS__);            \
+        (void)c;                                                                 \
+        if ((prec) == 0) {                                                       \
+            const Cfg cw = cfg_wave(bc, KERNEL<double>, Vh, nrhs);               \
+            KERNEL<double><<<cw.grid, cw.block, 0, s>>>(cw, __VA_ARGS__);        \
+        } else {                                                                 \
+            const Cfg cw = cfg_wave(bc, KERNEL<float>, Vh, nrhs);                \
+            KERNEL<float><<<cw.grid, cw.block, 0, s>>>(cw, __VA_ARGS__);         \
+        }                                                                        \
     } while (0)
 
 cudaError_t blas_bicg_init(BlasCtx &bc, int prec, const void *b, void *r, void *rhat, void *p,
@@ -550,7 +589,7 @@ cudaError_t blas_bicg_update(BlasCtx &bc, int prec, void *x, void *r, const void
 cudaError_t blas_residual64(BlasCtx &bc, const double2 *b, const double2 *y, double2 *r,
                             long long Vh, int nrhs, RhsState *st, const int *mask, cudaStream_t s)
 {
-    Cfg c = cfg(bc, Vh, nrhs);
+    const Cfg c = cfg_wave(bc, k_residual64, Vh, nrhs);
     k_residual64<<<c.grid, c.block, 0, s>>>(c, b, y, r, Vh, nrhs, st, mask, bc.partials, bc.counter);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -675,6 +714,30 @@ __global__ void k_zero_masked(double2 *v, long long Vh, int n, const int *mask)
     for (int k = 0; k < 12; k++) v[k * cs + gid] = make_double2(0.0, 0.0);
 }
 }  // namespace
+
+namespace {
+__global__ void k_sub64_masked(const double2 *a, const double2 *b, double2 *out, long long Vh, int n,
+                               const int *mask)
+{
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= Vh * n) return;
+    if (!mask[gid % n]) return;
+    const long long cs = Vh * n;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        const double2 x = a[k * cs + gid], y = b[k * cs + gid];
+        out[k * cs + gid] = make_double2(x.x - y.x, x.y - y.y);
+    }
+}
+}  // namespace
+
+cudaError_t blas_sub64_masked(const double2 *a, const double2 *b, double2 *out, long long Vh,
+                              int nrhs, const int *mask, cudaStream_t s)
+{
+    const long long n = Vh * nrhs;
+    k_sub64_masked<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, out, Vh, nrhs, mask);
+    return cudaGetLastError();
+}
 
 cudaError_t blas_zero_masked(double2 *v, long long Vh, int nrhs, const int *mask, cudaStream_t s)
 {

@@ -105,7 +105,7 @@ struct Ctx {
     std::map<std::string, Stat> stats;
     std::atomic<long> launches{0};
 
-    std::map<TuneKey, int> tuned_block;
+    std::map<TuneKey, std::pair<int, int>> tuned;  // (threads per block, RHS per thread)
 
     std::unique_ptr<Scheduler, SchedDeleter> sched;
 
@@ -116,7 +116,8 @@ struct Ctx {
     void time_begin(const char *name, cudaEvent_t *a);
     void time_end(const char *name, cudaEvent_t a);
     void collect_timing();
-    int block_for(long long Vh, int prec, int link_fmt, int nrhs);
+    // dslash launch shape for the Schur launches: tuned, else a default
+    void launch_shape(long long Vh, int prec, int link_fmt, int nrhs, int *block, int *rpt);
 };
 
 std::shared_ptr<Field> find_field(Ctx *c, dp_field f);

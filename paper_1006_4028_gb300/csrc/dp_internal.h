@@ -67,8 +67,13 @@ struct DslashParams {
 
 // ---- launch wrappers (dslash.cu) ----
 // prec: 0 = FP64 (links LINK_F64_18), 1 = FP32 (links LINK_F32_18 / LINK_F32_12)
+// rpt: RHS per thread (1-4; >1 only for FP32 and the A^-1 / x - A^-1 D
+// epilogues); rpt 0 selects the shared-memory staged kernel (FP32 12-real
+// links, one RHS per thread, `block` ignored)
 cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi, int block,
-                          cudaStream_t st);
+                          int rpt, cudaStream_t st);
+cudaError_t launch_dslash_staged(const DslashParams &p, int epi, cudaStream_t st);
+bool dslash_rpt_ok(int nrhs, int rpt, int prec, int epi);
 
 // ---- clover (clover.cu) ----
 // clover term (no mass) for all sites of both parities, FP64, layout above
@@ -160,6 +165,9 @@ cudaError_t blas_bicg_update(BlasCtx &bc, int prec, void *x, void *r, const void
 cudaError_t blas_residual64(BlasCtx &bc, const double2 *b, const double2 *y, double2 *r,
                             long long Vh, int nrhs, RhsState *st, const int *mask,
                             cudaStream_t s);
+// out = a - b (FP64) for the RHS with mask[r] != 0
+cudaError_t blas_sub64_masked(const double2 *a, const double2 *b, double2 *out, long long Vh,
+                              int nrhs, const int *mask, cudaStream_t s);
 // zero the FP64 vector entries of the RHS with mask[r] != 0
 cudaError_t blas_zero_masked(double2 *v, long long Vh, int nrhs, const int *mask, cudaStream_t s);
 // r32 = r64 / scale (active RHS); zero for inactive

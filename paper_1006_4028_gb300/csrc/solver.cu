@@ -70,7 +70,8 @@ dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void
     const char *name = op.pr == 0 ? "dslash_fp64" : "dslash_fp32";
     cudaEvent_t ev;
     c->time_begin(name, &ev);
-    CK(launch_dslash(P, op.pr, op.lf, epi, op.block, c->stream));
+    const int rpt = (epi == EPI_AINV || epi == EPI_XMY_AINV) ? op.rpt : 1;
+    CK(launch_dslash(P, op.pr, op.lf, epi, op.block, rpt, c->stream));
     c->time_end(name, ev);
     c->launches++;
     return DP_OK;
@@ -80,19 +81,21 @@ constexpr int kStateStride = (int)(sizeof(RhsState) / sizeof(int));
 
 const int *state_mask(const RhsState *st) { return st ? &st[0].active : nullptr; }
 
-// y = Mhat x = x - A_ee^-1 D_eo A_oo^-1 D_oe x ; tmp: odd-parity vector
-dp_status apply_mhat(Ctx *c, const Op &op, const void *x, void *y, void *tmp,
+// Schur operator on parity p (q = 1 - p):
+// y = Mhat x = x - A_pp^-1 D_pq A_qq^-1 D_qp x ; tmp (parity q) keeps A_qq^-1 D_qp x
+dp_status apply_mhat(Ctx *c, const Op &op, int p, const void *x, void *y, void *tmp,
                      const RhsState *mask)
 {
-    dp_status s = dslash(c, op, 1, EPI_AINV, x, tmp, nullptr, state_mask(mask), kStateStride);
+    dp_status s = dslash(c, op, 1 - p, EPI_AINV, x, tmp, nullptr, state_mask(mask), kStateStride);
     if (s != DP_OK) return s;
-    return dslash(c, op, 0, EPI_XMY_AINV, tmp, y, x, state_mask(mask), kStateStride);
+    return dslash(c, op, p, EPI_XMY_AINV, tmp, y, x, state_mask(mask), kStateStride);
 }
 
 }  // namespace
 
-Batch::Batch(Ctx *cc, std::shared_ptr<Field> ff, int nslots, const dp_solve_opts &o, int round_cap)
-    : c(cc), f(std::move(ff)), n(nslots), opts(o), round_iters(round_cap)
+Batch::Batch(Ctx *cc, std::shared_ptr<Field> ff, int nslots, const dp_solve_opts &o, int round_cap,
+             int schur_parity)
+    : c(cc), f(std::move(ff)), n(nslots), opts(o), round_iters(round_cap), sp(schur_parity & 1)
 {
 }
 
@@ -116,7 +119,7 @@ size_t Batch::bytes_needed(const Geom &g, int nslots, int prec)
 {
     const size_t v64 = (size_t)g.Vh * nslots * 24 * sizeof(double);
     const size_t vin = (size_t)g.Vh * nslots * 24 * (prec == DP_PREC_FP64 ? 8 : 4);
-    return 5 * v64 + 8 * vin + ((size_t)1 << 20);
+    return 6 * v64 + 8 * vin + ((size_t)1 << 20);
 }
 
 dp_status Batch::init()
@@ -134,7 +137,8 @@ dp_status Batch::init()
     r64 = (double2 *)get(v64);
     y64 = (double2 *)get(v64);
     to64 = (double2 *)get(v64);
-    bool ok = bh && x && r64 && y64 && to64;
+    t64 = (double2 *)get(v64);
+    bool ok = bh && x && r64 && y64 && to64 && t64;
     void **iv[8] = {&in.r, &in.rh, &in.p, &in.v, &in.s, &in.t, &in.x, &in.to};
     for (auto pp : iv) {
         *pp = get(vin);
@@ -177,12 +181,12 @@ dp_status Batch::init()
     op64.lf = LINK_F64_18;
     op64.hop = hop64_d;
     op64.nrhs = n;
-    op64.block = c->block_for(Vh, 0, LINK_F64_18, n);
+    c->launch_shape(Vh, 0, LINK_F64_18, n, &op64.block, &op64.rpt);
     opin = op64;
     opin.pr = ipr;
     opin.lf = ilf;
     opin.hop = ipr == 0 ? (const void *)hop64_d : (const void *)hop32_d;
-    opin.block = c->block_for(Vh, ipr, ilf, n);
+    c->launch_shape(Vh, ipr, ilf, n, &opin.block, &opin.rpt);
     check_every = opts.check_every > 0 ? opts.check_every : (Vh * n >= (1 << 20) ? 2 : 8);
     return DP_OK;
 }
@@ -297,23 +301,35 @@ dp_status Batch::admit(Job *j)
     s = upload_mask(m);
     if (s != DP_OK) return s;
     const long long Vh = g.Vh;
-    // eta'_e -> y64, eta'_o -> to64 (only this job's slots are non-zero)
+    // eta'_p -> y64, eta'_q -> to64 (p = Schur parity; only this job's slots
+    // are non-zero)
     CK(cudaMemsetAsync(y64, 0, v64, c->stream));
     CK(cudaMemsetAsync(to64, 0, v64, c->stream));
-    CK(launch_point_source(g, slots_d, n, mask_d, y64, to64, c->stream));
-    // to64 <- A_oo^-1 eta'_o (in place), bhat = A_ee^-1 (eta'_e - D_eo to64)
+    CK(launch_point_source(g, slots_d, n, mask_d, sp == 0 ? y64 : to64, sp == 0 ? to64 : y64,
+                           c->stream));
     CloverApplyParams cp{};
-    for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[1][k];
     memcpy(cp.grp_of, op64.grp_of, sizeof cp.grp_of);
     cp.mask = mask_d;
-    cp.in = to64;
-    cp.out = to64;
     cp.Vh = Vh;
     cp.nrhs = n;
-    CK(launch_clover_apply(cp, 0, c->stream));
-    s = dslash(c, op64, 0, EPI_AINV_XMY, to64, bh, y64, mask_d, 1);
-    if (s != DP_OK) return s;
+    const int src_par = (j->grp.src[0] + j->grp.src[1] + j->grp.src[2] + j->grp.src[3]) & 1;
+    if (src_par == sp) {
+        // point source on the Schur parity: eta'_q = 0, bhat = A_pp^-1 eta'_p
+        for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[sp][k];
+        cp.in = y64;
+        cp.out = bh;
+        CK(launch_clover_apply(cp, 0, c->stream));
+    } else {
+        // to64 <- A_qq^-1 eta'_q (in place), bhat = A_pp^-1 (eta'_p - D_pq to64)
+        for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[1 - sp][k];
+        cp.in = to64;
+        cp.out = to64;
+        CK(launch_clover_apply(cp, 0, c->stream));
+        s = dslash(c, op64, sp, EPI_AINV_XMY, to64, bh, y64, mask_d, 1);
+        if (s != DP_OK) return s;
+    }
     CK(blas_zero_masked(x, Vh, n, mask_d, c->stream));
+    CK(blas_zero_masked(t64, Vh, n, mask_d, c->stream));
     // outer state rows: active, fresh (r = bhat, |bhat|^2 sets the threshold)
     for (int k = 0; k < j->ncomp; k++) {
         RhsState st{};
@@ -345,11 +361,11 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
     }
     auto body = [&](int first) -> dp_status {
         CK(blas_bicg_p(bc, pr, in.r, in.p, in.v, Vh, n, inner, first, c->stream));
-        dp_status s = apply_mhat(c, opin, in.p, in.v, in.to, inner);
+        dp_status s = apply_mhat(c, opin, sp, in.p, in.v, in.to, inner);
         if (s != DP_OK) return s;
         CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, c->stream));
         CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, c->stream));
-        s = apply_mhat(c, opin, in.s, in.t, in.to, inner);
+        s = apply_mhat(c, opin, sp, in.s, in.t, in.to, inner);
         if (s != DP_OK) return s;
         CK(blas_bicg_omega(bc, pr, in.t, in.s, Vh, n, inner, c->stream));
         CK(blas_bicg_update(bc, pr, in.x, in.r, in.p, in.s, in.t, in.rh, Vh, n, inner, max_iter, c->stream));
@@ -445,7 +461,9 @@ dp_status Batch::round()
         CK(blas_acc_f32(x, (const float4 *)in.x, Vh, n, outer, c->stream));
     else
         CK(blas_acc64(x, (const double2 *)in.x, Vh, n, outer, c->stream));
-    s = apply_mhat(c, op64, x, y64, to64, outer);
+    // t64 keeps A_qq^-1 D_qp x of this (final, once converged) x: the
+    // reconstruction of the other parity reuses it
+    s = apply_mhat(c, op64, sp, x, y64, t64, outer);
     if (s != DP_OK) return s;
     CK(blas_residual64(c->bc, bh, y64, r64, Vh, n, outer, nullptr, c->stream));
     c->launches += 3;
@@ -469,25 +487,31 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
         for (int k = 0; k < j->ncomp; k++) m[j->slot0 + k] = 1;
         dp_status s = upload_mask(m);
         if (s != DP_OK) return s;
-        // eta'_o again (to64; y64 takes the even part), then x_o -> y64
+        // other parity q = 1 - p: x_q = A_qq^-1 (eta'_q - D_qp x_p)
+        //                           = A_qq^-1 eta'_q - t64, t64 = A_qq^-1 D_qp x_p
+        // from the last FP64 Schur application (x_p final): no extra dslash
         CK(cudaMemsetAsync(y64, 0, v64, c->stream));
         CK(cudaMemsetAsync(to64, 0, v64, c->stream));
-        CK(launch_point_source(g, slots_d, n, mask_d, y64, to64, c->stream));
-        s = dslash(c, op64, 1, EPI_AINV_XMY, x, y64, to64, mask_d, 1);
-        if (s != DP_OK) return s;
-        // residual report: the full residual of (D'+M)S' = eta' is (A_ee rhat, 0)
-        // with x_o rebuilt from x_e, so |A_ee rhat| / |eta'|
+        CK(launch_point_source(g, slots_d, n, mask_d, sp == 0 ? y64 : to64, sp == 0 ? to64 : y64,
+                               c->stream));
         CloverApplyParams cp{};
-        for (int k = 0; k < kMaxGroups; k++) {
-            cp.mat[k] = f->clov[0];
-            cp.diag[k] = jobs[k] ? 4.0 + jobs[k]->grp.M : 0.0;
-        }
         memcpy(cp.grp_of, op64.grp_of, sizeof cp.grp_of);
         cp.mask = mask_d;
-        cp.in = r64;
-        cp.out = to64;
         cp.Vh = Vh;
         cp.nrhs = n;
+        for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[1 - sp][k];
+        cp.in = to64;
+        cp.out = to64;
+        CK(launch_clover_apply(cp, 0, c->stream));
+        CK(blas_sub64_masked(to64, t64, y64, Vh, n, mask_d, c->stream));
+        // residual report: the full residual of (D'+M)S' = eta' is (A_pp rhat, 0)
+        // with x_q rebuilt from x_p, so |A_pp rhat| / |eta'|
+        for (int k = 0; k < kMaxGroups; k++) {
+            cp.mat[k] = f->clov[sp];
+            cp.diag[k] = jobs[k] ? 4.0 + jobs[k]->grp.M : 0.0;
+        }
+        cp.in = r64;
+        cp.out = to64;
         CK(launch_clover_apply(cp, 0, c->stream));
         CK(blas_norm2(c->bc, 0, to64, Vh, n, nrm_d, c->stream));
         double2 *prop_d = nullptr;
@@ -500,8 +524,8 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
             }
             prop_d = (double2 *)prop_tmp;
         }
-        CK(launch_restore_contract(x, y64, g, n, alpha_d, slots_d, kMaxGroups, tsrc_d, mask_d, cpp_d,
-                                   cpart, prop_d, c->stream));
+        CK(launch_restore_contract(sp == 0 ? x : y64, sp == 0 ? y64 : x, g, n, alpha_d, slots_d,
+                                   kMaxGroups, tsrc_d, mask_d, cpp_d, cpart, prop_d, c->stream));
         if (j->cpp_dst) CK(launch_cpp_commit(cpp_d + (size_t)tab * g.T, j->cpp_dst, g.T, j->accumulate, c->stream));
         if (j->cpp_host) CK(cudaMemcpyAsync(j->cpp_host, cpp_d + (size_t)tab * g.T, sizeof(double) * g.T, cudaMemcpyDeviceToHost, c->stream));
         if (prop_d)
@@ -562,7 +586,9 @@ dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group
     }
     res.assign(ng, SolveResult());
     const bool batched = o.batched != 0;
-    Batch B(c, f, batched ? 12 * ng : 1, o, 0);
+    // all groups share the source: solve on its parity
+    const int sp = (groups[0].src[0] + groups[0].src[1] + groups[0].src[2] + groups[0].src[3]) & 1;
+    Batch B(c, f, batched ? 12 * ng : 1, o, 0, sp);
     dp_status s = B.init();
     if (s != DP_OK) return s;
     std::vector<Job> jobs(batched ? ng : 12 * ng);

@@ -130,6 +130,53 @@ def test_invalid_arguments_are_errors(ctx):
         dp.dp_field_free(ctx, f)
 
 
+@pytest.mark.parametrize("prec,tol,rpts", [("mixed_fp32", 1e-6, (1, 2, 3, 4, -1)),
+                                           ("fp64", 1e-13, (1,))])
+def test_schur_launch_all_rhs_per_thread(ctx, setup, prec, tol, rpts):
+    """out_e = A_ee^-1 D_eo psi_o on packed device spinors (the solver's launch),
+    for every launch shape (1-4 RHS per thread, and -1: the shared-memory
+    staged kernel): equal to each other and, through A_ee out_e = D_eo psi_o,
+    to the oracle."""
+    torch = pytest.importorskip("torch")
+    dims, f, op, _ = setup
+    M = 0.2
+    prof = ("cosh_4d", 0.3)
+    psi = li.random_spinor(dims, 12, 31)
+    ev, od = dp.pack_half_spinors(psi, dims)
+    Vh = ev.shape[1]
+
+    # FP64 chunks are one complex component; FP32 chunks (float4) are two
+    def dev(a):
+        if prec == "fp64":
+            return torch.from_numpy(np.ascontiguousarray(a).view(np.float64)).cuda()
+        b = a.reshape(6, 2, Vh, 12).transpose(0, 2, 3, 1).astype(np.complex64)
+        return torch.from_numpy(np.ascontiguousarray(b).view(np.float32)).cuda()
+
+    def host(t):
+        if prec == "fp64":
+            return t.cpu().numpy().view(np.complex128).reshape(12, Vh, 12)
+        b = t.cpu().numpy().view(np.complex64).reshape(6, Vh, 12, 2)
+        return b.transpose(0, 3, 1, 2).reshape(12, Vh, 12).astype(np.complex128)
+
+    xin = dev(od)
+    outs = []
+    for r in rpts:
+        out = torch.zeros_like(xin)
+        dp.dp_dslash_dev(ctx, f, M, prof, prec, 1, 0, xin.data_ptr(), out.data_ptr(), 12,
+                         0, r, 1)
+        torch.cuda.synchronize()
+        outs.append(host(out))
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    full_out = dp.unpack_half_spinors(outs[0], np.zeros_like(outs[0]), dims)
+    psi_odd = dp.unpack_half_spinors(np.zeros_like(ev), od, dims)
+    lhs = (4 + M) * full_out + op.clover(full_out)
+    rhs = op.hop(psi_odd, (prof[0], prof[1], (0, 0, 0, 0)))
+    t, z, y, x = np.indices(oracle.array_shape(dims))
+    even = ((t + x + y + z) % 2) == 0
+    assert per_site_rel(lhs[:, even], rhs[:, even]) < 10 * tol
+
+
 def test_full_size_48x24_fp32_hop(ctx):
     """One multi-RHS FP32 hopping application on the 48x24^3 heavy-quark
     lattice (eps = 0.3, seed 1), all sites compared with the oracle."""
