@@ -223,6 +223,10 @@ def run_reference(args):
     return 0
 
 
+LINKS = {"mixed_fp32": "12-real FP32 links", "mixed_fp16": "12-real FP16 links + FP32 scale",
+         "mixed_bf16": "12-real BF16 links + FP32 scale"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,6 +241,11 @@ def main():
                     help="offered load as a fraction of the measured batch-solve rate")
     ap.add_argument("--dims", default=None,
                     help="T,Lx,Ly,Lz of a smaller lattice for profiling runs (not the headline)")
+    ap.add_argument("--prec", default="mixed_fp32",
+                    choices=["mixed_fp32", "mixed_fp16", "mixed_bf16"],
+                    help="inner-solver precision (links: 12 FP32 reals, or 12 16-bit reals "
+                         "plus one FP32 scale)")
+    ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "cgne"])
     ap.add_argument("--graphs", type=int, default=0,
                     help="capture solver iterations as CUDA graphs in the timed region "
                          "(per-kernel event timing needs them off)")
@@ -275,7 +284,9 @@ def main():
     dp.dp_field_set_csw(ctx, field, CSW)
     del U
     T, V = DIMS[0], int(np.prod(DIMS))
-    opts = {"prec": "mixed_fp32", "compress12": 1, "batched": 1, "use_graph": args.graphs}
+    opts = {"prec": args.prec, "compress12": 1, "batched": 1, "use_graph": args.graphs,
+            "solver": args.solver}
+    link_bytes = 48 if args.prec == "mixed_fp32" else 28  # per link in the inner dslash
     prof = ("cosh_t", ALPHA0)
     rng = np.random.default_rng(1000 + rank)
 
@@ -284,7 +295,7 @@ def main():
 
     # tune the launch shapes of the dslash for this volume and batch
     tuned = {}
-    for prec, c12 in (("mixed_fp32", 1), ("fp64", 0)):
+    for prec, c12 in ((args.prec, 1), ("fp64", 0)):
         for nr in (12, 1):
             tuned["%s_n%d" % (prec, nr)] = dp.dp_autotune(ctx, field, prec, c12, nr)
 
@@ -348,21 +359,22 @@ def main():
     # ---- roofline of the dominant kernel (multi-RHS FP32 dslash) ----
     Vh = V // 2
     n = 12
-    # algorithmic bytes per half-site: spinor in/out n*(24+24)*4, 8 links of
-    # 12 FP32 reals, the FP32 clover inverse (72 reals); the second Schur
-    # launch also reads x (n*24*4): average of the two launch kinds
-    b_ainv = n * 48 * 4 + 8 * 12 * 4 + 72 * 4
+    # algorithmic bytes per half-site: spinor in/out n*(24+24)*4, 8 links
+    # (12 FP32 reals, or 12 16-bit reals + an FP32 scale), the FP32 clover
+    # inverse (72 reals); the second Schur launch also reads x (n*24*4):
+    # average of the two launch kinds
+    b_ainv = n * 48 * 4 + 8 * link_bytes + 72 * 4
     b_xmy = b_ainv + n * 24 * 4
     bytes_per_launch = Vh * (b_ainv + b_xmy) / 2
     avg_ms = d32_ms / max(d32_n, 1)
     hbm_peak, peak_src = peaks()
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     # cross-check: the same kernel with all 12 RHS active, timed in isolation
-    buf_in = torch.zeros(dp.dp_spinor_bytes(ctx, field, "mixed_fp32", 12) // 4, dtype=torch.float32,
+    buf_in = torch.zeros(dp.dp_spinor_bytes(ctx, field, args.prec, 12) // 4, dtype=torch.float32,
                          device="cuda")
     buf_in.normal_()
     buf_out = torch.empty_like(buf_in)
-    iso_ms = dp.dp_dslash_dev(ctx, field, MASS, prof, "mixed_fp32", 1, 0, buf_in.data_ptr(),
+    iso_ms = dp.dp_dslash_dev(ctx, field, MASS, prof, args.prec, 1, 0, buf_in.data_ptr(),
                               buf_out.data_ptr(), 12, 0, 0, 20)
     del buf_in, buf_out
     iso_gbs = Vh * b_ainv / (iso_ms / 1e3) / 1e9
@@ -387,7 +399,9 @@ def main():
         "config": dict(WORKLOAD, parallelism="replicas" if ws > 1 else "single",
                        l2="working set ~%.1f GB >> 129 MB L2 (no flush needed)"
                           % (dp.dp_device_bytes(ctx) / 1e9),
-                       solver="BiCGStab FP32 inner (12-real links) in FP64 defect correction",
+                       solver="%s FP32 inner (%s) in FP64 defect correction"
+                              % ({"bicgstab": "BiCGStab", "cgne": "CGNE"}[args.solver],
+                                 LINKS[args.prec]),
                        graphs=bool(args.graphs), tuned_launch=tuned),
         "gpu_launches": launches,
         "iterations": {"inner_mean": float(np.mean([i["iters_inner"] for i in infos])),
@@ -395,7 +409,7 @@ def main():
                        "true_rel_residue_max": float(max(i["true_rel_residue"] for i in infos))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
-                     "kernel": "dslash_fp32 (12 RHS, 12-real links, fused A^-1 epilogue)",
+                     "kernel": "dslash_fp32 (12 RHS, %s, fused A^-1 epilogue)" % LINKS[args.prec],
                      "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                      "launches": d32_n, "peak_source": peak_src,
                      "measured_in": kernel_timing_region,

@@ -103,14 +103,18 @@ typedef enum {
     DP_PREC_MIXED_BF16 = 3  /* FP32 inner with BF16 links (per-link scale)       */
 } dp_prec;
 
+/* BiCGStab on Mhat x = b (Sec. I, eqs. linsysunprec/linsysprec solved
+ * iteratively), or CG on the normal equations Mhat^dag Mhat x = Mhat^dag b
+ * (CGNE), both stopping on |b - Mhat x| / |b|. */
 typedef enum { DP_SOLVER_BICGSTAB = 0, DP_SOLVER_CGNE = 1 } dp_solver;
 
 typedef struct {
     int max_iter;     /* total inner iterations allowed (0: 20000)                  */
     int solver;       /* dp_solver                                                 */
     int prec;         /* dp_prec                                                   */
-    int compress12;   /* FP32/16-bit links stored as 12 reals (row 2 rebuilt)        */
-    double inner_tol; /* relative reduction per inner solve (0: 1e-5 FP32)          */
+    int compress12;   /* FP32 links stored as 12 reals (row 2 rebuilt); 16-bit
+                         links always are                                           */
+    double inner_tol; /* relative reduction per inner solve (0: 1e-6 mixed)         */
     int batched;      /* 1: all RHS in one multi-RHS solve; 0: one RHS at a time    */
     int use_graph;    /* capture one solver iteration as a CUDA graph               */
     int check_every;  /* iterations between convergence reads (0: automatic)        */
@@ -147,8 +151,11 @@ size_t dp_device_bytes(dp_ctx *ctx);
 /* ---- gauge fields (Sec. I: D[U]; Sec. II: O(a)-improved operator) -------- */
 
 /* Upload and pack a gauge field: lexicographic complex128 links (layout above)
- * to even-odd, site-blocked SoA on the device in FP64 (18 reals), FP32 (12 and
- * 18 reals) and 16-bit (12 reals + one FP32 scale per link) copies.
+ * to even-odd, site-blocked SoA on the device in FP64 (18 reals) and FP32 (12
+ * and 18 reals) copies.  The 16-bit copies (rows 0 and 1 as FP16 or BF16
+ * times one FP32 scale per link, the largest modulus of those six entries)
+ * are made from the FP64 links the first time a DP_PREC_MIXED_FP16 / _BF16
+ * call needs them.
  * bc_t = -1 antiperiodic time (the paper's case, Sec. II), +1 periodic. */
 dp_status dp_field_load(dp_ctx *ctx, const double *links, const int dims[4], int bc_t,
                         dp_field *out);
@@ -237,9 +244,10 @@ typedef enum {
 } dp_apply_kind;
 
 /* out = op(in) for nrhs host spinors [nrhs][V][4][3] (complex128), computed
- * in precision `prec` (DP_PREC_FP64 or DP_PREC_MIXED_FP32: FP32 kernels with
- * FP32-rounded inputs).  The profile is placed relative to src (NULL src: the
- * origin).  compress12 selects 12-real FP32 links. */
+ * in precision `prec` (DP_PREC_FP64; the mixed precisions: FP32 kernels with
+ * FP32-rounded inputs and the links of that precision).  The profile is
+ * placed relative to src (NULL src: the origin).  compress12 selects 12-real
+ * FP32 links. */
 dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_profile *profile,
                    const int src[4], int prec, int compress12, const double *in, double *out,
                    int nrhs);
@@ -258,13 +266,15 @@ dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profi
 
 /* One hopping application D_{p,1-p} with the fused clover-inverse epilogue
  * (out = A_pp^-1 D_{p,1-p} in), on packed even-odd device spinors of nrhs
- * right-hand sides: layout [chunk][V/2][nrhs] with chunk = float4 (6 per
- * spinor, FP32) or double2 (12, FP64).  `in`/`out` are device pointers the
+ * right-hand sides.  FP64 layout: double2 [12 components][V/2][nrhs]
+ * (component = 3*spin + colour).  FP32 layout (RHS pairs): float4
+ * [12 components][V/2][nrhs/2] holding (re_2q, re_2q+1, im_2q, im_2q+1) of
+ * pair q.  `in`/`out` are device pointers the
  * caller allocated with dp_spinor_bytes().  Launch shape from the tuner
- * unless given: block_threads > 0 sets the block; rhs_per_thread 1-4 selects
- * the register kernel with that many RHS per thread (2-4: FP32 only, nrhs a
- * multiple and 12 divisible by it), -1 the shared-memory staged kernel (FP32,
- * 12-real links, nrhs dividing 96), 0 the tuned or default shape.  iters
+ * unless given: block_threads > 0 sets the block; rhs_per_thread selects the
+ * RHS per thread (FP64: 1; FP32: 2 or 4, i.e. one or two RHS pairs of the
+ * paired layout, 4 needing nrhs % 4 == 0), 0 the tuned or default shape.
+ * FP32 needs nrhs even.  iters
  * launches back to back; if ms_out is non-NULL it receives the average launch
  * time measured with CUDA events on the context stream. */
 size_t dp_spinor_bytes(dp_ctx *ctx, dp_field field, int prec, int nrhs);
@@ -273,12 +283,26 @@ dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile 
                         int nrhs, int block_threads, int rhs_per_thread, int iters,
                         float *ms_out);
 
+/* The even-odd Schur operator of the preconditioned system (Sec. II, eq.
+ * linsysprec, reduced to parity p = `parity`, q = 1 - p):
+ *   dagger = 0:  out = Mhat in = in - A_pp^-1 D_pq A_qq^-1 D_qp in
+ *   dagger = 1:  out = Mhat^dag in = in - g5 D~_pq A_qq^-1 D~_qp g5 A_pp^-1 in
+ * with A = 4 + M + clover, D the hopping part with the profile placed at src
+ * (NULL: origin) and D~ the hopping part of the reciprocal profile 1/alpha_B
+ * (D(alpha_B)^dag = g5 D(1/alpha_B) g5).  These are the operators the BiCGStab
+ * and CGNE solvers apply.  in/out: distinct device arrays of one parity in the
+ * packed layout of `prec` (see dp_dslash_dev), caller-owned; scratch (two
+ * spinor arrays, two hop tables) comes from the context allocator.  FP32 and
+ * 16-bit precisions need nrhs even.  Returns after the stream work finished. */
+dp_status dp_schur_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
+                       const int src[4], int prec, int compress12, int parity, int dagger,
+                       const void *in, void *out, int nrhs);
+
 /* ---- autotuner ----------------------------------------------------------- */
 
 /* Time candidate launch shapes of the multi-RHS dslash for this field,
- * precision and nrhs (register kernel: 64-256 threads per block x 1-4 RHS per
- * thread; shared-memory staged kernel), and keep the fastest for the solver's
- * later launches.  best_rhs_per_thread returns -1 for the staged kernel.
+ * precision and nrhs (64-256 threads per block x the RHS-per-thread choices
+ * of dp_dslash_dev), and keep the fastest for the solver's later launches.
  * best_* may be NULL. */
 dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int nrhs,
                       int *best_block_threads, int *best_rhs_per_thread, float *best_ms);

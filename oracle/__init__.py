@@ -417,3 +417,52 @@ def dense_matrix(op, M, profile=None, batch=768):
         E[np.arange(nb), j0 + np.arange(nb)] = 1
         A[:, j0:j0 + nb] = op.apply(E, M, profile).reshape(nb, N).T
     return A
+
+
+# --------------------------------------------------------------------------
+# 16-bit link storage (the compressed gauge field of the mixed-precision
+# inner solver): what the operator sees when the links are kept as rows 0
+# and 1 in FP16 or BF16 with one FP32 scale per link and row 2 rebuilt.
+# --------------------------------------------------------------------------
+def round_bf16(x):
+    """float32 -> nearest bfloat16 (ties to even), returned as float32.
+
+    bfloat16 is the upper 16 bits of an IEEE float32; rounding adds half an
+    ulp of the kept part (0x7FFF, plus the kept part's last bit for ties) to
+    the 32-bit pattern and clears the low 16 bits.  Finite inputs only.
+    """
+    b = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def stored_links16(links, kind):
+    """The gauge field as the 16-bit storage reproduces it, in FP64.
+
+    Per link U: s = fp32(max of |Re|, |Im| over rows 0 and 1) (1 if that is
+    0); each of those 12 reals r is kept as q = round16(fp32(r * (1/s))) with
+    round16 = FP16 or BF16 round-to-nearest-even; the operator uses s*q for
+    rows 0 and 1 and row 2 = conj(row0 x row1), which is the third row of a
+    special unitary matrix (the SU(3) links of Sec. I).  kind: "fp16" | "bf16".
+    """
+    U = _c128(links)
+    rows = U[..., :2, :]
+    re, im = rows.real, rows.imag
+    mx = np.maximum(np.abs(re), np.abs(im)).max(axis=(-2, -1))
+    s = mx.astype(np.float32)
+    s = np.where(s > 0, s, np.float32(1.0)).astype(np.float64)
+    inv = (1.0 / s)[..., None, None]
+
+    def q(a):
+        a32 = (a * inv).astype(np.float32)
+        if kind == "fp16":
+            return a32.astype(np.float16).astype(np.float64)
+        if kind == "bf16":
+            return round_bf16(a32).astype(np.float64)
+        raise ValueError("kind must be 'fp16' or 'bf16'")
+
+    r01 = (q(re) + 1j * q(im)) * s[..., None, None]
+    out = np.empty_like(U)
+    out[..., :2, :] = r01
+    out[..., 2, :] = np.conj(np.cross(r01[..., 0, :], r01[..., 1, :]))
+    return out

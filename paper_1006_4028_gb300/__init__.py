@@ -26,14 +26,16 @@ __all__ = [
     "dp_create", "dp_destroy", "dp_last_error", "dp_device_bytes",
     "dp_field_load", "dp_field_set_csw", "dp_field_free",
     "dp_solve_point", "dp_solve_point_multi", "dp_solve_point_dev",
-    "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_autotune",
+    "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
+    "dp_autotune",
     "dp_timing_enable", "dp_timing_reset", "dp_timing_get", "dp_launch_count",
     "dp_serve_start", "dp_submit", "dp_wait", "dp_cancel", "dp_serve_stats_get", "dp_serve_stop",
-    "PROFILE_KINDS", "PREC", "APPLY", "STATUS",
+    "PROFILE_KINDS", "PREC", "SOLVER", "APPLY", "STATUS",
 ]
 
 PROFILE_KINDS = {"none": 0, "exp_t": 1, "cosh_t": 2, "cosh_4d": 3, "table": 4}
 PREC = {"fp64": 0, "mixed_fp32": 1, "mixed_fp16": 2, "mixed_bf16": 3}
+SOLVER = {"bicgstab": 0, "cgne": 1}
 APPLY = {"hop": 0, "clover": 1, "full": 2, "clover_inv": 3}
 STATUS = {0: "DP_OK", 1: "DP_ERR_INVALID_ARG", 2: "DP_ERR_OOM", 3: "DP_ERR_NOT_CONVERGED",
           4: "DP_ERR_BREAKDOWN", 5: "DP_ERR_NONFINITE", 6: "DP_ERR_TIMEOUT", 7: "DP_ERR_REJECTED",
@@ -119,6 +121,7 @@ def load(build_if_missing=False):
         "dp_restore_contract_dev": ([vp, up, ip, vp, vp, vp, vp, vp], ip),
         "dp_restore_contract_noalloc": ([vp, up, ip, vp, vp, vp, vp, vp], ip),
         "dp_spinor_bytes": ([vp, up, ip, ip], sz),
+        "dp_schur_dev": ([vp, up, dp, P(Profile), P(C.c_int * 4), ip, ip, ip, ip, vp, vp, ip], ip),
         "dp_dslash_dev": ([vp, up, dp, P(Profile), ip, ip, ip, vp, vp, ip, ip, ip, ip,
                            P(C.c_float)], ip),
         "dp_autotune": ([vp, up, ip, ip, ip, P(C.c_int), P(C.c_int), P(C.c_float)], ip),
@@ -176,7 +179,8 @@ def _opts(o):
     s = SolveOpts()
     o = dict(o or {})
     s.max_iter = int(o.get("max_iter", 0))
-    s.solver = int(o.get("solver", 0))
+    sv = o.get("solver", "bicgstab")
+    s.solver = SOLVER[sv] if isinstance(sv, str) else int(sv)
     prec = o.get("prec", "mixed_fp32")
     s.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     s.compress12 = int(o.get("compress12", 1))
@@ -397,6 +401,18 @@ def dp_dslash_dev(ctx, field, M, profile, prec, compress12, out_parity, in_ptr, 
                                 int(nrhs), int(block_threads), int(rhs_per_thread), int(iters),
                                 C.byref(ms)))
     return ms.value
+
+
+def dp_schur_dev(ctx, field, M, profile, src, prec, compress12, parity, dagger, in_ptr, out_ptr,
+                 nrhs):
+    """out = Mhat in (dagger=0) or Mhat^dag in (dagger=1) on packed device
+    spinors of one parity (the solvers' operators)."""
+    pr, keep = _profile(profile)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    s = (C.c_int * 4)(*(src if src is not None else (0, 0, 0, 0)))
+    _check(load().dp_schur_dev(ctx, int(field), float(M), C.byref(pr), C.byref(s), p,
+                               int(compress12), int(parity), int(dagger), C.c_void_p(int(in_ptr)),
+                               C.c_void_p(int(out_ptr)), int(nrhs)))
 
 
 def dp_autotune(ctx, field, prec, compress12, nrhs):

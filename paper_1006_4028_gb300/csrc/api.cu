@@ -122,8 +122,8 @@ void Ctx::launch_shape(long long Vh, int prec, int link_fmt, int nrhs, int *bloc
         *rpt = it->second.second;
         return;
     }
-    *block = prec == 0 ? 64 : 64;
-    *rpt = 1;
+    *block = 64;
+    *rpt = prec == 0 ? 1 : 2;  // FP32: one RHS pair per thread
 }
 
 std::shared_ptr<Field> find_field(Ctx *c, dp_field f)
@@ -132,6 +132,53 @@ std::shared_ptr<Field> find_field(Ctx *c, dp_field f)
     auto it = c->fields.find(f);
     if (it == c->fields.end()) return nullptr;
     return it->second;
+}
+
+int inner_link_format(int prec, int compress12)
+{
+    switch (prec) {
+    case DP_PREC_FP64: return LINK_F64_18;
+    case DP_PREC_MIXED_FP16: return LINK_H16_12;
+    case DP_PREC_MIXED_BF16: return LINK_B16_12;
+    default: return compress12 ? LINK_F32_12 : LINK_F32_18;
+    }
+}
+
+dp_status field_links(Ctx *c, Field &f, int link_fmt, int parity, const void **out)
+{
+    switch (link_fmt) {
+    case LINK_F64_18: *out = f.l64[parity]; return DP_OK;
+    case LINK_F32_18: *out = f.l32f[parity]; return DP_OK;
+    case LINK_F32_12: *out = f.l32c[parity]; return DP_OK;
+    case LINK_H16_12:
+    case LINK_B16_12: break;
+    default: set_error("unknown link format %d", link_fmt); return DP_ERR_INVALID_ARG;
+    }
+    const int k = link_fmt == LINK_H16_12 ? 0 : 1;
+    std::lock_guard<std::mutex> lk(f.inv_mu);
+    if (!f.l16[k][0]) {
+        void *p0 = c->alloc(links16_bytes(f.g.Vh)), *p1 = c->alloc(links16_bytes(f.g.Vh));
+        if (!p0 || !p1) {
+            c->release(p0);
+            c->release(p1);
+            set_error("out of device memory (16-bit links)");
+            return DP_ERR_OOM;
+        }
+        cudaError_t e = launch_pack_links16(f.l64[0], f.g.Vh, link_fmt, p0, c->stream);
+        if (e == cudaSuccess) e = launch_pack_links16(f.l64[1], f.g.Vh, link_fmt, p1, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            c->release(p0);
+            c->release(p1);
+            set_error("packing 16-bit links: %s", cudaGetErrorString(e));
+            return DP_ERR_CUDA;
+        }
+        c->launches += 2;
+        f.l16[k][0] = p0;
+        f.l16[k][1] = p1;
+    }
+    *out = f.l16[k][parity];
+    return DP_OK;
 }
 
 dp_status profile_tables(const dp_profile &p, const Geom &g, int bc_t, const int src[4],
@@ -257,12 +304,8 @@ dp_status check_opts(const dp_solve_opts *in, dp_solve_opts *out)
         set_error("invalid precision %d", o.prec);
         return DP_ERR_INVALID_ARG;
     }
-    if (o.prec == DP_PREC_MIXED_FP16 || o.prec == DP_PREC_MIXED_BF16) {
-        set_error("16-bit link precision is not available in this build");
-        return DP_ERR_INVALID_ARG;
-    }
-    if (o.solver != DP_SOLVER_BICGSTAB) {
-        set_error("solver %d is not available in this build (BiCGStab only)", o.solver);
+    if (o.solver != DP_SOLVER_BICGSTAB && o.solver != DP_SOLVER_CGNE) {
+        set_error("unknown solver %d", o.solver);
         return DP_ERR_INVALID_ARG;
     }
     if (!(o.inner_tol >= 0) || o.inner_tol >= 1) {
@@ -511,6 +554,8 @@ dp_status dp_field_free(dp_ctx *ctx, dp_field field)
         c.release(f->l32c[p]);
         c.release(f->clov[p]);
         c.release(f->clov32[p]);
+        c.release(f->l16[0][p]);
+        c.release(f->l16[1][p]);
     }
     {
         std::lock_guard<std::mutex> lk(f->inv_mu);
@@ -532,8 +577,8 @@ dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_pro
         return DP_ERR_NOT_FOUND;
     }
     Field &f = *fp;
-    if (!in || !out || nrhs < 1 || nrhs > kMaxRhs || kind < 0 || kind > 3 ||
-        (prec != DP_PREC_FP64 && prec != DP_PREC_MIXED_FP32) || !std::isfinite(M)) {
+    if (!in || !out || nrhs < 1 || nrhs > kMaxRhs || kind < 0 || kind > 3 || prec < DP_PREC_FP64 ||
+        prec > DP_PREC_MIXED_BF16 || !std::isfinite(M)) {
         set_error("dp_apply: invalid argument");
         return DP_ERR_INVALID_ARG;
     }
@@ -557,14 +602,23 @@ dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_pro
                                    alpha.data(), hop.data());
     if (stt != DP_OK) return stt;
     std::vector<float> hopf(hop.begin(), hop.end());
+    const int lf = inner_link_format(prec, compress12);
+    const void *links[2];
+    for (int p = 0; p < 2; p++) {
+        stt = field_links(&c, f, lf, p, &links[p]);
+        if (stt != DP_OK) return stt;
+    }
 
     std::shared_ptr<CloverInv> ci;
     if (kind == DP_APPLY_CLOVER_INV) {
         stt = get_clover_inv(&c, f, M, &ci);
         if (stt != DP_OK) return stt;
     }
-    const size_t vb = (size_t)g.Vh * nrhs * 24 * (pr == 0 ? 8 : 4);
-    double2 *lex = (double2 *)c.alloc(nlex * sizeof(double));
+    // FP32 kernels work on RHS pairs: an odd count gets one zero RHS appended
+    const int nk = (pr == 1 && (nrhs & 1)) ? nrhs + 1 : nrhs;
+    const size_t nlex_k = (size_t)g.V * 24 * nk;
+    const size_t vb = (size_t)g.Vh * nk * 24 * (pr == 0 ? 8 : 4);
+    double2 *lex = (double2 *)c.alloc(nlex_k * sizeof(double));
     void *ie = c.alloc(vb), *io = c.alloc(vb), *oe = c.alloc(vb), *oo = c.alloc(vb);
     void *te = c.alloc(vb), *to = c.alloc(vb);
     void *hopd = c.alloc(hop.size() * sizeof(double));
@@ -574,15 +628,16 @@ dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_pro
         ret = DP_ERR_OOM;
     } else {
         auto run = [&]() -> dp_status {
+            if (nk > nrhs)
+                CUDA_OK(cudaMemsetAsync((double *)lex + nlex, 0, (nlex_k - nlex) * sizeof(double), c.stream));
             CUDA_OK(cudaMemcpyAsync(lex, in, nlex * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-            CUDA_OK(launch_pack_spinor(lex, g, nrhs, pr, ie, io, c.stream));
+            CUDA_OK(launch_pack_spinor(lex, g, nk, pr, ie, io, c.stream));
             if (pr == 0)
                 CUDA_OK(cudaMemcpyAsync(hopd, hop.data(), hop.size() * sizeof(double),
                                         cudaMemcpyHostToDevice, c.stream));
             else
                 CUDA_OK(cudaMemcpyAsync(hopd, hopf.data(), hopf.size() * sizeof(float),
                                         cudaMemcpyHostToDevice, c.stream));
-            const int lf = pr == 0 ? LINK_F64_18 : (compress12 ? LINK_F32_12 : LINK_F32_18);
             void *inp[2] = {ie, io}, *outp[2] = {oe, oo}, *tmp[2] = {te, to};
             for (int p = 0; p < 2; p++) {
                 const void *mat;
@@ -594,7 +649,7 @@ dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_pro
                 cp.mat[0] = mat;
                 cp.diag[0] = kind == DP_APPLY_FULL ? 4.0 + M : 0.0;
                 cp.Vh = g.Vh;
-                cp.nrhs = nrhs;
+                cp.nrhs = nk;
                 cp.in = inp[p];
                 cp.out = (kind == DP_APPLY_FULL) ? tmp[p] : outp[p];
                 if (kind == DP_APPLY_CLOVER || kind == DP_APPLY_CLOVER_INV) {
@@ -604,14 +659,12 @@ dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_pro
                 DslashParams P{};
                 P.in = inp[1 - p];
                 P.out = outp[p];
-                P.links[0] = pr == 0 ? (const void *)f.l64[0]
-                                     : (compress12 ? (const void *)f.l32c[0] : (const void *)f.l32f[0]);
-                P.links[1] = pr == 0 ? (const void *)f.l64[1]
-                                     : (compress12 ? (const void *)f.l32c[1] : (const void *)f.l32f[1]);
+                P.links[0] = links[0];
+                P.links[1] = links[1];
                 P.hop = hopd;
                 P.g = g;
                 P.parity = p;
-                P.nrhs = nrhs;
+                P.nrhs = nk;
                 int epi = EPI_HOP;
                 if (kind == DP_APPLY_FULL) {
                     CUDA_OK(launch_clover_apply(cp, pr, c.stream));
@@ -619,10 +672,10 @@ dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_pro
                     epi = EPI_XPY;
                 }
                 int blk, rpt;
-                c.launch_shape(g.Vh, pr, lf, nrhs, &blk, &rpt);
-                CUDA_OK(launch_dslash(P, pr, lf, epi, blk, 1, c.stream));
+                c.launch_shape(g.Vh, pr, lf, nk, &blk, &rpt);
+                CUDA_OK(launch_dslash(P, pr, lf, epi, blk, pr == 0 ? 1 : 2, c.stream));
             }
-            CUDA_OK(launch_unpack_spinor(oe, oo, g, nrhs, pr, lex, c.stream));
+            CUDA_OK(launch_unpack_spinor(oe, oo, g, nk, pr, lex, c.stream));
             CUDA_OK(cudaMemcpyAsync(out, lex, nlex * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
             CUDA_OK(cudaStreamSynchronize(c.stream));
             c.launches += 6;
@@ -664,24 +717,27 @@ dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile 
     }
     Field &f = *fp;
     if (!in || !out || nrhs < 1 || nrhs > kMaxRhs || iters < 1 || (out_parity & ~1) ||
-        (prec != DP_PREC_FP64 && prec != DP_PREC_MIXED_FP32) ||
-        rhs_per_thread < -1 ||
+        prec < DP_PREC_FP64 || prec > DP_PREC_MIXED_BF16 ||
+        rhs_per_thread < 0 ||
         (block_threads != 0 && (block_threads < 32 || block_threads > 256 || block_threads % 32))) {
         set_error("dp_dslash_dev: invalid argument");
         return DP_ERR_INVALID_ARG;
     }
-    // ABI: -1 = shared-memory staged kernel, internally rpt 0
-    const int want_rpt = rhs_per_thread == -1 ? 0 : rhs_per_thread;
+    const int want_rpt = rhs_per_thread;
     if (rhs_per_thread != 0 &&
-        (!dslash_rpt_ok(nrhs, want_rpt, prec == DP_PREC_FP64 ? 0 : 1, EPI_AINV) ||
-         (want_rpt == 0 && !compress12))) {
+        !dslash_rpt_ok(nrhs, want_rpt, prec == DP_PREC_FP64 ? 0 : 1, EPI_AINV)) {
         set_error("dp_dslash_dev: launch shape %d is not available for %d RHS in this precision",
                   rhs_per_thread, nrhs);
         return DP_ERR_INVALID_ARG;
     }
     const Geom &g = f.g;
     const int pr = prec == DP_PREC_FP64 ? 0 : 1;
-    const int lf = pr == 0 ? LINK_F64_18 : (compress12 ? LINK_F32_12 : LINK_F32_18);
+    const int lf = inner_link_format(prec, compress12);
+    const void *links[2];
+    for (int p = 0; p < 2; p++) {
+        dp_status s2 = field_links(&c, f, lf, p, &links[p]);
+        if (s2 != DP_OK) return s2;
+    }
     std::shared_ptr<CloverInv> ci;
     dp_status stt = get_clover_inv(&c, f, M, &ci);
     if (stt != DP_OK) return stt;
@@ -704,8 +760,8 @@ dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile 
     DslashParams P{};
     P.in = in;
     P.out = out;
-    P.links[0] = pr == 0 ? (const void *)f.l64[0] : (compress12 ? (const void *)f.l32c[0] : (const void *)f.l32f[0]);
-    P.links[1] = pr == 0 ? (const void *)f.l64[1] : (compress12 ? (const void *)f.l32c[1] : (const void *)f.l32f[1]);
+    P.links[0] = links[0];
+    P.links[1] = links[1];
     P.clov[0] = pr == 0 ? (const void *)ci->inv64[out_parity] : (const void *)ci->inv32[out_parity];
     P.hop = hopd;
     P.g = g;
@@ -740,13 +796,13 @@ dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int
         set_error("unknown field");
         return DP_ERR_NOT_FOUND;
     }
-    if (nrhs < 1 || nrhs > kMaxRhs || (prec != DP_PREC_FP64 && prec != DP_PREC_MIXED_FP32)) {
+    if (nrhs < 1 || nrhs > kMaxRhs || prec < DP_PREC_FP64 || prec > DP_PREC_MIXED_BF16) {
         set_error("dp_autotune: invalid argument");
         return DP_ERR_INVALID_ARG;
     }
     const Geom &g = fp->g;
     const int pr = prec == DP_PREC_FP64 ? 0 : 1;
-    const int lf = pr == 0 ? LINK_F64_18 : (compress12 ? LINK_F32_12 : LINK_F32_18);
+    const int lf = inner_link_format(prec, compress12);
     const size_t vb = dp_spinor_bytes(ctx, field, prec, nrhs);
     void *in = c.alloc(vb), *out = c.alloc(vb);
     if (!in || !out) {
@@ -756,18 +812,17 @@ dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int
         return DP_ERR_OOM;
     }
     cudaMemsetAsync(in, 0, vb, c.stream);
-    // candidates: the register kernel with 1-4 RHS per thread and four block
-    // sizes, and the shared-memory staged kernel (rpt 0; FP32 12-real links)
+    // candidates: four block sizes x RHS per thread (FP64: 1; FP32: one or
+    // two RHS pairs)
     const int blocks[] = {64, 128, 192, 256};
-    const int rpts[] = {0, 1, 2, 3, 4};
+    const int rpts[] = {1, 2, 4};
     int best = 0, best_rpt = 1;
     float bms = 1e30f;
     dp_status st = DP_OK;
     for (int r : rpts) {
-        if (!dslash_rpt_ok(nrhs, r, pr, EPI_AINV) || (r == 0 && lf != LINK_F32_12)) continue;
+        if (!dslash_rpt_ok(nrhs, r, pr, EPI_AINV)) continue;
         for (int b : blocks) {
-            if (r == 0 && b != blocks[0]) continue;  // the staged kernel fixes its block
-            const int abi_rpt = r == 0 ? -1 : r;
+            const int abi_rpt = r;
             float ms = 0;
             // warm up once, then time a few launches
             st = dp_dslash_dev(ctx, field, 0.1, nullptr, prec, compress12, 0, in, out, nrhs, b,
@@ -792,7 +847,7 @@ dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int
         c.tuned[TuneKey{g.Vh, pr, lf, nrhs}] = {best, best_rpt};
     }
     if (best_block_threads) *best_block_threads = best;
-    if (best_rhs_per_thread) *best_rhs_per_thread = best_rpt == 0 ? -1 : best_rpt;
+    if (best_rhs_per_thread) *best_rhs_per_thread = best_rpt;
     if (best_ms) *best_ms = bms;
     return DP_OK;
 }

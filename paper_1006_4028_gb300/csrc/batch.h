@@ -30,6 +30,7 @@ struct Op {
     const Field *f = nullptr;
     int pr = 0;  // 0 FP64, 1 FP32
     int lf = 0;  // link format
+    const void *links[2] = {nullptr, nullptr};  // per parity, in format lf
     const void *hop = nullptr;
     const void *inv[2][kMaxGroups] = {};
     int8_t grp_of[kMaxRhs] = {};
@@ -63,6 +64,8 @@ class Batch {
     // finish jobs whose RHS are all done: odd sites, residual, restore, C_PP
     dp_status harvest(std::vector<Job *> &finished);
     int active_jobs() const;
+    // at most this many jobs at once (0: as many as the slots hold)
+    void set_max_jobs(int m) { max_jobs = m; }
     size_t bytes() const { return total_bytes; }
     const std::shared_ptr<Field> &field() const { return f; }
 
@@ -70,6 +73,7 @@ class Batch {
     void *get(size_t bytes);
     dp_status upload_mask(const std::vector<int> &m);
     dp_status bicgstab(int max_iter, int *iters_done);
+    dp_status cgne(int max_iter, int *iters_done);
 
     Ctx *c;
     std::shared_ptr<Field> f;
@@ -77,6 +81,7 @@ class Batch {
     dp_solve_opts opts;
     int round_iters;
     int sp = 0;
+    int max_jobs = 0;
     int mixed = 1, ipr = 1, ilf = LINK_F32_12;
     int check_every = 4;
     size_t v64 = 0, vin = 0, total_bytes = 0;
@@ -85,12 +90,12 @@ class Batch {
             *t64 = nullptr;
     InnerVecs in;
     RhsState *outer = nullptr, *inner = nullptr;
-    double *alpha_d = nullptr, *hop64_d = nullptr;
-    float *hop32_d = nullptr;
+    double *alpha_d = nullptr, *hop64_d = nullptr, *hopadj64_d = nullptr;
+    float *hop32_d = nullptr, *hopadj32_d = nullptr;  // adj: the reciprocal profile (CGNE)
     SlotInfo *slots_d = nullptr;
     int *tsrc_d = nullptr, *mask_d = nullptr;
     double *cpp_d = nullptr, *cpart = nullptr, *nrm_d = nullptr;
-    Op op64, opin;
+    Op op64, opin, opin_adj;
     cudaGraphExec_t graph = nullptr;
     int graph_max_iter = 0;
     Job *jobs[kMaxGroups] = {};

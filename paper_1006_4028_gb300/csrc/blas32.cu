@@ -1,0 +1,513 @@
+// FP32 inner-solver BLAS-1 kernels on the paired layout of pair.cuh: one
+// thread per (site, RHS pair), every update one packed f32x2 instruction for
+// the two RHS, per-RHS scalars (alpha, omega, beta) held per lane.  Dot
+// products are formed per site in FP32 (24 terms) and accumulated across
+// sites in FP64 per RHS; the reductions and scalar recurrences are those of
+// the FP64 kernels (reduce.cuh), so every decision stays per RHS.
+//
+// A pair is processed while either of its RHS is active; an inactive lane's
+// solution x is never changed (lane blend), and its terms are excluded from
+// every reduction.  Other vectors of an inactive lane are scratch.
+#include "cplx.cuh"
+#include "dp_internal.h"
+#include "pair.cuh"
+#include "reduce.cuh"
+
+namespace dp {
+namespace {
+
+struct P12 {
+    C2 c[12];
+};
+
+__device__ __forceinline__ P12 ldp(const void *base, long long cs, long long me)
+{
+    P12 v;
+    load_pair(static_cast<const float4 *>(base) + me, cs, v.c);
+    return v;
+}
+__device__ __forceinline__ void stp(void *base, long long cs, long long me, const P12 &v)
+{
+    store_pair(static_cast<float4 *>(base) + me, cs, v.c);
+}
+
+// component k of one pair
+__device__ __forceinline__ C2 ld1(const void *base, long long cs, long long me, int k)
+{
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(base) + me + k * cs);
+    return {v.x, v.y};
+}
+__device__ __forceinline__ void st1(void *base, long long cs, long long me, int k, C2 v)
+{
+    reinterpret_cast<ulonglong2 *>(base)[me + k * cs] = make_ulonglong2(v.re, v.im);
+}
+
+// per-lane complex scalar from the two RHS states
+__device__ __forceinline__ C2 lanes(double2 a0, double2 a1)
+{
+    return {pk((float)a0.x, (float)a1.x), pk((float)a0.y, (float)a1.y)};
+}
+__device__ __forceinline__ C2 neg(C2 a) { return {fneg2(a.re), fneg2(a.im)}; }
+
+// <a, b> per lane over one site, FP32
+__device__ __forceinline__ C2 pdot(const P12 &a, const P12 &b)
+{
+    f2 re = 0ull, im = 0ull;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        re = ffma2(a.c[k].re, b.c[k].re, re);
+        re = ffma2(a.c[k].im, b.c[k].im, re);
+        im = ffma2(a.c[k].re, b.c[k].im, im);
+        im = ffma2(fneg2(a.c[k].im), b.c[k].re, im);
+    }
+    return {re, im};
+}
+__device__ __forceinline__ f2 pnorm(const P12 &a)
+{
+    f2 s = 0ull;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        s = ffma2(a.c[k].re, a.c[k].re, s);
+        s = ffma2(a.c[k].im, a.c[k].im, s);
+    }
+    return s;
+}
+
+// add the two lanes of an f2 into FP64 accumulators, only for active lanes
+__device__ __forceinline__ void add_lanes(double &d0, double &d1, f2 v, bool a0, bool a1)
+{
+    float l0, l1;
+    upk(v, l0, l1);
+    if (a0) d0 += (double)l0;
+    if (a1) d1 += (double)l1;
+}
+
+#define PAIR_LOOP                                                              \
+    const int P = nrhs / 2;                                                    \
+    const int q = threadIdx.x % P, lane = threadIdx.x / P;                     \
+    const long long cs = Vh * P;                                               \
+    const bool a0 = st[2 * q].active != 0, a1 = st[2 * q + 1].active != 0;     \
+    for (long long s = (long long)blockIdx.x * c.lanes + lane; (a0 || a1) && s < Vh; \
+         s += (long long)gridDim.x * c.lanes)
+
+__global__ void __launch_bounds__(kMaxBlock) k32_p(Cfg c, const void *rv, void *pv, const void *vv, long long Vh, int nrhs,
+                      const RhsState *st, int first)
+{
+    const int qq = threadIdx.x % (nrhs / 2);
+    const C2 be = lanes(st[2 * qq].beta, st[2 * qq + 1].beta);
+    const C2 mom = neg(lanes(st[2 * qq].omega, st[2 * qq + 1].omega));
+    PAIR_LOOP
+    {
+        const long long me = s * P + q;
+        P12 r = ldp(rv, cs, me);
+        if (first) {
+            stp(pv, cs, me, r);
+            continue;
+        }
+        P12 p = ldp(pv, cs, me), v = ldp(vv, cs, me);
+#pragma unroll
+        for (int k = 0; k < 12; k++) p.c[k] = c2_lanefma(be, c2_lanefma(mom, v.c[k], p.c[k]), r.c[k]);
+        stp(pv, cs, me, p);
+    }
+}
+
+__global__ void __launch_bounds__(kMaxBlock) k32_alpha(Cfg c, const void *rh, const void *vv, long long Vh, int nrhs,
+                          RhsState *st, double *partials, unsigned int *counter)
+{
+    double acc[4] = {0, 0, 0, 0};  // lane 0: re, im; lane 1: re, im
+    {
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            const C2 d = pdot(ldp(rh, cs, me), ldp(vv, cs, me));
+            add_lanes(acc[0], acc[2], d.re, a0, a1);
+            add_lanes(acc[1], acc[3], d.im, a0, a1);
+        }
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<2, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    finish_alpha(st[2 * q], acc[0], acc[1]);
+    finish_alpha(st[2 * q + 1], acc[2], acc[3]);
+}
+
+__global__ void __launch_bounds__(kMaxBlock) k32_s(Cfg c, const void *rv, const void *vv, void *sv, long long Vh, int nrhs,
+                      const RhsState *st)
+{
+    const int qq = threadIdx.x % (nrhs / 2);
+    const C2 mal = neg(lanes(st[2 * qq].alpha, st[2 * qq + 1].alpha));
+    PAIR_LOOP
+    {
+        const long long me = s * P + q;
+        P12 r = ldp(rv, cs, me), v = ldp(vv, cs, me);
+#pragma unroll
+        for (int k = 0; k < 12; k++) r.c[k] = c2_lanefma(mal, v.c[k], r.c[k]);
+        stp(sv, cs, me, r);
+    }
+}
+
+__global__ void __launch_bounds__(kMaxBlock) k32_omega(Cfg c, const void *tv, const void *sv, long long Vh, int nrhs,
+                          RhsState *st, double *partials, unsigned int *counter)
+{
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    {
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            const P12 t = ldp(tv, cs, me), sx = ldp(sv, cs, me);
+            const C2 d = pdot(t, sx);
+            add_lanes(acc[0], acc[3], d.re, a0, a1);
+            add_lanes(acc[1], acc[4], d.im, a0, a1);
+            add_lanes(acc[2], acc[5], pnorm(t), a0, a1);
+        }
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<3, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    finish_omega(st[2 * q], acc[0], acc[1], acc[2]);
+    finish_omega(st[2 * q + 1], acc[3], acc[4], acc[5]);
+}
+
+// keep the lanes of `old` whose RHS is inactive
+__device__ __forceinline__ f2 blend(f2 nw, f2 old, f2 m) { return (nw & m) | (old & ~m); }
+
+// one component at a time: five streams in, two out, few live registers
+__global__ void __launch_bounds__(kMaxBlock)
+k32_update(Cfg c, void *xv, void *rv, const void *pv, const void *sv, const void *tv,
+           const void *rh, long long Vh, int nrhs, RhsState *st, int max_iter, double *partials,
+           unsigned int *counter)
+{
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    {
+        const int qq = threadIdx.x % (nrhs / 2);
+        const C2 al = lanes(st[2 * qq].alpha, st[2 * qq + 1].alpha);
+        const C2 om = lanes(st[2 * qq].omega, st[2 * qq + 1].omega);
+        const C2 mom = neg(om);
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            const f2 m = (a0 ? 0x00000000ffffffffull : 0ull) | (a1 ? 0xffffffff00000000ull : 0ull);
+            f2 dre = 0ull, dim = 0ull, nn = 0ull;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                const C2 x = ld1(xv, cs, me, k), p = ld1(pv, cs, me, k), sx = ld1(sv, cs, me, k);
+                const C2 t = ld1(tv, cs, me, k), h = ld1(rh, cs, me, k);
+                C2 xn = c2_lanefma(om, sx, c2_lanefma(al, p, x));
+                xn.re = blend(xn.re, x.re, m);
+                xn.im = blend(xn.im, x.im, m);
+                st1(xv, cs, me, k, xn);
+                const C2 r = c2_lanefma(mom, t, sx);
+                st1(rv, cs, me, k, r);
+                dre = ffma2(h.re, r.re, dre);
+                dre = ffma2(h.im, r.im, dre);
+                dim = ffma2(h.re, r.im, dim);
+                dim = ffma2(fneg2(h.im), r.re, dim);
+                nn = ffma2(r.re, r.re, nn);
+                nn = ffma2(r.im, r.im, nn);
+            }
+            add_lanes(acc[0], acc[3], dre, a0, a1);
+            add_lanes(acc[1], acc[4], dim, a0, a1);
+            add_lanes(acc[2], acc[5], nn, a0, a1);
+        }
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<3, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    finish_update(st[2 * q], acc[0], acc[1], acc[2], max_iter);
+    finish_update(st[2 * q + 1], acc[3], acc[4], acc[5], max_iter);
+}
+
+__global__ void __launch_bounds__(kMaxBlock) k32_init(Cfg c, const void *bv, void *rv, void *rh, long long Vh, int nrhs,
+                         RhsState *st, double *partials, unsigned int *counter)
+{
+    double acc[2] = {0, 0};
+    {
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            const P12 b = ldp(bv, cs, me);
+            stp(rv, cs, me, b);
+            stp(rh, cs, me, b);
+            add_lanes(acc[0], acc[1], pnorm(b), a0, a1);
+        }
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    finish_init(st[2 * q], acc[0]);
+    finish_init(st[2 * q + 1], acc[1]);
+}
+
+// ---- CGNE on the normal equations: real per-RHS scalars, per lane ----
+
+__device__ __forceinline__ f2 lanes_re(double a0, double a1) { return pk((float)a0, (float)a1); }
+
+__global__ void __launch_bounds__(kMaxBlock)
+k32_cg_gamma(Cfg c, const void *zv, long long Vh, int nrhs, RhsState *st, int first,
+             double *partials, unsigned int *counter)
+{
+    double acc[2] = {0, 0};
+    {
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            f2 nn = 0ull;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                const C2 z = ld1(zv, cs, me, k);
+                nn = ffma2(z.re, z.re, nn);
+                nn = ffma2(z.im, z.im, nn);
+            }
+            add_lanes(acc[0], acc[1], nn, a0, a1);
+        }
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    finish_cg_gamma(st[2 * q], acc[0], first);
+    finish_cg_gamma(st[2 * q + 1], acc[1], first);
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(kMaxBlock)
+k32_cg_p(Cfg c, const void *zv, void *pv, long long Vh, int nrhs, const RhsState *st)
+{
+    const int qq = threadIdx.x % (nrhs / 2);
+    const f2 be = lanes_re(st[2 * qq].beta.x, st[2 * qq + 1].beta.x);
+    PAIR_LOOP
+    {
+        const long long me = s * P + q;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            const C2 z = ld1(zv, cs, me, k);
+            C2 p = ld1(pv, cs, me, k);
+            p.re = ffma2(be, p.re, z.re);
+            p.im = ffma2(be, p.im, z.im);
+            st1(pv, cs, me, k, p);
+        }
+    }
+}
+
+// alpha = rho / |w|^2
+__global__ void __launch_bounds__(kMaxBlock)
+k32_cg_alpha(Cfg c, const void *wv, long long Vh, int nrhs, RhsState *st, double *partials,
+             unsigned int *counter)
+{
+    double acc[2] = {0, 0};
+    {
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            f2 nn = 0ull;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                const C2 w = ld1(wv, cs, me, k);
+                nn = ffma2(w.re, w.re, nn);
+                nn = ffma2(w.im, w.im, nn);
+            }
+            add_lanes(acc[0], acc[1], nn, a0, a1);
+        }
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    finish_cg_alpha(st[2 * q], acc[0]);
+    finish_cg_alpha(st[2 * q + 1], acc[1]);
+}
+
+// x += alpha p (active lanes only), r -= alpha w, |r|^2
+__global__ void __launch_bounds__(kMaxBlock)
+k32_cg_update(Cfg c, void *xv, void *rv, const void *pv, const void *wv, long long Vh, int nrhs,
+              RhsState *st, int max_iter, double *partials, unsigned int *counter)
+{
+    double acc[2] = {0, 0};
+    {
+        const int qq = threadIdx.x % (nrhs / 2);
+        const f2 al = lanes_re(st[2 * qq].alpha.x, st[2 * qq + 1].alpha.x);
+        const f2 mal = fneg2(al);
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            const f2 m = (a0 ? 0x00000000ffffffffull : 0ull) | (a1 ? 0xffffffff00000000ull : 0ull);
+            f2 nn = 0ull;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                const C2 x = ld1(xv, cs, me, k), p = ld1(pv, cs, me, k);
+                C2 xn = {ffma2(al, p.re, x.re), ffma2(al, p.im, x.im)};
+                xn.re = blend(xn.re, x.re, m);
+                xn.im = blend(xn.im, x.im, m);
+                st1(xv, cs, me, k, xn);
+                C2 r = ld1(rv, cs, me, k);
+                const C2 w = ld1(wv, cs, me, k);
+                r.re = ffma2(mal, w.re, r.re);
+                r.im = ffma2(mal, w.im, r.im);
+                st1(rv, cs, me, k, r);
+                nn = ffma2(r.re, r.re, nn);
+                nn = ffma2(r.im, r.im, nn);
+            }
+            add_lanes(acc[0], acc[1], nn, a0, a1);
+        }
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    finish_cg_update(st[2 * q], acc[0], max_iter);
+    finish_cg_update(st[2 * q + 1], acc[1], max_iter);
+}
+
+// r32 (paired) = r64 / |r| per RHS (zero for inactive RHS)
+__global__ void k32_from64(const double2 *r64, float4 *r32, long long Vh, int n, const RhsState *st)
+{
+    const int P = n / 2;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= Vh * P) return;
+    const long long s = gid / P;
+    const int q = (int)(gid - s * P);
+    const double i0 = st[2 * q].active ? 1.0 / st[2 * q].scale : 0.0;
+    const double i1 = st[2 * q + 1].active ? 1.0 / st[2 * q + 1].scale : 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        const long long b64 = ((long long)k * Vh + s) * n + 2 * q;
+        const double2 u = r64[b64], v = r64[b64 + 1];
+        r32[((long long)k * Vh + s) * P + q] =
+            make_float4((float)(u.x * i0), (float)(v.x * i1), (float)(u.y * i0), (float)(v.y * i1));
+    }
+}
+
+// x64 += |r| e32 per active RHS
+__global__ void k32_acc64(double2 *x64, const float4 *e32, long long Vh, int n, const RhsState *st)
+{
+    const int P = n / 2;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= Vh * P) return;
+    const long long s = gid / P;
+    const int q = (int)(gid - s * P);
+    const bool a0 = st[2 * q].active != 0, a1 = st[2 * q + 1].active != 0;
+    if (!a0 && !a1) return;
+    const double s0 = st[2 * q].scale, s1 = st[2 * q + 1].scale;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        const float4 e = e32[((long long)k * Vh + s) * P + q];
+        const long long b64 = ((long long)k * Vh + s) * n + 2 * q;
+        if (a0) {
+            double2 x = x64[b64];
+            x.x = fmx(s0, (double)e.x, x.x);
+            x.y = fmx(s0, (double)e.z, x.y);
+            x64[b64] = x;
+        }
+        if (a1) {
+            double2 x = x64[b64 + 1];
+            x.x = fmx(s1, (double)e.y, x.x);
+            x.y = fmx(s1, (double)e.w, x.y);
+            x64[b64 + 1] = x;
+        }
+    }
+}
+
+inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t blas32_init(BlasCtx &bc, const void *b, void *r, void *rh, long long Vh, int nrhs,
+                        RhsState *st, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_init, Vh, nrhs / 2);
+    k32_init<<<c.grid, c.block, 0, s>>>(c, b, r, rh, Vh, nrhs, st, bc.partials, bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_p(BlasCtx &bc, const void *r, void *p, const void *v, long long Vh, int nrhs,
+                     const RhsState *st, int first, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_p, Vh, nrhs / 2);
+    k32_p<<<c.grid, c.block, 0, s>>>(c, r, p, v, Vh, nrhs, st, first);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_alpha(BlasCtx &bc, const void *rh, const void *v, long long Vh, int nrhs,
+                         RhsState *st, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_alpha, Vh, nrhs / 2);
+    k32_alpha<<<c.grid, c.block, 0, s>>>(c, rh, v, Vh, nrhs, st, bc.partials, bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_s(BlasCtx &bc, const void *r, const void *v, void *sv, long long Vh, int nrhs,
+                     const RhsState *st, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_s, Vh, nrhs / 2);
+    k32_s<<<c.grid, c.block, 0, s>>>(c, r, v, sv, Vh, nrhs, st);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_omega(BlasCtx &bc, const void *t, const void *sv, long long Vh, int nrhs,
+                         RhsState *st, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_omega, Vh, nrhs / 2);
+    k32_omega<<<c.grid, c.block, 0, s>>>(c, t, sv, Vh, nrhs, st, bc.partials, bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_update(BlasCtx &bc, void *x, void *r, const void *p, const void *sv,
+                          const void *t, const void *rh, long long Vh, int nrhs, RhsState *st,
+                          int max_iter, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_update, Vh, nrhs / 2);
+    k32_update<<<c.grid, c.block, 0, s>>>(c, x, r, p, sv, t, rh, Vh, nrhs, st, max_iter,
+                                          bc.partials, bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_cg_gamma(BlasCtx &bc, const void *z, long long Vh, int nrhs, RhsState *st,
+                            int first, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_cg_gamma, Vh, nrhs / 2);
+    k32_cg_gamma<<<c.grid, c.block, 0, s>>>(c, z, Vh, nrhs, st, first, bc.partials, bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_cg_p(BlasCtx &bc, const void *z, void *p, long long Vh, int nrhs,
+                        const RhsState *st, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_cg_p, Vh, nrhs / 2);
+    k32_cg_p<<<c.grid, c.block, 0, s>>>(c, z, p, Vh, nrhs, st);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_cg_alpha(BlasCtx &bc, const void *w, long long Vh, int nrhs, RhsState *st,
+                            cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_cg_alpha, Vh, nrhs / 2);
+    k32_cg_alpha<<<c.grid, c.block, 0, s>>>(c, w, Vh, nrhs, st, bc.partials, bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_cg_update(BlasCtx &bc, void *x, void *r, const void *p, const void *w,
+                             long long Vh, int nrhs, RhsState *st, int max_iter, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_cg_update, Vh, nrhs / 2);
+    k32_cg_update<<<c.grid, c.block, 0, s>>>(c, x, r, p, w, Vh, nrhs, st, max_iter, bc.partials,
+                                             bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas_to_f32_scaled(const double2 *r64, float4 *r32, long long Vh, int nrhs,
+                               const RhsState *st, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    k32_from64<<<blocks_for(Vh * (nrhs / 2), 256), 256, 0, s>>>(r64, r32, Vh, nrhs, st);
+    return cudaGetLastError();
+}
+
+cudaError_t blas_acc_f32(double2 *x64, const float4 *e32, long long Vh, int nrhs,
+                         const RhsState *st, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    k32_acc64<<<blocks_for(Vh * (nrhs / 2), 256), 256, 0, s>>>(x64, e32, Vh, nrhs, st);
+    return cudaGetLastError();
+}
+
+}  // namespace dp

@@ -12,6 +12,7 @@
 // Hermitian matrix [[Z_3, Z_1 - i Z_2], [Z_1 + i Z_2, -Z_3]].
 #include "cplx.cuh"
 #include "dp_internal.h"
+#include "pair.cuh"
 
 namespace dp {
 namespace {
@@ -257,29 +258,61 @@ __global__ void k_clover_invert(const double2 *cl, long long Vh, double diag, do
 }
 
 // out = (diag_g + C_g) in with the packed clover matrix of the RHS's group
-template <typename R>
-__global__ void k_clover_apply(const CloverApplyParams p)
+// (FP64 spinors, one thread per (site, RHS))
+__global__ void k_clover_apply64(const CloverApplyParams p)
 {
-    using CT = typename Chunk<R>::T;
     const int n = p.nrhs;
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long s = gid / n;
     if (s >= p.Vh) return;
     const int r = (int)(gid - s * n);
-    if (p.mask && !p.mask[r]) return;
+    const int ms = p.mask_stride > 1 ? p.mask_stride : 1;
+    if (p.mask && !p.mask[r * ms]) return;
     const int grp = p.grp_of[r];
     const long long cs = p.Vh * n;
-    Cx<R> v[12], w[12];
-    load_spinor(static_cast<const CT *>(p.in) + gid, cs, v);
+    Cx<double> v[12], w[12];
+    load_spinor(static_cast<const double2 *>(p.in) + gid, cs, v);
 #pragma unroll
     for (int blk = 0; blk < 2; blk++) {
-        R m[36];
-        load_clover_block(static_cast<const CT *>(p.mat[grp]), p.Vh, s, blk, m);
+        double m[36];
+        load_clover_block(static_cast<const double2 *>(p.mat[grp]), p.Vh, s, blk, m);
 #pragma unroll
-        for (int i = 0; i < 6; i++) m[i] += (R)p.diag[grp];
+        for (int i = 0; i < 6; i++) m[i] += p.diag[grp];
         herm6_apply(m, v + 6 * blk, w + 6 * blk);
     }
-    store_spinor(static_cast<CT *>(p.out) + gid, cs, w);
+    if (p.g5)
+#pragma unroll
+        for (int j = 6; j < 12; j++) w[j] = -w[j];
+    store_spinor(static_cast<double2 *>(p.out) + gid, cs, w);
+}
+
+// FP32 spinors on the paired layout, one thread per (site, RHS pair); the
+// two RHS of a pair share their group (pairs never straddle a 12-RHS group)
+__global__ void k_clover_apply32(const CloverApplyParams p)
+{
+    const int P = p.nrhs / 2;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long s = gid / P;
+    if (s >= p.Vh) return;
+    const int q = (int)(gid - s * P);
+    const int ms = p.mask_stride > 1 ? p.mask_stride : 1;
+    if (p.mask && !p.mask[2 * q * ms] && !p.mask[(2 * q + 1) * ms]) return;
+    const int grp = p.grp_of[2 * q];
+    const long long cs = p.Vh * P;
+    C2 v[12], w[12];
+    load_pair(static_cast<const float4 *>(p.in) + gid, cs, v);
+#pragma unroll
+    for (int blk = 0; blk < 2; blk++) {
+        float m[36];
+        load_clover_block(static_cast<const float4 *>(p.mat[grp]), p.Vh, s, blk, m);
+#pragma unroll
+        for (int i = 0; i < 6; i++) m[i] += (float)p.diag[grp];
+        herm6_pair(m, v + 6 * blk, w + 6 * blk);
+    }
+    if (p.g5)
+#pragma unroll
+        for (int j = 6; j < 12; j++) w[j] = {fneg2(w[j].re), fneg2(w[j].im)};
+    store_pair(static_cast<float4 *>(p.out) + gid, cs, w);
 }
 
 // FP64 [36 double2][Vh] -> FP32 [18 float4][Vh], same order of the 72 reals
@@ -327,11 +360,14 @@ cudaError_t launch_clover_invert(const double2 *clov, long long Vh, double M, do
 cudaError_t launch_clover_apply(const CloverApplyParams &p, int prec, cudaStream_t st)
 {
     const int block = 128;
-    const unsigned grid = (unsigned)((p.Vh * p.nrhs + block - 1) / block);
-    if (prec == 0)
-        k_clover_apply<double><<<grid, block, 0, st>>>(p);
-    else
-        k_clover_apply<float><<<grid, block, 0, st>>>(p);
+    if (prec == 0) {
+        const unsigned grid = (unsigned)((p.Vh * p.nrhs + block - 1) / block);
+        k_clover_apply64<<<grid, block, 0, st>>>(p);
+    } else {
+        if (p.nrhs % 2) return cudaErrorInvalidValue;
+        const unsigned grid = (unsigned)((p.Vh * (p.nrhs / 2) + block - 1) / block);
+        k_clover_apply32<<<grid, block, 0, st>>>(p);
+    }
     return cudaGetLastError();
 }
 

@@ -2,6 +2,8 @@
 // kernels.  Layouts are described in dp_internal.h.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "dp_internal.h"
@@ -163,6 +165,62 @@ __device__ __forceinline__ void load_link<LINK_F32_12, float>(const void *base, 
     u[6] = {a.re, -a.im};
     u[7] = {b.re, -b.im};
     u[8] = {c.re, -c.im};
+}
+
+// 16-bit storage: rows 0 and 1 in FP16 / BF16 times one FP32 scale per link,
+// row 2 rebuilt as above
+template <typename H2>
+__device__ __forceinline__ float2 h2f(unsigned v);
+template <>
+__device__ __forceinline__ float2 h2f<__half2>(unsigned v)
+{
+    __half2 h;
+    memcpy(&h, &v, 4);
+    return __half22float2(h);
+}
+template <>
+__device__ __forceinline__ float2 h2f<__nv_bfloat162>(unsigned v)
+{
+    __nv_bfloat162 h;
+    memcpy(&h, &v, 4);
+    return __bfloat1622float2(h);
+}
+
+template <typename H2>
+__device__ __forceinline__ void load_link16(const void *base, long long Vh, long long site, int mu,
+                                            Cx<float> u[9])
+{
+    const uint2 *l = static_cast<const uint2 *>(base) + (long long)mu * 3 * Vh + site;
+    const float sc = __ldg(reinterpret_cast<const float *>(static_cast<const uint2 *>(base) + 12 * Vh) +
+                           (long long)mu * Vh + site);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const uint2 v = __ldg(l + k * Vh);
+        const float2 a = h2f<H2>(v.x), b = h2f<H2>(v.y);
+        u[2 * k] = {sc * a.x, sc * a.y};
+        u[2 * k + 1] = {sc * b.x, sc * b.y};
+    }
+    Cx<float> a = cmul(u[1], u[5]) - cmul(u[2], u[4]);
+    Cx<float> b = cmul(u[2], u[3]) - cmul(u[0], u[5]);
+    Cx<float> c = cmul(u[0], u[4]) - cmul(u[1], u[3]);
+    u[6] = {a.re, -a.im};
+    u[7] = {b.re, -b.im};
+    u[8] = {c.re, -c.im};
+}
+
+template <>
+__device__ __forceinline__ void load_link<LINK_H16_12, float>(const void *base, long long Vh,
+                                                             long long site, int mu,
+                                                             Cx<float> u[9])
+{
+    load_link16<__half2>(base, Vh, site, mu, u);
+}
+template <>
+__device__ __forceinline__ void load_link<LINK_B16_12, float>(const void *base, long long Vh,
+                                                             long long site, int mu,
+                                                             Cx<float> u[9])
+{
+    load_link16<__nv_bfloat162>(base, Vh, site, mu, u);
 }
 
 // ---- clover blocks ------------------------------------------------------------

@@ -39,6 +39,7 @@ struct Field {
     double2 *l64[2] = {nullptr, nullptr};
     float2 *l32f[2] = {nullptr, nullptr};
     float4 *l32c[2] = {nullptr, nullptr};
+    void *l16[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [FP16, BF16][parity], lazily
     double2 *clov[2] = {nullptr, nullptr};  // clover term, FP64 (no mass)
     float4 *clov32[2] = {nullptr, nullptr}; // clover term, FP32 copy
     bool has_clover = false;
@@ -121,6 +122,10 @@ struct Ctx {
 };
 
 std::shared_ptr<Field> find_field(Ctx *c, dp_field f);
+// device links of one parity in a storage format (16-bit ones built on first use)
+dp_status field_links(Ctx *c, Field &f, int link_fmt, int parity, const void **out);
+// link format of the inner solver for a precision and compress12 choice
+int inner_link_format(int prec, int compress12);
 // clover inverse of (4+M) + clover for both parities, cached per mass
 dp_status get_clover_inv(Ctx *c, Field &f, double M, std::shared_ptr<CloverInv> *out);
 // FP64 alpha_B tables [4][Lmax] and hop tables [4][2][Lmax] (with the -1/2)

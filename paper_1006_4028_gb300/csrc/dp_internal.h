@@ -34,10 +34,19 @@ enum Epi {
     EPI_AINV = 1,     // out = A^-1 D in
     EPI_XMY_AINV = 2, // out = x - A^-1 D in
     EPI_AINV_XMY = 3, // out = A^-1 (x - D in)
-    EPI_XPY = 4       // out = x + D in
+    EPI_XPY = 4,      // out = x + D in
+    EPI_XMY_G5 = 5    // out = x - gamma5 D in (last step of the adjoint Schur operator)
 };
 
-enum LinkFmt { LINK_F64_18 = 0, LINK_F32_18 = 1, LINK_F32_12 = 2 };
+// link storage formats; the 16-bit ones hold rows 0 and 1 as FP16 or BF16
+// values divided by one FP32 scale per link (max |element| of the two rows):
+// [mu][3][s] uint2 (four 16-bit values each), then [mu][s] float scales
+enum LinkFmt { LINK_F64_18 = 0, LINK_F32_18 = 1, LINK_F32_12 = 2, LINK_H16_12 = 3, LINK_B16_12 = 4 };
+
+// quantise FP64 links of one parity ([mu][9 double2][Vh]) into a 16-bit format
+cudaError_t launch_pack_links16(const double2 *l64, long long Vh, int fmt, void *out,
+                                cudaStream_t st);
+inline size_t links16_bytes(long long Vh) { return (size_t)Vh * 4 * (3 * 8 + 4); }
 
 constexpr int kMaxGroups = 8;  // point-source groups (12 RHS each) per batch
 
@@ -91,7 +100,9 @@ struct CloverApplyParams {
     const void *mat[kMaxGroups];
     double diag[kMaxGroups];
     int8_t grp_of[kMaxRhs];
-    const int *mask;  // NULL or per-RHS flags: RHS with mask[r] == 0 are skipped
+    const int *mask;  // NULL or per-RHS flags: RHS with mask[r * stride] == 0 are skipped
+    int mask_stride;  // 0 or 1: consecutive ints; else the stride in ints (RhsState rows)
+    int g5;           // 1: out = gamma5 (mat + diag) in (sign flip of chiral block 1)
     const void *in;
     void *out;        // may alias `in`
     long long Vh;
@@ -158,6 +169,42 @@ cudaError_t blas_bicg_omega(BlasCtx &bc, int prec, const void *t, const void *sv
 cudaError_t blas_bicg_update(BlasCtx &bc, int prec, void *x, void *r, const void *p,
                              const void *sv, const void *t, const void *rhat, long long Vh,
                              int nrhs, RhsState *st, int max_iter, cudaStream_t s);
+// FP32 inner solver on the paired layout (blas32.cu); nrhs even
+cudaError_t blas32_init(BlasCtx &bc, const void *b, void *r, void *rh, long long Vh, int nrhs,
+                        RhsState *st, cudaStream_t s);
+cudaError_t blas32_p(BlasCtx &bc, const void *r, void *p, const void *v, long long Vh, int nrhs,
+                     const RhsState *st, int first, cudaStream_t s);
+cudaError_t blas32_alpha(BlasCtx &bc, const void *rh, const void *v, long long Vh, int nrhs,
+                         RhsState *st, cudaStream_t s);
+cudaError_t blas32_s(BlasCtx &bc, const void *r, const void *v, void *sv, long long Vh, int nrhs,
+                     const RhsState *st, cudaStream_t s);
+cudaError_t blas32_omega(BlasCtx &bc, const void *t, const void *sv, long long Vh, int nrhs,
+                         RhsState *st, cudaStream_t s);
+cudaError_t blas32_update(BlasCtx &bc, void *x, void *r, const void *p, const void *sv,
+                          const void *t, const void *rh, long long Vh, int nrhs, RhsState *st,
+                          int max_iter, cudaStream_t s);
+// CGNE (CG on the normal equations Mhat^dag Mhat x = Mhat^dag b), per RHS,
+// real scalars in the .x parts of rho / alpha / beta.  Init: blas_bicg_init
+// (r = b, x = p = 0, |b|^2).  Per iteration, with z = Mhat^dag r and
+// w = Mhat p:  gamma: rho' = |z|^2, beta = rho'/rho (0 when first);
+// p = z + beta p;  alpha = rho / |w|^2;  x += alpha p, r -= alpha w, |r|^2
+// decides convergence
+cudaError_t blas_cg_gamma(BlasCtx &bc, int prec, const void *z, long long Vh, int nrhs,
+                          RhsState *st, int first, cudaStream_t s);
+cudaError_t blas_cg_p(BlasCtx &bc, int prec, const void *z, void *p, long long Vh, int nrhs,
+                      const RhsState *st, cudaStream_t s);
+cudaError_t blas_cg_alpha(BlasCtx &bc, int prec, const void *w, long long Vh, int nrhs,
+                          RhsState *st, cudaStream_t s);
+cudaError_t blas_cg_update(BlasCtx &bc, int prec, void *x, void *r, const void *p, const void *w,
+                           long long Vh, int nrhs, RhsState *st, int max_iter, cudaStream_t s);
+cudaError_t blas32_cg_gamma(BlasCtx &bc, const void *z, long long Vh, int nrhs, RhsState *st,
+                            int first, cudaStream_t s);
+cudaError_t blas32_cg_p(BlasCtx &bc, const void *z, void *p, long long Vh, int nrhs,
+                        const RhsState *st, cudaStream_t s);
+cudaError_t blas32_cg_alpha(BlasCtx &bc, const void *w, long long Vh, int nrhs, RhsState *st,
+                            cudaStream_t s);
+cudaError_t blas32_cg_update(BlasCtx &bc, void *x, void *r, const void *p, const void *w,
+                             long long Vh, int nrhs, RhsState *st, int max_iter, cudaStream_t s);
 // FP64 outer loop helpers
 // r = b - y (r = b for `fresh` RHS); |r|^2 -> st.rr; st.scale = |r|;
 // convergence vs st.tol2 -> active

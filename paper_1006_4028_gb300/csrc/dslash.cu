@@ -10,26 +10,32 @@
 // and the antiperiodic sign on the time seam (eq. redeftbc), read from a small
 // per-group table.
 //
-// Thread mapping: one thread per (output site, RPT consecutive RHS), RHS
-// fastest.  The RHS of a site sit in adjacent threads of one warp; for every
-// chunk of the spinor layout [chunk][site][rhs] a warp reads one contiguous
-// run, so all loads are 128-bit and coalesced.  A thread loads (and, for
-// 12-real storage, rebuilds) each link once and applies it to its RPT
-// spinors, and loads the clover inverse once for them: RPT > 1 trades
-// registers for fewer instructions per RHS (the tuner picks it).  Neighbour
-// spinors are re-read by the 8 neighbours through L1/L2 (the 129 MB L2 holds
-// several time slices of a 12-RHS field); links and the clover inverse are
-// read once per site.
-//
 // Spin projection in the chiral basis gamma_mu = [[0, e_mu], [e_mu^dag, 0]]
 // (e_0 = -1, e_k = -i sigma_k): (1 -/+ gamma_mu) psi = [h; -/+ e_mu^dag h] with
 // h = psi_up -/+ e_mu psi_down, so only the 2-spin half spinor h is multiplied
 // by the link and the lower spins are rebuilt from U h.
+//
+// Two kernels:
+//  * FP64, one thread per (output site, RHS), scalar double arithmetic (the
+//    FP64 pipe is the bound on GB300);
+//  * FP32, one thread per (output site, 1 or 2 RHS pairs) on the paired layout
+//    of pair.cuh: every arithmetic step is one packed f32x2 instruction for two
+//    RHS, with links, hop factors and the clover inverse loaded once per
+//    thread and broadcast to both lanes.
+// RHS (pairs) are the fastest index: the RHS of a site sit in adjacent threads
+// of one warp, every component load of the [component][site][rhs] layout is
+// one contiguous 128-bit run per warp, and the RHS threads of a site share
+// their link and clover loads in L1.  Neighbour spinors are re-read by the 8
+// neighbours through L1/L2 (the 129 MB L2 holds several time slices of a
+// 12-RHS field).
 #include "cplx.cuh"
 #include "dp_internal.h"
+#include "pair.cuh"
 
 namespace dp {
 namespace {
+
+// ---- FP64 (scalar) -------------------------------------------------------------
 
 // h = upper two spins of (1 + SG*gamma_mu) psi, SG = -1 forward, +1 backward
 template <int MU, int SG, typename R>
@@ -90,386 +96,135 @@ __device__ __forceinline__ void accumulate(Cx<R> acc[12], const Cx<R> uh[6], R c
     }
 }
 
-// one hop (SG = -1: forward with U, SG = +1: backward with U^dag) applied to
-// the RPT spinors of this thread; `nb` points at the neighbour's first RHS
-template <typename R, int LF, int MU, int SG, int RPT>
-__device__ __forceinline__ void hop(Cx<R> (&acc)[RPT][12], const typename Chunk<R>::T *nb,
-                                    long long cs, const void *lk, long long Vh, long long lsite,
-                                    R c, const bool (&act)[RPT])
-{
-    Cx<R> u[9];
-    load_link<LF, R>(lk, Vh, lsite, MU, u);
-#pragma unroll
-    for (int k = 0; k < RPT; k++) {
-        if (!act[k]) continue;
-        Cx<R> ps[12];
-        load_spinor(nb + k, cs, ps);
-        Cx<R> h[6];
-        project<MU, SG>(ps, h);
-        Cx<R> uh[6];
-#pragma unroll
-        for (int sp = 0; sp < 2; sp++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                Cx<R> t;
-                if (SG < 0) {
-                    t = cmul(u[3 * a], h[3 * sp]);
-                    t = cfma(u[3 * a + 1], h[3 * sp + 1], t);
-                    t = cfma(u[3 * a + 2], h[3 * sp + 2], t);
-                } else {
-                    t = cjmul(u[a], h[3 * sp]);
-                    t = cjfma(u[3 + a], h[3 * sp + 1], t);
-                    t = cjfma(u[6 + a], h[3 * sp + 2], t);
-                }
-                uh[3 * sp + a] = t;
-            }
-        accumulate<MU, SG>(acc[k], uh, c);
-    }
-}
-
-template <typename R, int LF, int EPI, int RPT>
-__global__ void __launch_bounds__(256) k_dslash(const DslashParams p)
-{
-    using CT = typename Chunk<R>::T;
-    const Geom &g = p.g;
-    const int n = p.nrhs;
-    const int per_site = n / RPT;
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long s = gid / per_site;
-    const int r0 = (int)(gid - s * per_site) * RPT;
-    if (s >= g.Vh) return;
-    bool act[RPT];
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < RPT; k++) {
-        act[k] = !p.active || p.active[(r0 + k) * p.active_stride];  // skip converged RHS
-        any = any || act[k];
-    }
-    if (!any) return;
-
-    const int xh = (int)(s % g.Lxh);
-    long long q = s / g.Lxh;
-    const int y = (int)(q % g.Ly);
-    q /= g.Ly;
-    const int z = (int)(q % g.Lz);
-    const int t = (int)(q / g.Lz);
-    const int x = 2 * xh + ((t + y + z + p.parity) & 1);
-
-    const long long cs = g.Vh * n;
-    const CT *in = static_cast<const CT *>(p.in) + r0;
-    const int grp = p.grp_of[r0];  // the RPT RHS of a thread share their group
-    const R *hop_t = static_cast<const R *>(p.hop) + (long long)grp * 8 * g.Lmax;
-    const void *lown = p.links[p.parity];
-    const void *loth = p.links[1 - p.parity];
-    const long long Vh = g.Vh;
-
-    Cx<R> acc[RPT][12];
-#pragma unroll
-    for (int k = 0; k < RPT; k++)
-#pragma unroll
-        for (int j = 0; j < 12; j++) acc[k][j] = {R(0), R(0)};
-
-    auto row = [&](int tt, int zz, int yy) -> long long {
-        return (((long long)tt * g.Lz + zz) * g.Ly + yy) * g.Lxh;
-    };
-    // time
-    {
-        const int tp = (t + 1 == g.T) ? 0 : t + 1, tm = (t == 0) ? g.T - 1 : t - 1;
-        const long long sf = row(tp, z, y) + xh, sb = row(tm, z, y) + xh;
-        hop<R, LF, 0, -1, RPT>(acc, in + sf * n, cs, lown, Vh, s, hop_t[(0 * 2 + 0) * g.Lmax + t], act);
-        hop<R, LF, 0, +1, RPT>(acc, in + sb * n, cs, loth, Vh, sb, hop_t[(0 * 2 + 1) * g.Lmax + t], act);
-    }
-    // x
-    {
-        const int xp = (x + 1 == g.Lx) ? 0 : x + 1, xm = (x == 0) ? g.Lx - 1 : x - 1;
-        const long long r0w = row(t, z, y);
-        const long long sf = r0w + (xp >> 1), sb = r0w + (xm >> 1);
-        hop<R, LF, 1, -1, RPT>(acc, in + sf * n, cs, lown, Vh, s, hop_t[(1 * 2 + 0) * g.Lmax + x], act);
-        hop<R, LF, 1, +1, RPT>(acc, in + sb * n, cs, loth, Vh, sb, hop_t[(1 * 2 + 1) * g.Lmax + x], act);
-    }
-    // y
-    {
-        const int yp = (y + 1 == g.Ly) ? 0 : y + 1, ym = (y == 0) ? g.Ly - 1 : y - 1;
-        const long long sf = row(t, z, yp) + xh, sb = row(t, z, ym) + xh;
-        hop<R, LF, 2, -1, RPT>(acc, in + sf * n, cs, lown, Vh, s, hop_t[(2 * 2 + 0) * g.Lmax + y], act);
-        hop<R, LF, 2, +1, RPT>(acc, in + sb * n, cs, loth, Vh, sb, hop_t[(2 * 2 + 1) * g.Lmax + y], act);
-    }
-    // z
-    {
-        const int zp = (z + 1 == g.Lz) ? 0 : z + 1, zm = (z == 0) ? g.Lz - 1 : z - 1;
-        const long long sf = row(t, zp, y) + xh, sb = row(t, zm, y) + xh;
-        hop<R, LF, 3, -1, RPT>(acc, in + sf * n, cs, lown, Vh, s, hop_t[(3 * 2 + 0) * g.Lmax + z], act);
-        hop<R, LF, 3, +1, RPT>(acc, in + sb * n, cs, loth, Vh, sb, hop_t[(3 * 2 + 1) * g.Lmax + z], act);
-    }
-
-    const long long me = s * n + r0;
-    CT *out = static_cast<CT *>(p.out) + me;
-    const CT *xin = static_cast<const CT *>(p.x) + me;
-    if (EPI == EPI_HOP || EPI == EPI_XPY) {
-#pragma unroll
-        for (int k = 0; k < RPT; k++) {
-            if (!act[k]) continue;
-            if (EPI == EPI_XPY) {
-                Cx<R> v[12];
-                load_spinor(xin + k, cs, v);
-#pragma unroll
-                for (int j = 0; j < 12; j++) acc[k][j] = v[j] + acc[k][j];
-            }
-            store_spinor(out + k, cs, acc[k]);
-        }
-        return;
-    }
-    if (EPI == EPI_AINV_XMY) {
-#pragma unroll
-        for (int k = 0; k < RPT; k++) {
-            if (!act[k]) continue;
-            Cx<R> v[12];
-            load_spinor(xin + k, cs, v);
-#pragma unroll
-            for (int j = 0; j < 12; j++) acc[k][j] = v[j] - acc[k][j];
-        }
-    }
-    // A^-1 of the output parity for the mass of this group, loaded once per
-    // site and applied to every RHS of the thread
-    const CT *cl = static_cast<const CT *>(p.clov[grp]);
-#pragma unroll
-    for (int blk = 0; blk < 2; blk++) {
-        R m[36];
-        load_clover_block(cl, Vh, s, blk, m);
-#pragma unroll
-        for (int k = 0; k < RPT; k++) {
-            Cx<R> w[6];
-            herm6_apply(m, acc[k] + 6 * blk, w);
-#pragma unroll
-            for (int j = 0; j < 6; j++) acc[k][6 * blk + j] = w[j];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < RPT; k++) {
-        if (!act[k]) continue;
-        if (EPI == EPI_XMY_AINV) {
-            Cx<R> v[12];
-            load_spinor(xin + k, cs, v);
-#pragma unroll
-            for (int j = 0; j < 12; j++) acc[k][j] = v[j] - acc[k][j];
-        }
-        store_spinor(out + k, cs, acc[k]);
-    }
-}
-
-template <typename R, int LF, int RPT>
-cudaError_t launch_rpt(const DslashParams &p, int epi, int block, cudaStream_t st)
-{
-    const long long threads = p.g.Vh * (p.nrhs / RPT);
-    const unsigned grid = (unsigned)((threads + block - 1) / block);
-    if (RPT > 1) {
-        // several RHS per thread only for the two Schur-operator launches
-        switch (epi) {
-        case EPI_AINV: k_dslash<R, LF, EPI_AINV, RPT><<<grid, block, 0, st>>>(p); break;
-        case EPI_XMY_AINV: k_dslash<R, LF, EPI_XMY_AINV, RPT><<<grid, block, 0, st>>>(p); break;
-        default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
-    switch (epi) {
-    case EPI_HOP: k_dslash<R, LF, EPI_HOP, RPT><<<grid, block, 0, st>>>(p); break;
-    case EPI_AINV: k_dslash<R, LF, EPI_AINV, RPT><<<grid, block, 0, st>>>(p); break;
-    case EPI_XMY_AINV: k_dslash<R, LF, EPI_XMY_AINV, RPT><<<grid, block, 0, st>>>(p); break;
-    case EPI_AINV_XMY: k_dslash<R, LF, EPI_AINV_XMY, RPT><<<grid, block, 0, st>>>(p); break;
-    case EPI_XPY: k_dslash<R, LF, EPI_XPY, RPT><<<grid, block, 0, st>>>(p); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-template <typename R, int LF>
-cudaError_t launch_fmt(const DslashParams &p, int epi, int block, int rpt, cudaStream_t st)
-{
-    switch (rpt) {
-    case 1: return launch_rpt<R, LF, 1>(p, epi, block, st);
-    case 2: return launch_rpt<R, LF, 2>(p, epi, block, st);
-    case 3: return launch_rpt<R, LF, 3>(p, epi, block, st);
-    case 4: return launch_rpt<R, LF, 4>(p, epi, block, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-// ---- staged variant: FP32, 12-real links, one RHS per thread ----------------
-//
-// Every thread first issues asynchronous global->shared copies (cp.async,
-// 16 bytes each) of its 8 neighbour spinors, and the threads of a site share
-// the copies of the site's 8 links; after one wait and a block barrier
-// everything is computed from shared memory.  No register is held by a load
-// in flight, so many more bytes are in flight per SM than in the register
-// path, whose threads each wait on one neighbour at a time.  A block holds
-// whole sites (sites_per_block x n threads) so a site's threads share its
-// staged links.  Shared memory per block: 768 B per thread (spinors) plus
-// 384 B per site (links).
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-
-// rows 0, 1 from three float4; row 2 = conj(row0 x row1)
-__device__ __forceinline__ void link12(const float4 *l, Cx<float> u[9])
-{
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const float4 v = l[k];
-        u[2 * k] = {v.x, v.y};
-        u[2 * k + 1] = {v.z, v.w};
-    }
-    const Cx<float> a = cmul(u[1], u[5]) - cmul(u[2], u[4]);
-    const Cx<float> b = cmul(u[2], u[3]) - cmul(u[0], u[5]);
-    const Cx<float> c = cmul(u[0], u[4]) - cmul(u[1], u[3]);
-    u[6] = {a.re, -a.im};
-    u[7] = {b.re, -b.im};
-    u[8] = {c.re, -c.im};
-}
-
+// one hop (SG = -1: forward with U, SG = +1: backward with U^dag)
 template <int MU, int SG>
-__device__ __forceinline__ void hop_smem(Cx<float> acc[12], const float4 *sp, int nt,
-                                         const float4 *lk, float c)
+__device__ __forceinline__ void hop64(Cx<double> acc[12], const double2 *nb, long long cs,
+                                      const void *lk, long long Vh, long long lsite, double c)
 {
-    Cx<float> ps[12];
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-        const float4 v = sp[k * nt];
-        ps[2 * k] = {v.x, v.y};
-        ps[2 * k + 1] = {v.z, v.w};
-    }
-    Cx<float> h[6];
+    Cx<double> u[9];
+    load_link<LINK_F64_18, double>(lk, Vh, lsite, MU, u);
+    Cx<double> ps[12];
+    load_spinor(nb, cs, ps);
+    Cx<double> h[6];
     project<MU, SG>(ps, h);
-    Cx<float> u[9];
-    link12(lk, u);
-    Cx<float> uh[6];
+    Cx<double> uh[6];
 #pragma unroll
-    for (int s2 = 0; s2 < 2; s2++)
+    for (int sp = 0; sp < 2; sp++)
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            Cx<float> t;
+            Cx<double> t;
             if (SG < 0) {
-                t = cmul(u[3 * a], h[3 * s2]);
-                t = cfma(u[3 * a + 1], h[3 * s2 + 1], t);
-                t = cfma(u[3 * a + 2], h[3 * s2 + 2], t);
+                t = cmul(u[3 * a], h[3 * sp]);
+                t = cfma(u[3 * a + 1], h[3 * sp + 1], t);
+                t = cfma(u[3 * a + 2], h[3 * sp + 2], t);
             } else {
-                t = cjmul(u[a], h[3 * s2]);
-                t = cjfma(u[3 + a], h[3 * s2 + 1], t);
-                t = cjfma(u[6 + a], h[3 * s2 + 2], t);
+                t = cjmul(u[a], h[3 * sp]);
+                t = cjfma(u[3 + a], h[3 * sp + 1], t);
+                t = cjfma(u[6 + a], h[3 * sp + 2], t);
             }
-            uh[3 * s2 + a] = t;
+            uh[3 * sp + a] = t;
         }
     accumulate<MU, SG>(acc, uh, c);
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(96) k_dslash_staged(const DslashParams p, int spb)
-{
-    extern __shared__ float4 smem[];
-    const Geom &g = p.g;
-    const int n = p.nrhs, nt = blockDim.x;
-    float4 *sp = smem;            // [8 neighbours][6 chunks][nt]
-    float4 *sl = smem + 48 * nt;  // [site][8 links: 4 forward (own), 4 backward][3]
-    const int tid = threadIdx.x;
-    const int ls = tid / n, r = tid - ls * n;
-    const long long s = (long long)blockIdx.x * spb + ls;
-    const bool valid = s < g.Vh;
-    const bool act = valid && (!p.active || p.active[r * p.active_stride]);
-    const long long cs = g.Vh * n;
-    const float4 *in = static_cast<const float4 *>(p.in);
-    int x = 0, y = 0, z = 0, t = 0;
-    long long nb[8];  // forward t, x, y, z then backward t, x, y, z
-    if (valid) {
-        const int xh = (int)(s % g.Lxh);
-        long long q = s / g.Lxh;
-        y = (int)(q % g.Ly);
-        q /= g.Ly;
-        z = (int)(q % g.Lz);
-        t = (int)(q / g.Lz);
-        x = 2 * xh + ((t + y + z + p.parity) & 1);
-        auto row = [&](int tt, int zz, int yy) -> long long {
-            return (((long long)tt * g.Lz + zz) * g.Ly + yy) * g.Lxh;
-        };
-        const int tp = (t + 1 == g.T) ? 0 : t + 1, tm = (t == 0) ? g.T - 1 : t - 1;
-        const int xp = (x + 1 == g.Lx) ? 0 : x + 1, xm = (x == 0) ? g.Lx - 1 : x - 1;
-        const int yp = (y + 1 == g.Ly) ? 0 : y + 1, ym = (y == 0) ? g.Ly - 1 : y - 1;
-        const int zp = (z + 1 == g.Lz) ? 0 : z + 1, zm = (z == 0) ? g.Lz - 1 : z - 1;
-        const long long r0 = row(t, z, y);
-        nb[0] = row(tp, z, y) + xh;
-        nb[1] = r0 + (xp >> 1);
-        nb[2] = row(t, z, yp) + xh;
-        nb[3] = row(t, zp, y) + xh;
-        nb[4] = row(tm, z, y) + xh;
-        nb[5] = r0 + (xm >> 1);
-        nb[6] = row(t, z, ym) + xh;
-        nb[7] = row(t, zm, y) + xh;
-        if (act) {
-#pragma unroll
-            for (int d = 0; d < 8; d++) {
-                const float4 *src = in + nb[d] * n + r;
-#pragma unroll
-                for (int c = 0; c < 6; c++) cp_async16(&sp[(d * 6 + c) * nt + tid], src + c * cs);
-            }
-        }
-        // the site's 24 link chunks, shared out over its n threads
-        const float4 *lown = static_cast<const float4 *>(p.links[p.parity]);
-        const float4 *loth = static_cast<const float4 *>(p.links[1 - p.parity]);
-        for (int qc = r; qc < 24; qc += n) {
-            const int d = qc / 3, c = qc - 3 * (qc / 3);
-            const float4 *src = d < 4 ? lown + ((long long)d * 3 + c) * g.Vh + s
-                                      : loth + ((long long)(d - 4) * 3 + c) * g.Vh + nb[d];
-            cp_async16(&sl[(ls * 8 + d) * 3 + c], src);
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    if (!act) return;
+// site coordinates and the half-site indices of its 8 neighbours
+// (half-site indices fit in 32 bits: V/2 < 2^31 for every allowed geometry)
+struct Nbr {
+    int t, x, y, z;
+    int f[4], b[4];  // forward / backward neighbour per direction
+};
 
+__device__ __forceinline__ Nbr neighbours(const Geom &g, long long s64, int parity)
+{
+    Nbr o;
+    const unsigned s = (unsigned)s64;
+    const int xh = (int)(s % (unsigned)g.Lxh);
+    unsigned q = s / (unsigned)g.Lxh;
+    o.y = (int)(q % (unsigned)g.Ly);
+    q /= (unsigned)g.Ly;
+    o.z = (int)(q % (unsigned)g.Lz);
+    o.t = (int)(q / (unsigned)g.Lz);
+    o.x = 2 * xh + ((o.t + o.y + o.z + parity) & 1);
+    auto row = [&](int tt, int zz, int yy) -> int {
+        return ((tt * g.Lz + zz) * g.Ly + yy) * g.Lxh;
+    };
+    const int tp = (o.t + 1 == g.T) ? 0 : o.t + 1, tm = (o.t == 0) ? g.T - 1 : o.t - 1;
+    const int xp = (o.x + 1 == g.Lx) ? 0 : o.x + 1, xm = (o.x == 0) ? g.Lx - 1 : o.x - 1;
+    const int yp = (o.y + 1 == g.Ly) ? 0 : o.y + 1, ym = (o.y == 0) ? g.Ly - 1 : o.y - 1;
+    const int zp = (o.z + 1 == g.Lz) ? 0 : o.z + 1, zm = (o.z == 0) ? g.Lz - 1 : o.z - 1;
+    const int r0 = row(o.t, o.z, o.y);
+    o.f[0] = row(tp, o.z, o.y) + xh;
+    o.b[0] = row(tm, o.z, o.y) + xh;
+    o.f[1] = r0 + (xp >> 1);
+    o.b[1] = r0 + (xm >> 1);
+    o.f[2] = row(o.t, o.z, yp) + xh;
+    o.b[2] = row(o.t, o.z, ym) + xh;
+    o.f[3] = row(o.t, zp, o.y) + xh;
+    o.b[3] = row(o.t, zm, o.y) + xh;
+    return o;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(256) k_dslash64(const DslashParams p)
+{
+    const Geom &g = p.g;
+    const int n = p.nrhs;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long s = gid / n;
+    const int r = (int)(gid - s * n);
+    if (s >= g.Vh) return;
+    if (p.active && !p.active[r * p.active_stride]) return;  // converged RHS
+    const Nbr nb = neighbours(g, s, p.parity);
+    const long long cs = g.Vh * n;
+    const double2 *in = static_cast<const double2 *>(p.in) + r;
     const int grp = p.grp_of[r];
-    const float *ht = static_cast<const float *>(p.hop) + (long long)grp * 8 * g.Lmax;
-    const float4 *myl = sl + ls * 24;
-    const float4 *mys = sp + tid;
-    Cx<float> acc[12];
+    const double *ht = static_cast<const double *>(p.hop) + (long long)grp * 8 * g.Lmax;
+    const void *lown = p.links[p.parity], *loth = p.links[1 - p.parity];
+    const long long Vh = g.Vh;
+    Cx<double> acc[12];
 #pragma unroll
-    for (int k = 0; k < 12; k++) acc[k] = {0.f, 0.f};
-    // same accumulation order as the register kernel (per direction: forward,
-    // backward), so both give bit-identical results
-    hop_smem<0, -1>(acc, mys + 0 * 6 * nt, nt, myl + 0 * 3, ht[(0 * 2 + 0) * g.Lmax + t]);
-    hop_smem<0, +1>(acc, mys + 4 * 6 * nt, nt, myl + 4 * 3, ht[(0 * 2 + 1) * g.Lmax + t]);
-    hop_smem<1, -1>(acc, mys + 1 * 6 * nt, nt, myl + 1 * 3, ht[(1 * 2 + 0) * g.Lmax + x]);
-    hop_smem<1, +1>(acc, mys + 5 * 6 * nt, nt, myl + 5 * 3, ht[(1 * 2 + 1) * g.Lmax + x]);
-    hop_smem<2, -1>(acc, mys + 2 * 6 * nt, nt, myl + 2 * 3, ht[(2 * 2 + 0) * g.Lmax + y]);
-    hop_smem<2, +1>(acc, mys + 6 * 6 * nt, nt, myl + 6 * 3, ht[(2 * 2 + 1) * g.Lmax + y]);
-    hop_smem<3, -1>(acc, mys + 3 * 6 * nt, nt, myl + 3 * 3, ht[(3 * 2 + 0) * g.Lmax + z]);
-    hop_smem<3, +1>(acc, mys + 7 * 6 * nt, nt, myl + 7 * 3, ht[(3 * 2 + 1) * g.Lmax + z]);
+    for (int k = 0; k < 12; k++) acc[k] = {0.0, 0.0};
+    hop64<0, -1>(acc, in + nb.f[0] * n, cs, lown, Vh, s, ht[0 * g.Lmax + nb.t]);
+    hop64<0, +1>(acc, in + nb.b[0] * n, cs, loth, Vh, nb.b[0], ht[1 * g.Lmax + nb.t]);
+    hop64<1, -1>(acc, in + nb.f[1] * n, cs, lown, Vh, s, ht[2 * g.Lmax + nb.x]);
+    hop64<1, +1>(acc, in + nb.b[1] * n, cs, loth, Vh, nb.b[1], ht[3 * g.Lmax + nb.x]);
+    hop64<2, -1>(acc, in + nb.f[2] * n, cs, lown, Vh, s, ht[4 * g.Lmax + nb.y]);
+    hop64<2, +1>(acc, in + nb.b[2] * n, cs, loth, Vh, nb.b[2], ht[5 * g.Lmax + nb.y]);
+    hop64<3, -1>(acc, in + nb.f[3] * n, cs, lown, Vh, s, ht[6 * g.Lmax + nb.z]);
+    hop64<3, +1>(acc, in + nb.b[3] * n, cs, loth, Vh, nb.b[3], ht[7 * g.Lmax + nb.z]);
 
     const long long me = s * n + r;
-    float4 *out = static_cast<float4 *>(p.out) + me;
-    const float4 *xin = static_cast<const float4 *>(p.x) + me;
+    double2 *out = static_cast<double2 *>(p.out) + me;
+    const double2 *xin = static_cast<const double2 *>(p.x) + me;
+    Cx<double> v[12];
+    if (EPI == EPI_HOP || EPI == EPI_XPY || EPI == EPI_XMY_G5) {
+        if (EPI == EPI_XPY) {
+            load_spinor(xin, cs, v);
+#pragma unroll
+            for (int j = 0; j < 12; j++) acc[j] = v[j] + acc[j];
+        }
+        if (EPI == EPI_XMY_G5) {  // gamma5 = +1 on spins 0, 1 and -1 on spins 2, 3
+            load_spinor(xin, cs, v);
+#pragma unroll
+            for (int j = 0; j < 12; j++) acc[j] = j < 6 ? v[j] - acc[j] : v[j] + acc[j];
+        }
+        store_spinor(out, cs, acc);
+        return;
+    }
     if (EPI == EPI_AINV_XMY) {
-        Cx<float> v[12];
         load_spinor(xin, cs, v);
 #pragma unroll
         for (int j = 0; j < 12; j++) acc[j] = v[j] - acc[j];
     }
-    const float4 *cl = static_cast<const float4 *>(p.clov[grp]);
-    Cx<float> w[12];
+    const double2 *cl = static_cast<const double2 *>(p.clov[grp]);
+    Cx<double> w[12];
 #pragma unroll
     for (int blk = 0; blk < 2; blk++) {
-        float m[36];
-        load_clover_block(cl, g.Vh, s, blk, m);
+        double m[36];
+        load_clover_block(cl, Vh, s, blk, m);
         herm6_apply(m, acc + 6 * blk, w + 6 * blk);
     }
     if (EPI == EPI_XMY_AINV) {
-        Cx<float> v[12];
         load_spinor(xin, cs, v);
 #pragma unroll
         for (int j = 0; j < 12; j++) w[j] = v[j] - w[j];
@@ -477,60 +232,276 @@ __global__ void __launch_bounds__(96) k_dslash_staged(const DslashParams p, int 
     store_spinor(out, cs, w);
 }
 
-int staged_sites_per_block(int nrhs) { return nrhs >= 96 ? 1 : 96 / nrhs; }
+// ---- FP32, two RHS per packed lane pair ------------------------------------------
 
-size_t staged_smem_bytes(int nrhs)
+// upper two spins of (1 + SG*gamma_mu) psi for one colour, from its 4 spins
+template <int MU, int SG>
+__device__ __forceinline__ void project_pair(const C2 p0, const C2 p1, const C2 p2, const C2 p3,
+                                             C2 &h0, C2 &h1)
 {
-    const int spb = staged_sites_per_block(nrhs);
-    const int nt = spb * nrhs;
-    return (size_t)(48 * nt + 24 * spb) * sizeof(float4);
+    if (MU == 0) {
+        h0 = SG < 0 ? c2_add(p0, p2) : c2_sub(p0, p2);
+        h1 = SG < 0 ? c2_add(p1, p3) : c2_sub(p1, p3);
+    } else if (MU == 1) {
+        h0 = SG < 0 ? c2_addi(p0, p3) : c2_subi(p0, p3);
+        h1 = SG < 0 ? c2_addi(p1, p2) : c2_subi(p1, p2);
+    } else if (MU == 2) {
+        h0 = SG < 0 ? c2_add(p0, p3) : c2_sub(p0, p3);
+        h1 = SG < 0 ? c2_sub(p1, p2) : c2_add(p1, p2);
+    } else {
+        h0 = SG < 0 ? c2_addi(p0, p2) : c2_subi(p0, p2);
+        h1 = SG < 0 ? c2_subi(p1, p3) : c2_addi(p1, p3);
+    }
+}
+
+// acc += c t, acc += c (i t), acc += c (-i t); C = (c, c), MC = (-c, -c)
+__device__ __forceinline__ void acc1(C2 &acc, f2 C, C2 t)
+{
+    acc.re = ffma2(C, t.re, acc.re);
+    acc.im = ffma2(C, t.im, acc.im);
+}
+__device__ __forceinline__ void acc_i(C2 &acc, f2 C, f2 MC, C2 t)
+{
+    acc.re = ffma2(MC, t.im, acc.re);
+    acc.im = ffma2(C, t.re, acc.im);
+}
+__device__ __forceinline__ void acc_mi(C2 &acc, f2 C, f2 MC, C2 t)
+{
+    acc.re = ffma2(C, t.im, acc.re);
+    acc.im = ffma2(MC, t.re, acc.im);
+}
+
+// acc += c (1 + SG*gamma_mu) psi, colour a, given t0, t1 = (U h)_a of spins 0, 1
+template <int MU, int SG>
+__device__ __forceinline__ void accumulate_pair(C2 acc[12], int a, f2 C, f2 MC, C2 t0, C2 t1)
+{
+    acc1(acc[a], C, t0);
+    acc1(acc[3 + a], C, t1);
+    if (MU == 0) {
+        acc1(acc[6 + a], SG < 0 ? C : MC, t0);
+        acc1(acc[9 + a], SG < 0 ? C : MC, t1);
+    } else if (MU == 1) {
+        if (SG < 0) {
+            acc_mi(acc[6 + a], C, MC, t1);
+            acc_mi(acc[9 + a], C, MC, t0);
+        } else {
+            acc_i(acc[6 + a], C, MC, t1);
+            acc_i(acc[9 + a], C, MC, t0);
+        }
+    } else if (MU == 2) {
+        acc1(acc[6 + a], SG < 0 ? MC : C, t1);
+        acc1(acc[9 + a], SG < 0 ? C : MC, t0);
+    } else {
+        if (SG < 0) {
+            acc_mi(acc[6 + a], C, MC, t0);
+            acc_i(acc[9 + a], C, MC, t1);
+        } else {
+            acc_i(acc[6 + a], C, MC, t0);
+            acc_mi(acc[9 + a], C, MC, t1);
+        }
+    }
+}
+
+// one hop for the PPT pairs of this thread
+template <int LF, int MU, int SG, int PPT>
+__device__ __forceinline__ void hop_pair(C2 (&acc)[PPT][12], const float4 *nb, long long cs,
+                                         const void *lk, long long Vh, long long lsite, float c,
+                                         const bool (&act)[PPT])
+{
+    Cx<float> u[9];
+    load_link<LF, float>(lk, Vh, lsite, MU, u);
+    const f2 C = bc(c), MC = bc(-c);
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        if (!act[k]) continue;
+        // project colour by colour: only the 4 spins of one colour are live
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(nb + k);
+        C2 h[6];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            C2 q[4];
+#pragma unroll
+            for (int sp = 0; sp < 4; sp++) {
+                const ulonglong2 v = __ldg(src + (sp * 3 + a) * cs);
+                q[sp] = {v.x, v.y};
+            }
+            project_pair<MU, SG>(q[0], q[1], q[2], q[3], h[a], h[3 + a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            C2 t0, t1;
+            // forward: (U h)_a = sum_b U_ab h_b; backward: (U^dag h)_a = sum_b conj(U_ba) h_b
+            const Cx<float> e0 = SG < 0 ? u[3 * a] : u[a];
+            const Cx<float> e1 = SG < 0 ? u[3 * a + 1] : u[3 + a];
+            const Cx<float> e2 = SG < 0 ? u[3 * a + 2] : u[6 + a];
+            const B2 b0 = bcast(e0.re, e0.im), b1 = bcast(e1.re, e1.im), b2 = bcast(e2.re, e2.im);
+            if (SG < 0) {
+                t0 = c2_mul(b0, h[0]);
+                t1 = c2_mul(b0, h[3]);
+                t0 = c2_fma(b1, h[1], t0);
+                t1 = c2_fma(b1, h[4], t1);
+                t0 = c2_fma(b2, h[2], t0);
+                t1 = c2_fma(b2, h[5], t1);
+            } else {
+                t0 = c2_cjmul(b0, h[0]);
+                t1 = c2_cjmul(b0, h[3]);
+                t0 = c2_cjfma(b1, h[1], t0);
+                t1 = c2_cjfma(b1, h[4], t1);
+                t0 = c2_cjfma(b2, h[2], t0);
+                t1 = c2_cjfma(b2, h[5], t1);
+            }
+            accumulate_pair<MU, SG>(acc[k], a, C, MC, t0, t1);
+        }
+    }
+}
+
+template <int LF, int EPI, int PPT>
+__global__ void __launch_bounds__(256) k_dslash32(const DslashParams p)
+{
+    const Geom &g = p.g;
+    const int P = p.nrhs / 2;  // RHS pairs
+    const int per_site = P / PPT;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long s = gid / per_site;
+    const int q0 = (int)(gid - s * per_site) * PPT;
+    if (s >= g.Vh) return;
+    bool act[PPT];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int r = 2 * (q0 + k);
+        // a pair is computed while either of its RHS is still iterating
+        act[k] = !p.active || p.active[r * p.active_stride] || p.active[(r + 1) * p.active_stride];
+        any = any || act[k];
+    }
+    if (!any) return;
+    const Nbr nb = neighbours(g, s, p.parity);
+    const long long cs = g.Vh * P;
+    const float4 *in = static_cast<const float4 *>(p.in) + q0;
+    const int grp = p.grp_of[2 * q0];  // the RHS of a thread share their group
+    const float *ht = static_cast<const float *>(p.hop) + (long long)grp * 8 * g.Lmax;
+    const void *lown = p.links[p.parity], *loth = p.links[1 - p.parity];
+    const long long Vh = g.Vh;
+    C2 acc[PPT][12];
+#pragma unroll
+    for (int k = 0; k < PPT; k++)
+#pragma unroll
+        for (int j = 0; j < 12; j++) acc[k][j] = {0ull, 0ull};
+    hop_pair<LF, 0, -1, PPT>(acc, in + nb.f[0] * P, cs, lown, Vh, s, ht[0 * g.Lmax + nb.t], act);
+    hop_pair<LF, 0, +1, PPT>(acc, in + nb.b[0] * P, cs, loth, Vh, nb.b[0], ht[1 * g.Lmax + nb.t], act);
+    hop_pair<LF, 1, -1, PPT>(acc, in + nb.f[1] * P, cs, lown, Vh, s, ht[2 * g.Lmax + nb.x], act);
+    hop_pair<LF, 1, +1, PPT>(acc, in + nb.b[1] * P, cs, loth, Vh, nb.b[1], ht[3 * g.Lmax + nb.x], act);
+    hop_pair<LF, 2, -1, PPT>(acc, in + nb.f[2] * P, cs, lown, Vh, s, ht[4 * g.Lmax + nb.y], act);
+    hop_pair<LF, 2, +1, PPT>(acc, in + nb.b[2] * P, cs, loth, Vh, nb.b[2], ht[5 * g.Lmax + nb.y], act);
+    hop_pair<LF, 3, -1, PPT>(acc, in + nb.f[3] * P, cs, lown, Vh, s, ht[6 * g.Lmax + nb.z], act);
+    hop_pair<LF, 3, +1, PPT>(acc, in + nb.b[3] * P, cs, loth, Vh, nb.b[3], ht[7 * g.Lmax + nb.z], act);
+
+    const long long me = s * P + q0;
+    float4 *out = static_cast<float4 *>(p.out) + me;
+    const float4 *xin = static_cast<const float4 *>(p.x) + me;
+    if (EPI == EPI_HOP || EPI == EPI_XPY || EPI == EPI_XMY_G5) {
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            if (!act[k]) continue;
+            if (EPI == EPI_XPY) {
+                C2 v[12];
+                load_pair(xin + k, cs, v);
+#pragma unroll
+                for (int j = 0; j < 12; j++) acc[k][j] = c2_add(v[j], acc[k][j]);
+            }
+            if (EPI == EPI_XMY_G5) {  // gamma5 = +1 on spins 0, 1 and -1 on spins 2, 3
+                C2 v[12];
+                load_pair(xin + k, cs, v);
+#pragma unroll
+                for (int j = 0; j < 12; j++)
+                    acc[k][j] = j < 6 ? c2_sub(v[j], acc[k][j]) : c2_add(v[j], acc[k][j]);
+            }
+            store_pair(out + k, cs, acc[k]);
+        }
+        return;
+    }
+    if (EPI == EPI_AINV_XMY) {
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            if (!act[k]) continue;
+            C2 v[12];
+            load_pair(xin + k, cs, v);
+#pragma unroll
+            for (int j = 0; j < 12; j++) acc[k][j] = c2_sub(v[j], acc[k][j]);
+        }
+    }
+    // A^-1 of the output parity for this group's mass, loaded once per thread
+    const float4 *cl = static_cast<const float4 *>(p.clov[grp]);
+#pragma unroll
+    for (int blk = 0; blk < 2; blk++) {
+        float m[36];
+        load_clover_block(cl, Vh, s, blk, m);
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            C2 w[6];
+            herm6_pair(m, acc[k] + 6 * blk, w);
+#pragma unroll
+            for (int j = 0; j < 6; j++) acc[k][6 * blk + j] = w[j];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        if (!act[k]) continue;
+        if (EPI == EPI_XMY_AINV) {
+            C2 v[12];
+            load_pair(xin + k, cs, v);
+#pragma unroll
+            for (int j = 0; j < 12; j++) acc[k][j] = c2_sub(v[j], acc[k][j]);
+        }
+        store_pair(out + k, cs, acc[k]);
+    }
 }
 
 template <int EPI>
-cudaError_t launch_staged_epi(const DslashParams &p, cudaStream_t st)
+cudaError_t launch64(const DslashParams &p, int block, cudaStream_t st)
 {
-    const int spb = staged_sites_per_block(p.nrhs);
-    const int nt = spb * p.nrhs;
-    const size_t sm = staged_smem_bytes(p.nrhs);
-    static bool attr_set[kMaxRhs + 1] = {};
-    if (!attr_set[p.nrhs]) {
-        cudaError_t e = cudaFuncSetAttribute(k_dslash_staged<EPI>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        attr_set[p.nrhs] = true;
+    const long long threads = p.g.Vh * p.nrhs;
+    const unsigned grid = (unsigned)((threads + block - 1) / block);
+    k_dslash64<EPI><<<grid, block, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int LF, int PPT>
+cudaError_t launch32(const DslashParams &p, int epi, int block, cudaStream_t st)
+{
+    const long long threads = p.g.Vh * (p.nrhs / 2 / PPT);
+    const unsigned grid = (unsigned)((threads + block - 1) / block);
+    if (PPT > 1) {
+        // two pairs per thread only for the two Schur-operator launches
+        switch (epi) {
+        case EPI_AINV: k_dslash32<LF, EPI_AINV, PPT><<<grid, block, 0, st>>>(p); break;
+        case EPI_XMY_AINV: k_dslash32<LF, EPI_XMY_AINV, PPT><<<grid, block, 0, st>>>(p); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
     }
-    const unsigned grid = (unsigned)((p.g.Vh + spb - 1) / spb);
-    k_dslash_staged<EPI><<<grid, nt, sm, st>>>(p, spb);
+    switch (epi) {
+    case EPI_HOP: k_dslash32<LF, EPI_HOP, 1><<<grid, block, 0, st>>>(p); break;
+    case EPI_AINV: k_dslash32<LF, EPI_AINV, 1><<<grid, block, 0, st>>>(p); break;
+    case EPI_XMY_AINV: k_dslash32<LF, EPI_XMY_AINV, 1><<<grid, block, 0, st>>>(p); break;
+    case EPI_AINV_XMY: k_dslash32<LF, EPI_AINV_XMY, 1><<<grid, block, 0, st>>>(p); break;
+    case EPI_XPY: k_dslash32<LF, EPI_XPY, 1><<<grid, block, 0, st>>>(p); break;
+    case EPI_XMY_G5: k_dslash32<LF, EPI_XMY_G5, 1><<<grid, block, 0, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_dslash_staged(const DslashParams &p, int epi, cudaStream_t st)
-{
-    if (p.nrhs < 1 || p.nrhs > kMaxRhs || p.nrhs > 96 || 96 % p.nrhs != 0)
-        return cudaErrorInvalidValue;
-    switch (epi) {
-    case EPI_AINV: return launch_staged_epi<EPI_AINV>(p, st);
-    case EPI_XMY_AINV: return launch_staged_epi<EPI_XMY_AINV>(p, st);
-    case EPI_AINV_XMY: return launch_staged_epi<EPI_AINV_XMY>(p, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
 bool dslash_rpt_ok(int nrhs, int rpt, int prec, int epi)
 {
-    // rpt 0: the shared-memory staged kernel (FP32, one RHS per thread, whole
-    // sites per block of 96 threads, so nrhs must divide 96)
-    if (rpt == 0)
-        return prec != 0 && nrhs >= 1 && nrhs <= 96 && 96 % nrhs == 0 &&
-               (epi == EPI_AINV || epi == EPI_XMY_AINV || epi == EPI_AINV_XMY);
-    // the RHS of one thread must share a point-source group (12-aligned);
-    // FP64 keeps one RHS per thread (more would spill), and only the Schur
-    // launches have multi-RHS-per-thread variants
-    if (rpt == 1) return true;
-    return prec != 0 && rpt >= 2 && rpt <= 4 && nrhs % rpt == 0 && 12 % rpt == 0 &&
-           (epi == EPI_AINV || epi == EPI_XMY_AINV);
+    if (prec == 0) return rpt == 1;
+    // FP32 works on RHS pairs: nrhs even; 4 RHS per thread (two pairs) only
+    // for the Schur launches, with the 4 RHS inside one 12-RHS group
+    if (nrhs % 2) return false;
+    if (rpt == 2) return true;
+    return rpt == 4 && nrhs % 4 == 0 && (epi == EPI_AINV || epi == EPI_XMY_AINV);
 }
 
 cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi, int block,
@@ -539,16 +510,27 @@ cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi
     if (block <= 0 || block > 256 || (block & 31)) return cudaErrorInvalidValue;
     if (p.nrhs < 1 || p.nrhs > kMaxRhs || !dslash_rpt_ok(p.nrhs, rpt, prec, epi))
         return cudaErrorInvalidValue;
-    if (rpt == 0) {
-        if (link_fmt != LINK_F32_12) return cudaErrorInvalidValue;
-        return launch_dslash_staged(p, epi, st);
-    }
     if (prec == 0) {
         if (link_fmt != LINK_F64_18) return cudaErrorInvalidValue;
-        return launch_rpt<double, LINK_F64_18, 1>(p, epi, block, st);
+        switch (epi) {
+        case EPI_HOP: return launch64<EPI_HOP>(p, block, st);
+        case EPI_AINV: return launch64<EPI_AINV>(p, block, st);
+        case EPI_XMY_AINV: return launch64<EPI_XMY_AINV>(p, block, st);
+        case EPI_AINV_XMY: return launch64<EPI_AINV_XMY>(p, block, st);
+        case EPI_XPY: return launch64<EPI_XPY>(p, block, st);
+        case EPI_XMY_G5: return launch64<EPI_XMY_G5>(p, block, st);
+        default: return cudaErrorInvalidValue;
+        }
     }
-    if (link_fmt == LINK_F32_12) return launch_fmt<float, LINK_F32_12>(p, epi, block, rpt, st);
-    if (link_fmt == LINK_F32_18) return launch_fmt<float, LINK_F32_18>(p, epi, block, rpt, st);
+    const int ppt = rpt / 2;
+    if (link_fmt == LINK_F32_12)
+        return ppt == 2 ? launch32<LINK_F32_12, 2>(p, epi, block, st) : launch32<LINK_F32_12, 1>(p, epi, block, st);
+    if (link_fmt == LINK_F32_18)
+        return ppt == 2 ? launch32<LINK_F32_18, 2>(p, epi, block, st) : launch32<LINK_F32_18, 1>(p, epi, block, st);
+    if (link_fmt == LINK_H16_12)
+        return ppt == 2 ? launch32<LINK_H16_12, 2>(p, epi, block, st) : launch32<LINK_H16_12, 1>(p, epi, block, st);
+    if (link_fmt == LINK_B16_12)
+        return ppt == 2 ? launch32<LINK_B16_12, 2>(p, epi, block, st) : launch32<LINK_B16_12, 1>(p, epi, block, st);
     return cudaErrorInvalidValue;
 }
 

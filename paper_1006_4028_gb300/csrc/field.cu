@@ -55,6 +55,52 @@ __global__ void k_pack_links(const double2 *lex, Geom g, double2 *l64e, double2 
                                    (float)v[2 * k + 1].y);
 }
 
+// FP64 links of one parity -> rows 0, 1 in 16-bit with one FP32 scale per link
+template <typename H2>
+__device__ __forceinline__ unsigned f2h(float a, float b);
+template <>
+__device__ __forceinline__ unsigned f2h<__half2>(float a, float b)
+{
+    const __half2 h = __floats2half2_rn(a, b);
+    unsigned v;
+    memcpy(&v, &h, 4);
+    return v;
+}
+template <>
+__device__ __forceinline__ unsigned f2h<__nv_bfloat162>(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    unsigned v;
+    memcpy(&v, &h, 4);
+    return v;
+}
+
+template <typename H2>
+__global__ void k_pack_links16(const double2 *l64, long long Vh, void *out)
+{
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= Vh * 4) return;
+    const int mu = (int)(gid / Vh);
+    const long long s = gid - (long long)mu * Vh;
+    double2 v[6];
+    double mx = 0;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        v[k] = l64[((long long)mu * 9 + k) * Vh + s];
+        mx = fmax(mx, fmax(fabs(v[k].x), fabs(v[k].y)));
+    }
+    const float sc = mx > 0 ? (float)mx : 1.0f;
+    const double inv = 1.0 / sc;
+    uint2 *o = static_cast<uint2 *>(out) + (long long)mu * 3 * Vh + s;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const double2 a = v[2 * k], b = v[2 * k + 1];
+        o[k * Vh] = make_uint2(f2h<H2>((float)(a.x * inv), (float)(a.y * inv)),
+                               f2h<H2>((float)(b.x * inv), (float)(b.y * inv)));
+    }
+    reinterpret_cast<float *>(static_cast<uint2 *>(out) + 12 * Vh)[(long long)mu * Vh + s] = sc;
+}
+
 // one thread per (full site, rhs)
 __global__ void k_pack_spinor(const double2 *lex, Geom g, int n, int prec, void *ev, void *od)
 {
@@ -73,11 +119,16 @@ __global__ void k_pack_spinor(const double2 *lex, Geom g, int n, int prec, void 
 #pragma unroll
         for (int k = 0; k < 12; k++) o[k * cs] = src[k];
     } else {
-        float4 *o = static_cast<float4 *>(par ? od : ev) + me;
+        // paired FP32 layout: float4 (re_2q, re_2q+1, im_2q, im_2q+1) at (k*Vh + s)*n/2 + q
+        float *o = reinterpret_cast<float *>(static_cast<float4 *>(par ? od : ev));
+        const int P = n / 2, q = r >> 1, L = r & 1;
+        const long long csp = g.Vh * P;
 #pragma unroll
-        for (int k = 0; k < 6; k++)
-            o[k * cs] = make_float4((float)src[2 * k].x, (float)src[2 * k].y,
-                                    (float)src[2 * k + 1].x, (float)src[2 * k + 1].y);
+        for (int k = 0; k < 12; k++) {
+            float *f = o + 4 * (k * csp + s * P + q);
+            f[L] = (float)src[k].x;
+            f[2 + L] = (float)src[k].y;
+        }
     }
 }
 
@@ -99,12 +150,13 @@ __global__ void k_unpack_spinor(const void *ev, const void *od, Geom g, int n, i
 #pragma unroll
         for (int k = 0; k < 12; k++) dst[k] = o[k * cs];
     } else {
-        const float4 *o = static_cast<const float4 *>(par ? od : ev) + me;
+        const float *o = reinterpret_cast<const float *>(static_cast<const float4 *>(par ? od : ev));
+        const int P = n / 2, q = r >> 1, L = r & 1;
+        const long long csp = g.Vh * P;
 #pragma unroll
-        for (int k = 0; k < 6; k++) {
-            const float4 v = o[k * cs];
-            dst[2 * k] = make_double2(v.x, v.y);
-            dst[2 * k + 1] = make_double2(v.z, v.w);
+        for (int k = 0; k < 12; k++) {
+            const float *f = o + 4 * (k * csp + s * P + q);
+            dst[k] = make_double2(f[L], f[2 + L]);
         }
     }
 }
@@ -214,6 +266,20 @@ cudaError_t launch_pack_links(const double2 *lex, const Geom &g, double2 *l64[2]
     const long long n = g.V * 4;
     k_pack_links<<<(unsigned)((n + block - 1) / block), block, 0, st>>>(
         lex, g, l64[0], l64[1], l32f[0], l32f[1], l32c[0], l32c[1]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_links16(const double2 *l64, long long Vh, int fmt, void *out,
+                                cudaStream_t st)
+{
+    const int block = 128;
+    const unsigned grid = (unsigned)((Vh * 4 + block - 1) / block);
+    if (fmt == LINK_H16_12)
+        k_pack_links16<__half2><<<grid, block, 0, st>>>(l64, Vh, out);
+    else if (fmt == LINK_B16_12)
+        k_pack_links16<__nv_bfloat162><<<grid, block, 0, st>>>(l64, Vh, out);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ struct Request {
     Clock::time_point t_submit, t_done;
     bool admitted = false, done = false, cancelled = false;
     dp_status status = DP_OK;
+    std::string err;  // message of a failed request (set on the scheduler thread)
     std::shared_ptr<Field> field;
 };
 
@@ -80,7 +81,13 @@ void Scheduler::run()
                 dp_status s = b->init();
                 lk.lock();
                 if (s != DP_OK) {
-                    ++it;
+                    rq->status = s;
+                    rq->err = dp_last_error();
+                    rq->done = true;
+                    rq->t_done = Clock::now();
+                    rq->field->users--;
+                    it = queue.erase(it);
+                    done_cv.notify_all();
                     continue;
                 }
                 in_use += b->bytes();
@@ -96,8 +103,10 @@ void Scheduler::run()
             lk.lock();
             if (s != DP_OK) {
                 rq->status = s;
+                rq->err = dp_last_error();
                 rq->done = true;
                 rq->t_done = Clock::now();
+                rq->field->users--;
                 it = queue.erase(it);
                 done_cv.notify_all();
                 continue;
@@ -119,6 +128,9 @@ void Scheduler::run()
             for (Job *j : fin) {
                 Request *rq = static_cast<Request *>(j->user);
                 rq->status = (dp_status)j->res.status;
+                if (rq->status != DP_OK)
+                    rq->err = rq->status == DP_ERR_NOT_CONVERGED ? "solve did not reach the requested residue"
+                                                                 : "solve failed";
                 rq->done = true;
                 rq->t_done = Clock::now();
                 rq->field->users--;
@@ -133,6 +145,7 @@ void Scheduler::run()
                     if (ar.second->admitted && !ar.second->done &&
                         ar.second->req.field == kv.first) {
                         ar.second->status = s;
+                        ar.second->err = dp_last_error();
                         ar.second->done = true;
                         ar.second->t_done = Clock::now();
                         ar.second->field->users--;
@@ -358,6 +371,7 @@ dp_status dp_wait(dp_ctx *ctx, dp_ticket ticket, double timeout_s, double *cpp_o
         info->status = rq->status;
     }
     S.all.erase(ticket);
+    if (rq->status != DP_OK) set_error("%s", rq->err.empty() ? "request failed" : rq->err.c_str());
     return rq->status;
 }
 

@@ -49,16 +49,8 @@ dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void
     P.out = out;
     P.x = x;
     const Field &f = *op.f;
-    if (op.pr == 0) {
-        P.links[0] = f.l64[0];
-        P.links[1] = f.l64[1];
-    } else if (op.lf == LINK_F32_12) {
-        P.links[0] = f.l32c[0];
-        P.links[1] = f.l32c[1];
-    } else {
-        P.links[0] = f.l32f[0];
-        P.links[1] = f.l32f[1];
-    }
+    P.links[0] = op.links[0];
+    P.links[1] = op.links[1];
     for (int k = 0; k < kMaxGroups; k++) P.clov[k] = op.inv[parity][k];
     P.hop = op.hop;
     P.active = mask;
@@ -70,7 +62,7 @@ dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void
     const char *name = op.pr == 0 ? "dslash_fp64" : "dslash_fp32";
     cudaEvent_t ev;
     c->time_begin(name, &ev);
-    const int rpt = (epi == EPI_AINV || epi == EPI_XMY_AINV) ? op.rpt : 1;
+    const int rpt = (epi == EPI_AINV || epi == EPI_XMY_AINV) ? op.rpt : (op.pr == 0 ? 1 : 2);
     CK(launch_dslash(P, op.pr, op.lf, epi, op.block, rpt, c->stream));
     c->time_end(name, ev);
     c->launches++;
@@ -89,6 +81,35 @@ dp_status apply_mhat(Ctx *c, const Op &op, int p, const void *x, void *y, void *
     dp_status s = dslash(c, op, 1 - p, EPI_AINV, x, tmp, nullptr, state_mask(mask), kStateStride);
     if (s != DP_OK) return s;
     return dslash(c, op, p, EPI_XMY_AINV, tmp, y, x, state_mask(mask), kStateStride);
+}
+
+// Adjoint Schur operator.  With the hopping part H(alpha_B) and the clover
+// blocks A (Hermitian, commuting with gamma5), H(alpha_B)^dag =
+// gamma5 H(1/alpha_B) gamma5, so
+//   Mhat^dag y = y - gamma5 H~_pq A_qq^-1 H~_qp gamma5 A_pp^-1 y,
+// H~ the hopping part with the reciprocal profile (op_adj's tables).
+// tmp_p (parity p) and tmp_q (parity q) are scratch.
+dp_status apply_mhat_dag(Ctx *c, const Op &op, const Op &op_adj, int p, const void *y, void *out,
+                         void *tmp_p, void *tmp_q, const RhsState *mask)
+{
+    CloverApplyParams cp{};
+    for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op.inv[p][k];
+    memcpy(cp.grp_of, op.grp_of, sizeof cp.grp_of);
+    cp.mask = state_mask(mask);
+    cp.mask_stride = kStateStride;
+    cp.g5 = 1;
+    cp.in = y;
+    cp.out = tmp_p;
+    cp.Vh = op.f->g.Vh;
+    cp.nrhs = op.nrhs;
+    cudaEvent_t ev;
+    c->time_begin("clover_apply", &ev);
+    CK(launch_clover_apply(cp, op.pr, c->stream));
+    c->time_end("clover_apply", ev);
+    c->launches++;
+    dp_status s = dslash(c, op_adj, 1 - p, EPI_AINV, tmp_p, tmp_q, nullptr, state_mask(mask), kStateStride);
+    if (s != DP_OK) return s;
+    return dslash(c, op_adj, p, EPI_XMY_G5, tmp_q, out, y, state_mask(mask), kStateStride);
 }
 
 }  // namespace
@@ -127,7 +148,7 @@ dp_status Batch::init()
     const Geom &g = f->g;
     mixed = opts.prec != DP_PREC_FP64;
     ipr = mixed ? 1 : 0;
-    ilf = mixed ? (opts.compress12 ? LINK_F32_12 : LINK_F32_18) : LINK_F64_18;
+    ilf = inner_link_format(opts.prec, opts.compress12);
     const long long Vh = g.Vh;
     const int Lm = g.Lmax;
     v64 = (size_t)Vh * n * 24 * sizeof(double);
@@ -149,13 +170,16 @@ dp_status Batch::init()
     alpha_d = (double *)get(sizeof(double) * kMaxGroups * 4 * Lm);
     hop64_d = (double *)get(sizeof(double) * kMaxGroups * 8 * Lm);
     hop32_d = (float *)get(sizeof(float) * kMaxGroups * 8 * Lm);
+    hopadj64_d = (double *)get(sizeof(double) * kMaxGroups * 8 * Lm);
+    hopadj32_d = (float *)get(sizeof(float) * kMaxGroups * 8 * Lm);
     slots_d = (SlotInfo *)get(sizeof(SlotInfo) * kMaxRhs);
     tsrc_d = (int *)get(sizeof(int) * kMaxGroups);
     mask_d = (int *)get(sizeof(int) * kMaxRhs);
     cpp_d = (double *)get(sizeof(double) * kMaxGroups * g.T);
     cpart = (double *)get(sizeof(double) * (size_t)g.T * contract_blocks_per_slice(g) * kMaxGroups);
     nrm_d = (double *)get(sizeof(double) * kMaxRhs);
-    ok = ok && outer && inner && alpha_d && hop64_d && hop32_d && slots_d && tsrc_d && mask_d &&
+    ok = ok && outer && inner && alpha_d && hop64_d && hop32_d && hopadj64_d && hopadj32_d &&
+         slots_d && tsrc_d && mask_d &&
          cpp_d && cpart && nrm_d;
     if (!ok) {
         set_error("out of device memory for a %d-slot solver batch (%zu bytes per FP64 vector)", n, v64);
@@ -174,19 +198,29 @@ dp_status Batch::init()
     CK(cudaMemsetAsync(alpha_d, 0, sizeof(double) * kMaxGroups * 4 * Lm, c->stream));
     CK(cudaMemsetAsync(hop64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, c->stream));
     CK(cudaMemsetAsync(hop32_d, 0, sizeof(float) * kMaxGroups * 8 * Lm, c->stream));
+    CK(cudaMemsetAsync(hopadj64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, c->stream));
+    CK(cudaMemsetAsync(hopadj32_d, 0, sizeof(float) * kMaxGroups * 8 * Lm, c->stream));
 
     op64 = Op{};
     op64.f = f.get();
     op64.pr = 0;
     op64.lf = LINK_F64_18;
+    op64.links[0] = f->l64[0];
+    op64.links[1] = f->l64[1];
     op64.hop = hop64_d;
     op64.nrhs = n;
     c->launch_shape(Vh, 0, LINK_F64_18, n, &op64.block, &op64.rpt);
     opin = op64;
     opin.pr = ipr;
     opin.lf = ilf;
+    for (int p = 0; p < 2; p++) {
+        dp_status e = field_links(c, *f, ilf, p, &opin.links[p]);
+        if (e != DP_OK) return e;
+    }
     opin.hop = ipr == 0 ? (const void *)hop64_d : (const void *)hop32_d;
     c->launch_shape(Vh, ipr, ilf, n, &opin.block, &opin.rpt);
+    opin_adj = opin;
+    opin_adj.hop = ipr == 0 ? (const void *)hopadj64_d : (const void *)hopadj32_d;
     check_every = opts.check_every > 0 ? opts.check_every : (Vh * n >= (1 << 20) ? 2 : 8);
     return DP_OK;
 }
@@ -201,6 +235,7 @@ int Batch::active_jobs() const
 
 bool Batch::can_admit(int ncomp) const
 {
+    if (max_jobs > 0 && active_jobs() >= max_jobs) return false;
     int free_tab = -1;
     for (int k = 0; k < kMaxGroups; k++)
         if (!jobs[k]) {
@@ -261,6 +296,13 @@ dp_status Batch::admit(Job *j)
     s = get_clover_inv(c, *f, j->grp.M, &ci);
     if (s != DP_OK) return s;
     std::vector<float> hopf(hop.begin(), hop.end());
+    // reciprocal profile: each hop factor -1/2 s alpha(x)/alpha(y) (s = +-1)
+    // becomes -1/2 s alpha(y)/alpha(x) = (1/4) / (its original)
+    std::vector<double> hopa(hop.size());
+    for (size_t k = 0; k < hop.size(); k++) hopa[k] = hop[k] != 0.0 ? 0.25 / hop[k] : 0.0;
+    std::vector<float> hopaf(hopa.begin(), hopa.end());
+    CK(cudaMemcpyAsync(hopadj64_d + (size_t)tab * 8 * Lm, hopa.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(hopadj32_d + (size_t)tab * 8 * Lm, hopaf.data(), sizeof(float) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(alpha_d + (size_t)tab * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(hop64_d + (size_t)tab * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(hop32_d + (size_t)tab * 8 * Lm, hopf.data(), sizeof(float) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
@@ -270,6 +312,7 @@ dp_status Batch::admit(Job *j)
     for (int p = 0; p < 2; p++) {
         op64.inv[p][tab] = ci->inv64[p];
         opin.inv[p][tab] = ipr == 0 ? (const void *)ci->inv64[p] : (const void *)ci->inv32[p];
+        opin_adj.inv[p][tab] = opin.inv[p][tab];
     }
     for (int k = 0; k < j->ncomp; k++) {
         SlotInfo &sl = slots[s0 + k];
@@ -280,7 +323,7 @@ dp_status Batch::admit(Job *j)
         sl.y = j->grp.src[2];
         sl.z = j->grp.src[3];
         sl.scale = scale;
-        op64.grp_of[s0 + k] = opin.grp_of[s0 + k] = (int8_t)tab;
+        op64.grp_of[s0 + k] = opin.grp_of[s0 + k] = opin_adj.grp_of[s0 + k] = (int8_t)tab;
         slot_job[s0 + k] = j;
         slot_inner[s0 + k] = 0;
         slot_outer[s0 + k] = 0;
@@ -406,6 +449,69 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
     return DP_OK;
 }
 
+// CG on the normal equations Mhat^dag Mhat x = Mhat^dag b, stopping on the
+// residual of Mhat x = b itself (recursively updated r = b - Mhat x)
+dp_status Batch::cgne(int max_iter, int *iters_done)
+{
+    BlasCtx &bc = c->bc;
+    const int pr = opin.pr;
+    const long long Vh = f->g.Vh;
+    CK(blas_bicg_init(bc, pr, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, c->stream));
+    c->launches += 2;
+    CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int it = 0;
+    if (*c->h_nactive == 0) {
+        *iters_done = 0;
+        return DP_OK;
+    }
+    // z -> in.s, w = Mhat p -> in.v; in.t and in.to are scratch
+    auto body = [&](int first) -> dp_status {
+        dp_status s = apply_mhat_dag(c, opin, opin_adj, sp, in.r, in.s, in.t, in.to, inner);
+        if (s != DP_OK) return s;
+        CK(blas_cg_gamma(bc, pr, in.s, Vh, n, inner, first, c->stream));
+        CK(blas_cg_p(bc, pr, in.s, in.p, Vh, n, inner, c->stream));
+        s = apply_mhat(c, opin, sp, in.p, in.v, in.to, inner);
+        if (s != DP_OK) return s;
+        CK(blas_cg_alpha(bc, pr, in.v, Vh, n, inner, c->stream));
+        CK(blas_cg_update(bc, pr, in.x, in.r, in.p, in.v, Vh, n, inner, max_iter, c->stream));
+        c->launches += 5;
+        return DP_OK;
+    };
+    const bool graphs = opts.use_graph && !c->timing;
+    while (true) {
+        if (it == 0 || !graphs) {
+            dp_status s = body(it == 0);
+            if (s != DP_OK) return s;
+        } else {
+            if (!graph) {
+                cudaGraph_t gr;
+                CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                const long before = c->launches.load();
+                dp_status s = body(0);
+                cudaError_t ce = cudaStreamEndCapture(c->stream, &gr);
+                c->launches = before;
+                if (s != DP_OK) return s;
+                CK(ce);
+                CK(cudaGraphInstantiate(&graph, gr, 0));
+                cudaGraphDestroy(gr);
+                graph_max_iter = max_iter;
+            }
+            CK(cudaGraphLaunch(graph, c->stream));
+            c->launches += 10;
+        }
+        it++;
+        if (it >= max_iter) break;
+        if (it % check_every == 0) {
+            CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (*c->h_nactive == 0) break;
+        }
+    }
+    *iters_done = it;
+    return DP_OK;
+}
+
 dp_status Batch::round()
 {
     const long long Vh = f->g.Vh;
@@ -442,7 +548,7 @@ dp_status Batch::round()
     // inner budget of this round
     int budget = round_iters > 0 ? round_iters : opts.max_iter;
     int done = 0;
-    dp_status s = bicgstab(budget, &done);
+    dp_status s = opts.solver == DP_SOLVER_CGNE ? cgne(budget, &done) : bicgstab(budget, &done);
     if (s != DP_OK) return s;
     CK(cudaMemcpyAsync(hin.data(), inner, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -588,7 +694,11 @@ dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group
     const bool batched = o.batched != 0;
     // all groups share the source: solve on its parity
     const int sp = (groups[0].src[0] + groups[0].src[1] + groups[0].src[2] + groups[0].src[3]) & 1;
-    Batch B(c, f, batched ? 12 * ng : 1, o, 0, sp);
+    // unbatched: one RHS at a time; the FP32 kernels work on RHS pairs, so the
+    // mixed-precision unbatched batch has two slots and admits one job
+    const bool mixed = o.prec != DP_PREC_FP64;
+    Batch B(c, f, batched ? 12 * ng : (mixed ? 2 : 1), o, 0, sp);
+    if (!batched) B.set_max_jobs(1);
     dp_status s = B.init();
     if (s != DP_OK) return s;
     std::vector<Job> jobs(batched ? ng : 12 * ng);
@@ -752,6 +862,91 @@ dp_status dp_solve_point_dev(dp_ctx *ctx, dp_field field, int n_mass, const doub
                              const dp_solve_opts *opts, double *cpp_out_dev, dp_solve_info *info)
 {
     return solve_common(ctx, field, n_mass, M, profiles, src, r, opts, cpp_out_dev, 1, nullptr, info);
+}
+
+dp_status dp_schur_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
+                       const int src[4], int prec, int compress12, int parity, int dagger,
+                       const void *in, void *out, int nrhs)
+{
+    if (!ctx) {
+        set_error("null context");
+        return DP_ERR_INVALID_ARG;
+    }
+    Ctx &c = ctx->c;
+    if (cudaSetDevice(c.device) != cudaSuccess) {
+        set_error("cudaSetDevice failed");
+        return DP_ERR_CUDA;
+    }
+    auto fp = find_field(&c, field);
+    if (!fp) {
+        set_error("unknown field");
+        return DP_ERR_NOT_FOUND;
+    }
+    Field &f = *fp;
+    const int pr = prec == DP_PREC_FP64 ? 0 : 1;
+    if (!in || !out || in == out || nrhs < 1 || nrhs > kMaxRhs || (parity & ~1) ||
+        (dagger != 0 && dagger != 1) || prec < DP_PREC_FP64 || prec > DP_PREC_MIXED_BF16 ||
+        (pr == 1 && nrhs % 2) || !std::isfinite(M)) {
+        set_error("dp_schur_dev: invalid argument");
+        return DP_ERR_INVALID_ARG;
+    }
+    if (!f.has_clover) {
+        set_error("clover term not built");
+        return DP_ERR_INVALID_ARG;
+    }
+    const Geom &g = f.g;
+    const int zero_src[4] = {0, 0, 0, 0};
+    dp_profile none{};
+    none.kind = DP_PROF_NONE;
+    std::vector<double> alpha(4 * g.Lmax), hop(8 * g.Lmax), hopa(8 * g.Lmax);
+    dp_status s = profile_tables(profile ? *profile : none, g, f.bc_t, src ? src : zero_src,
+                                 alpha.data(), hop.data());
+    if (s != DP_OK) return s;
+    for (size_t k = 0; k < hop.size(); k++) hopa[k] = hop[k] != 0.0 ? 0.25 / hop[k] : 0.0;
+    std::vector<float> hopf(hop.begin(), hop.end()), hopaf(hopa.begin(), hopa.end());
+    const int lf = inner_link_format(prec, compress12);
+    Op op{};
+    op.f = &f;
+    op.pr = pr;
+    op.lf = lf;
+    op.nrhs = nrhs;
+    for (int q = 0; q < 2; q++) {
+        s = field_links(&c, f, lf, q, &op.links[q]);
+        if (s != DP_OK) return s;
+    }
+    std::shared_ptr<CloverInv> ci;
+    s = get_clover_inv(&c, f, M, &ci);
+    if (s != DP_OK) return s;
+    for (int q = 0; q < 2; q++) op.inv[q][0] = pr == 0 ? (const void *)ci->inv64[q] : (const void *)ci->inv32[q];
+    c.launch_shape(g.Vh, pr, lf, nrhs, &op.block, &op.rpt);
+    if (!dslash_rpt_ok(nrhs, op.rpt, pr, EPI_AINV)) op.rpt = pr == 0 ? 1 : 2;
+    const size_t tb = hop.size() * (pr == 0 ? sizeof(double) : sizeof(float));
+    const size_t vb = (size_t)g.Vh * nrhs * 24 * (pr == 0 ? 8 : 4);
+    void *hd = c.alloc(tb), *had = c.alloc(tb), *tp = c.alloc(vb), *tq = c.alloc(vb);
+    auto run = [&]() -> dp_status {
+        if (!hd || !had || !tp || !tq) {
+            set_error("out of device memory (dp_schur_dev)");
+            return DP_ERR_OOM;
+        }
+        CK(cudaMemcpyAsync(hd, pr == 0 ? (const void *)hop.data() : (const void *)hopf.data(), tb,
+                           cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(had, pr == 0 ? (const void *)hopa.data() : (const void *)hopaf.data(), tb,
+                           cudaMemcpyHostToDevice, c.stream));
+        op.hop = hd;
+        Op adj = op;
+        adj.hop = had;
+        dp_status e = dagger ? apply_mhat_dag(&c, op, adj, parity, in, out, tp, tq, nullptr)
+                             : apply_mhat(&c, op, parity, in, out, tq, nullptr);
+        if (e != DP_OK) return e;
+        CK(cudaStreamSynchronize(c.stream));
+        return DP_OK;
+    };
+    s = run();
+    c.release(hd);
+    c.release(had);
+    c.release(tp);
+    c.release(tq);
+    return s;
 }
 
 }  // extern "C"

@@ -56,6 +56,22 @@ def test_hop_fp32(ctx, setup, prof, c12):
     assert per_site_rel(got, ref) < 1e-6
 
 
+@pytest.mark.parametrize("prof", PROFILES)
+@pytest.mark.parametrize("kind", ["fp16", "bf16"])
+def test_hop_16bit_links(ctx, setup, prof, kind):
+    """16-bit links: the FP32 kernel against the oracle run on the links as
+    the 16-bit storage reproduces them (quantised rows 0, 1; row 2 rebuilt)."""
+    dims, f, op, psi = setup
+    kp, a0, src = prof
+    got = dp.dp_apply(ctx, f, "hop", 0.0, (kp, a0), src, "mixed_" + kind, psi)
+    op16 = oracle.WilsonClover(oracle.stored_links16(op.U.reshape(oracle.array_shape(dims) + (4, 3, 3)),
+                                                     kind), dims, 0.0, -1)
+    assert per_site_rel(got, op16.hop(psi, (kp, a0, src))) < 1e-6
+    # and the quantisation is visible against the unquantised links
+    err = per_site_rel(got, op.hop(psi, (kp, a0, src)))
+    assert 1e-5 < err < (2e-2 if kind == "bf16" else 3e-3)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("mixed_fp32", 1e-6)])
 def test_clover_and_full_operator(ctx, setup, prec, tol):
     dims, f, op, psi = setup
@@ -130,13 +146,12 @@ def test_invalid_arguments_are_errors(ctx):
         dp.dp_field_free(ctx, f)
 
 
-@pytest.mark.parametrize("prec,tol,rpts", [("mixed_fp32", 1e-6, (1, 2, 3, 4, -1)),
+@pytest.mark.parametrize("prec,tol,rpts", [("mixed_fp32", 1e-6, (2, 4)),
                                            ("fp64", 1e-13, (1,))])
 def test_schur_launch_all_rhs_per_thread(ctx, setup, prec, tol, rpts):
     """out_e = A_ee^-1 D_eo psi_o on packed device spinors (the solver's launch),
-    for every launch shape (1-4 RHS per thread, and -1: the shared-memory
-    staged kernel): equal to each other and, through A_ee out_e = D_eo psi_o,
-    to the oracle."""
+    for every launch shape (RHS per thread): equal to each other and, through
+    A_ee out_e = D_eo psi_o, to the oracle."""
     torch = pytest.importorskip("torch")
     dims, f, op, _ = setup
     M = 0.2
@@ -145,18 +160,21 @@ def test_schur_launch_all_rhs_per_thread(ctx, setup, prec, tol, rpts):
     ev, od = dp.pack_half_spinors(psi, dims)
     Vh = ev.shape[1]
 
-    # FP64 chunks are one complex component; FP32 chunks (float4) are two
+    # FP64: double2 per complex component; FP32 (RHS pairs): float4
+    # (re_2q, re_2q+1, im_2q, im_2q+1) per component and pair
     def dev(a):
         if prec == "fp64":
             return torch.from_numpy(np.ascontiguousarray(a).view(np.float64)).cuda()
-        b = a.reshape(6, 2, Vh, 12).transpose(0, 2, 3, 1).astype(np.complex64)
-        return torch.from_numpy(np.ascontiguousarray(b).view(np.float32)).cuda()
+        pr = a.reshape(12, Vh, 6, 2)
+        b = np.stack([pr.real[..., 0], pr.real[..., 1], pr.imag[..., 0], pr.imag[..., 1]], -1)
+        return torch.from_numpy(np.ascontiguousarray(b.astype(np.float32))).cuda()
 
     def host(t):
         if prec == "fp64":
             return t.cpu().numpy().view(np.complex128).reshape(12, Vh, 12)
-        b = t.cpu().numpy().view(np.complex64).reshape(6, Vh, 12, 2)
-        return b.transpose(0, 3, 1, 2).reshape(12, Vh, 12).astype(np.complex128)
+        b = t.cpu().numpy().reshape(12, Vh, 6, 4).astype(np.float64)
+        z = np.stack([b[..., 0] + 1j * b[..., 2], b[..., 1] + 1j * b[..., 3]], -1)
+        return z.reshape(12, Vh, 12)
 
     xin = dev(od)
     outs = []

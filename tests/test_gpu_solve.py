@@ -19,6 +19,12 @@ MIXED = {"prec": "mixed_fp32", "compress12": 1, "batched": 1, "use_graph": 1}
 MIXED_NOGRAPH = {"prec": "mixed_fp32", "compress12": 0, "batched": 1, "use_graph": 0}
 PLAIN = {"prec": "fp64", "batched": 0, "use_graph": 0}
 FP64_BATCHED = {"prec": "fp64", "batched": 1, "use_graph": 1}
+# 16-bit links in the inner solver; the FP64 outer loop still fixes the answer
+MIXED_FP16 = {"prec": "mixed_fp16", "batched": 1, "use_graph": 1}
+MIXED_BF16 = {"prec": "mixed_bf16", "batched": 1, "use_graph": 0}
+# CG on the normal equations (the alternative Krylov solver)
+CGNE_MIXED = {"prec": "mixed_fp32", "solver": "cgne", "batched": 1, "use_graph": 1}
+CGNE_FP64 = {"prec": "fp64", "solver": "cgne", "batched": 1, "use_graph": 0}
 
 
 @pytest.fixture(scope="module")
@@ -62,7 +68,8 @@ CASES = [(0.5, ("cosh_t", 0.4), (0, 0, 0, 0)), (0.8, ("cosh_t", 0.5), (3, 1, 2, 
 
 
 @pytest.mark.parametrize("M,prof,src", CASES)
-@pytest.mark.parametrize("opts", [MIXED, MIXED_NOGRAPH, PLAIN])
+@pytest.mark.parametrize("opts", [MIXED, MIXED_NOGRAPH, PLAIN, MIXED_FP16, MIXED_BF16, CGNE_MIXED,
+                                  CGNE_FP64])
 def test_interacting_solve_matches_oracle(ctx, inter, M, prof, src, opts):
     dims, f, op = inter
     T, V = dims[0], int(np.prod(dims))
@@ -132,9 +139,10 @@ def test_not_converged_and_bad_arguments(ctx, inter):
         with pytest.raises(dp.DpError) as e:
             dp.dp_solve_point(ctx, f, args["M"], ("none", 0.0), args["src"], args["r"], MIXED, T=T)
         assert e.value.status == 1
-    with pytest.raises(dp.DpError):
-        dp.dp_solve_point(ctx, f, 0.5, ("none", 0.0), (0, 0, 0, 0), 1e-8,
-                          dict(MIXED, prec="mixed_bf16"), T=T)
+    for bad_opts in [dict(MIXED, prec=7), dict(MIXED, solver=5), dict(MIXED, inner_tol=1.5)]:
+        with pytest.raises(dp.DpError) as e:
+            dp.dp_solve_point(ctx, f, 0.5, ("none", 0.0), (0, 0, 0, 0), 1e-8, bad_opts, T=T)
+        assert e.value.status == 1
 
 
 def test_device_output_and_timing(ctx, inter):

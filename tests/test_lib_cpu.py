@@ -112,3 +112,20 @@ def test_create_without_gpu_fails_cleanly(lib):
         dp.dp_create(0)
     assert e.value.status == 8
     assert "device" in e.value.message
+
+
+@pytest.mark.parametrize("kind,alpha0", KINDS)
+@pytest.mark.parametrize("bc_t", [-1, 1])
+def test_reciprocal_profile_hop_factors(lib, kind, alpha0, bc_t):
+    """The adjoint operator's hopping part uses the reciprocal profile
+    1/alpha_B; the solver forms its hop factors as (1/4) / (the profile's own),
+    which must equal the oracle's factors for the profile 1/alpha_B."""
+    dims = (12, 6, 4, 8)
+    src = (3, 1, 2, 5)
+    _, hop = dp.dp_profile_tables(dims, bc_t, (kind, alpha0), src)
+    ref_al = oracle.profile_alpha(kind, alpha0, dims, src)
+    fwd, bwd, _ = oracle.hop_tables([1.0 / a for a in ref_al], dims, bc_t)
+    for mu in range(4):
+        L = dims[mu]
+        np.testing.assert_allclose(0.25 / hop[mu, 0, :L], -0.5 * fwd[mu, :L], rtol=1e-14, atol=0)
+        np.testing.assert_allclose(0.25 / hop[mu, 1, :L], -0.5 * bwd[mu, :L], rtol=1e-14, atol=0)
