@@ -295,8 +295,8 @@ def main():
 
     # tune the launch shapes of the dslash for this volume and batch
     tuned = {}
-    for prec, c12 in ((args.prec, 1), ("fp64", 0)):
-        for nr in (12, 1):
+    for prec, c12, nrs in ((args.prec, 1, (12,)), ("fp64", 0, (12, 1))):
+        for nr in nrs:
             tuned["%s_n%d" % (prec, nr)] = dp.dp_autotune(ctx, field, prec, c12, nr)
 
     cpp_dev = torch.zeros(T, dtype=torch.float64, device="cuda")

@@ -269,18 +269,22 @@ dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profi
  * right-hand sides.  FP64 layout: double2 [12 components][V/2][nrhs]
  * (component = 3*spin + colour).  FP32 layout (RHS pairs): float4
  * [12 components][V/2][nrhs/2] holding (re_2q, re_2q+1, im_2q, im_2q+1) of
- * pair q.  `in`/`out` are device pointers the
- * caller allocated with dp_spinor_bytes().  Launch shape from the tuner
- * unless given: block_threads > 0 sets the block; rhs_per_thread selects the
- * RHS per thread (FP64: 1; FP32: 2 or 4, i.e. one or two RHS pairs of the
- * paired layout, 4 needing nrhs % 4 == 0), 0 the tuned or default shape.
- * FP32 needs nrhs even.  iters
- * launches back to back; if ms_out is non-NULL it receives the average launch
- * time measured with CUDA events on the context stream. */
+ * pair q.  `in`/`out` are device pointers the caller allocated with
+ * dp_spinor_bytes().  Launch shape from the tuner unless given:
+ * block_threads > 0 sets the block; rhs_per_thread selects the RHS per
+ * thread (FP64: 1; FP32: 2 or 4, i.e. one or two RHS pairs of the paired
+ * layout, 4 needing nrhs % 4 == 0), 0 the tuned or default choice; stages
+ * selects how neighbour spinors and links reach the thread: 0 direct loads,
+ * 2-3 staged through shared memory with that many of the 8 directions in
+ * flight (FP32 or 16-bit 12-real links, 2 RHS per thread, 64, 96 or 128
+ * threads per block), -1 the tuned or default choice.
+ * FP32 needs nrhs even.  iters launches back to back; if ms_out is non-NULL
+ * it receives the average launch time measured with CUDA events on the
+ * context stream. */
 size_t dp_spinor_bytes(dp_ctx *ctx, dp_field field, int prec, int nrhs);
 dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
                         int prec, int compress12, int out_parity, const void *in, void *out,
-                        int nrhs, int block_threads, int rhs_per_thread, int iters,
+                        int nrhs, int block_threads, int rhs_per_thread, int stages, int iters,
                         float *ms_out);
 
 /* The even-odd Schur operator of the preconditioned system (Sec. II, eq.
@@ -301,11 +305,13 @@ dp_status dp_schur_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *
 /* ---- autotuner ----------------------------------------------------------- */
 
 /* Time candidate launch shapes of the multi-RHS dslash for this field,
- * precision and nrhs (64-256 threads per block x the RHS-per-thread choices
- * of dp_dslash_dev), and keep the fastest for the solver's later launches.
- * best_* may be NULL. */
+ * precision and nrhs (64-256 threads per block x the RHS-per-thread and
+ * staging choices of dp_dslash_dev), and keep the fastest for the solver's
+ * later launches.  best_* may be NULL.  DP_ERR_INVALID_ARG if no shape serves
+ * nrhs (FP32 with an odd count). */
 dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int nrhs,
-                      int *best_block_threads, int *best_rhs_per_thread, float *best_ms);
+                      int *best_block_threads, int *best_rhs_per_thread, int *best_stages,
+                      float *best_ms);
 
 /* ---- per-kernel timing (CUDA events on the context stream) ---------------- */
 

@@ -122,9 +122,10 @@ def load(build_if_missing=False):
         "dp_restore_contract_noalloc": ([vp, up, ip, vp, vp, vp, vp, vp], ip),
         "dp_spinor_bytes": ([vp, up, ip, ip], sz),
         "dp_schur_dev": ([vp, up, dp, P(Profile), P(C.c_int * 4), ip, ip, ip, ip, vp, vp, ip], ip),
-        "dp_dslash_dev": ([vp, up, dp, P(Profile), ip, ip, ip, vp, vp, ip, ip, ip, ip,
+        "dp_dslash_dev": ([vp, up, dp, P(Profile), ip, ip, ip, vp, vp, ip, ip, ip, ip, ip,
                            P(C.c_float)], ip),
-        "dp_autotune": ([vp, up, ip, ip, ip, P(C.c_int), P(C.c_int), P(C.c_float)], ip),
+        "dp_autotune": ([vp, up, ip, ip, ip, P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_float)],
+                        ip),
         "dp_timing_enable": ([vp, ip], ip),
         "dp_timing_reset": ([vp], ip),
         "dp_timing_get": ([vp, C.c_char_p, P(C.c_long), P(C.c_double)], ip),
@@ -390,7 +391,7 @@ def dp_spinor_bytes(ctx, field, prec, nrhs):
 
 
 def dp_dslash_dev(ctx, field, M, profile, prec, compress12, out_parity, in_ptr, out_ptr, nrhs,
-                  block_threads=0, rhs_per_thread=0, iters=1):
+                  block_threads=0, rhs_per_thread=0, iters=1, stages=-1):
     """Device-resident hopping application with the A^-1 epilogue; returns the
     average launch time in ms (CUDA events on the context stream)."""
     pr, keep = _profile(profile)
@@ -398,8 +399,8 @@ def dp_dslash_dev(ctx, field, M, profile, prec, compress12, out_parity, in_ptr, 
     ms = C.c_float()
     _check(load().dp_dslash_dev(ctx, int(field), float(M), C.byref(pr), p, int(compress12),
                                 int(out_parity), C.c_void_p(int(in_ptr)), C.c_void_p(int(out_ptr)),
-                                int(nrhs), int(block_threads), int(rhs_per_thread), int(iters),
-                                C.byref(ms)))
+                                int(nrhs), int(block_threads), int(rhs_per_thread), int(stages),
+                                int(iters), C.byref(ms)))
     return ms.value
 
 
@@ -417,10 +418,10 @@ def dp_schur_dev(ctx, field, M, profile, src, prec, compress12, parity, dagger, 
 
 def dp_autotune(ctx, field, prec, compress12, nrhs):
     p = PREC[prec] if isinstance(prec, str) else int(prec)
-    b, rpt, ms = C.c_int(), C.c_int(), C.c_float()
+    b, rpt, sg, ms = C.c_int(), C.c_int(), C.c_int(), C.c_float()
     _check(load().dp_autotune(ctx, int(field), p, int(compress12), int(nrhs), C.byref(b),
-                              C.byref(rpt), C.byref(ms)))
-    return b.value, rpt.value, ms.value
+                              C.byref(rpt), C.byref(sg), C.byref(ms)))
+    return b.value, rpt.value, sg.value, ms.value
 
 
 # ---- timing ----------------------------------------------------------------------

@@ -113,17 +113,16 @@ void Ctx::collect_timing()
     pending.clear();
 }
 
-void Ctx::launch_shape(long long Vh, int prec, int link_fmt, int nrhs, int *block, int *rpt)
+Shape Ctx::launch_shape(long long Vh, int prec, int link_fmt, int nrhs)
 {
     std::lock_guard<std::mutex> lk(mu);
     auto it = tuned.find(TuneKey{Vh, prec, link_fmt, nrhs});
-    if (it != tuned.end()) {
-        *block = it->second.first;
-        *rpt = it->second.second;
-        return;
-    }
-    *block = 64;
-    *rpt = prec == 0 ? 1 : 2;  // FP32: one RHS pair per thread
+    if (it != tuned.end()) return it->second;
+    Shape sh;
+    sh.block = 64;
+    sh.rpt = prec == 0 ? 1 : 2;  // FP32: one RHS pair per thread
+    sh.stages = 0;
+    return sh;
 }
 
 std::shared_ptr<Field> find_field(Ctx *c, dp_field f)
@@ -671,9 +670,8 @@ dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_pro
                     P.x = tmp[p];
                     epi = EPI_XPY;
                 }
-                int blk, rpt;
-                c.launch_shape(g.Vh, pr, lf, nk, &blk, &rpt);
-                CUDA_OK(launch_dslash(P, pr, lf, epi, blk, pr == 0 ? 1 : 2, c.stream));
+                const Shape sh = c.launch_shape(g.Vh, pr, lf, nk);
+                CUDA_OK(launch_dslash(P, pr, lf, epi, sh.block, pr == 0 ? 1 : 2, c.stream));
             }
             CUDA_OK(launch_unpack_spinor(oe, oo, g, nk, pr, lex, c.stream));
             CUDA_OK(cudaMemcpyAsync(out, lex, nlex * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -705,7 +703,7 @@ size_t dp_spinor_bytes(dp_ctx *ctx, dp_field field, int prec, int nrhs)
 
 dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
                         int prec, int compress12, int out_parity, const void *in, void *out,
-                        int nrhs, int block_threads, int rhs_per_thread, int iters,
+                        int nrhs, int block_threads, int rhs_per_thread, int stages, int iters,
                         float *ms_out)
 {
     CTX_CHECK(ctx);
@@ -718,7 +716,7 @@ dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile 
     Field &f = *fp;
     if (!in || !out || nrhs < 1 || nrhs > kMaxRhs || iters < 1 || (out_parity & ~1) ||
         prec < DP_PREC_FP64 || prec > DP_PREC_MIXED_BF16 ||
-        rhs_per_thread < 0 ||
+        rhs_per_thread < 0 || stages < -1 || stages > 3 ||
         (block_threads != 0 && (block_threads < 32 || block_threads > 256 || block_threads % 32))) {
         set_error("dp_dslash_dev: invalid argument");
         return DP_ERR_INVALID_ARG;
@@ -767,13 +765,21 @@ dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile 
     P.g = g;
     P.parity = out_parity;
     P.nrhs = nrhs;
-    int block, rpt;
-    c.launch_shape(g.Vh, pr, lf, nrhs, &block, &rpt);
+    const Shape sh = c.launch_shape(g.Vh, pr, lf, nrhs);
+    int block = sh.block, rpt = sh.rpt, stg = sh.stages;
     if (block_threads > 0) block = block_threads;
     if (rhs_per_thread != 0) rpt = want_rpt;
+    if (stages >= 0) stg = stages;
+    if (stg > 0 && !dslash_staged_ok(pr, lf, EPI_AINV, rpt, stg, block)) {
+        c.release(hopd);
+        set_error("dp_dslash_dev: shared-memory staging needs FP32 or 16-bit 12-real links, 2 RHS per "
+                  "thread and 64, 96 or 128 threads per block");
+        return DP_ERR_INVALID_ARG;
+    }
     cudaEvent_t a = c.get_event(), b = c.get_event();
     CUDA_OK(cudaEventRecord(a, c.stream));
-    for (int k = 0; k < iters; k++) CUDA_OK(launch_dslash(P, pr, lf, EPI_AINV, block, rpt, c.stream));
+    for (int k = 0; k < iters; k++)
+        CUDA_OK(launch_dslash(P, pr, lf, EPI_AINV, block, rpt, c.stream, stg));
     CUDA_OK(cudaEventRecord(b, c.stream));
     c.launches += iters;
     CUDA_OK(cudaEventSynchronize(b));
@@ -787,7 +793,8 @@ dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile 
 }
 
 dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int nrhs,
-                      int *best_block_threads, int *best_rhs_per_thread, float *best_ms)
+                      int *best_block_threads, int *best_rhs_per_thread, int *best_stages,
+                      float *best_ms)
 {
     CTX_CHECK(ctx);
     Ctx &c = ctx->c;
@@ -813,41 +820,52 @@ dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int
     }
     cudaMemsetAsync(in, 0, vb, c.stream);
     // candidates: four block sizes x RHS per thread (FP64: 1; FP32: one or
-    // two RHS pairs)
-    const int blocks[] = {64, 128, 192, 256};
+    // two RHS pairs) x shared-memory staging (FP32 one pair per thread: none
+    // or 2-3 directions in flight)
+    const int blocks[] = {64, 96, 128, 192, 256};
     const int rpts[] = {1, 2, 4};
-    int best = 0, best_rpt = 1;
+    const int stage_opts[] = {0, 2, 3};
+    Shape best;
     float bms = 1e30f;
     dp_status st = DP_OK;
     for (int r : rpts) {
         if (!dslash_rpt_ok(nrhs, r, pr, EPI_AINV)) continue;
-        for (int b : blocks) {
-            const int abi_rpt = r;
-            float ms = 0;
-            // warm up once, then time a few launches
-            st = dp_dslash_dev(ctx, field, 0.1, nullptr, prec, compress12, 0, in, out, nrhs, b,
-                               abi_rpt, 2, &ms);
-            if (st != DP_OK) break;
-            st = dp_dslash_dev(ctx, field, 0.1, nullptr, prec, compress12, 0, in, out, nrhs, b,
-                               abi_rpt, 10, &ms);
-            if (st != DP_OK) break;
-            if (ms < bms) {
-                bms = ms;
-                best = b;
-                best_rpt = r;
+        for (int sg : stage_opts) {
+            for (int b : blocks) {
+                if (sg > 0 && !dslash_staged_ok(pr, lf, EPI_AINV, r, sg, b)) continue;
+                float ms = 0;
+                // warm up once, then time a few launches
+                st = dp_dslash_dev(ctx, field, 0.1, nullptr, prec, compress12, 0, in, out, nrhs, b,
+                                   r, sg, 2, &ms);
+                if (st != DP_OK) break;
+                st = dp_dslash_dev(ctx, field, 0.1, nullptr, prec, compress12, 0, in, out, nrhs, b,
+                                   r, sg, 10, &ms);
+                if (st != DP_OK) break;
+                if (ms < bms) {
+                    bms = ms;
+                    best.block = b;
+                    best.rpt = r;
+                    best.stages = sg;
+                }
             }
+            if (st != DP_OK) break;
         }
         if (st != DP_OK) break;
     }
     c.release(in);
     c.release(out);
     if (st != DP_OK) return st;
+    if (bms >= 1e30f) {
+        set_error("dp_autotune: no launch shape serves %d RHS in this precision (FP32 needs an even count)", nrhs);
+        return DP_ERR_INVALID_ARG;
+    }
     {
         std::lock_guard<std::mutex> lk(c.mu);
-        c.tuned[TuneKey{g.Vh, pr, lf, nrhs}] = {best, best_rpt};
+        c.tuned[TuneKey{g.Vh, pr, lf, nrhs}] = best;
     }
-    if (best_block_threads) *best_block_threads = best;
-    if (best_rhs_per_thread) *best_rhs_per_thread = best_rpt;
+    if (best_block_threads) *best_block_threads = best.block;
+    if (best_rhs_per_thread) *best_rhs_per_thread = best.rpt;
+    if (best_stages) *best_stages = best.stages;
     if (best_ms) *best_ms = bms;
     return DP_OK;
 }

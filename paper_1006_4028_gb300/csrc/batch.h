@@ -36,7 +36,8 @@ struct Op {
     int8_t grp_of[kMaxRhs] = {};
     int nrhs = 0;
     int block = 128;
-    int rpt = 1;  // RHS per thread of the Schur launches
+    int rpt = 1;     // RHS per thread of the Schur launches
+    int stages = 0;  // shared-memory staging of the Schur launches (0: direct)
 };
 
 struct InnerVecs {

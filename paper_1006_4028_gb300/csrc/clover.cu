@@ -13,6 +13,7 @@
 #include "cplx.cuh"
 #include "dp_internal.h"
 #include "pair.cuh"
+#include "reduce.cuh"
 
 namespace dp {
 namespace {
@@ -315,6 +316,71 @@ __global__ void k_clover_apply32(const CloverApplyParams p)
     store_pair(static_cast<float4 *>(p.out) + gid, cs, w);
 }
 
+// The FP64 apply restricted to each RHS's own source site: for a point
+// source (mat + diag) in vanishes elsewhere.  One thread per RHS; the caller
+// zeroes `out` of the masked RHS beforehand (in and out may alias).
+__global__ void k_clover_point64(const CloverApplyParams p, Geom g, const SlotInfo *slots,
+                                 int parity)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= p.nrhs) return;
+    if (p.mask && !p.mask[r]) return;
+    const SlotInfo sl = slots[r];
+    if (((sl.t + sl.x + sl.y + sl.z) & 1) != parity) return;
+    const long long s = ((((long long)sl.t * g.Lz + sl.z) * g.Ly + sl.y) * g.Lx + sl.x) >> 1;
+    const int n = p.nrhs, grp = p.grp_of[r];
+    const long long cs = p.Vh * n, me = s * n + r;
+    Cx<double> v[12], w[12];
+    load_spinor(static_cast<const double2 *>(p.in) + me, cs, v);
+#pragma unroll
+    for (int blk = 0; blk < 2; blk++) {
+        double m[36];
+        load_clover_block(static_cast<const double2 *>(p.mat[grp]), p.Vh, s, blk, m);
+#pragma unroll
+        for (int i = 0; i < 6; i++) m[i] += p.diag[grp];
+        herm6_apply(m, v + 6 * blk, w + 6 * blk);
+    }
+    store_spinor(static_cast<double2 *>(p.out) + me, cs, w);
+}
+
+// Per-RHS |(mat + diag) in|^2 of an FP64 spinor with an FP32 clover (mat),
+// the product formed in FP32 and the squares summed in FP64: a residual
+// report needs a few digits only.  Block = lanes x n RHS (reduce.cuh).
+__global__ void __launch_bounds__(kMaxBlock)
+    k_clover_norm(Cfg c, const CloverApplyParams p, double *out, double *partials,
+                  unsigned int *counter)
+{
+    const int n = p.nrhs;
+    const int r = threadIdx.x % n, lane = threadIdx.x / n;
+    const long long cs = p.Vh * n;
+    double acc[1] = {0};
+    const bool act = !p.mask || p.mask[r];
+    const int grp = p.grp_of[r];
+    const float dg = (float)p.diag[grp];
+    for (long long s = (long long)blockIdx.x * c.lanes + lane; act && s < p.Vh;
+         s += (long long)gridDim.x * c.lanes) {
+        Cx<double> v[12];
+        load_spinor(static_cast<const double2 *>(p.in) + s * n + r, cs, v);
+        Cx<float> vf[12], w[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) vf[k] = {(float)v[k].re, (float)v[k].im};
+#pragma unroll
+        for (int blk = 0; blk < 2; blk++) {
+            float m[36];
+            load_clover_block(static_cast<const float4 *>(p.mat[grp]), p.Vh, s, blk, m);
+#pragma unroll
+            for (int i = 0; i < 6; i++) m[i] += dg;
+            herm6_apply(m, vf + 6 * blk, w + 6 * blk);
+        }
+        float ss = 0;
+#pragma unroll
+        for (int k = 0; k < 12; k++) ss = fmx(w[k].re, w[k].re, fmx(w[k].im, w[k].im, ss));
+        acc[0] += (double)ss;
+    }
+    if (!reduce_last<1, 1>(acc, c, partials, counter, n)) return;
+    out[r] = acc[0];
+}
+
 // FP64 [36 double2][Vh] -> FP32 [18 float4][Vh], same order of the 72 reals
 __global__ void k_clover_to_f32(const double2 *in, float4 *out, long long Vh)
 {
@@ -354,6 +420,21 @@ cudaError_t launch_clover_invert(const double2 *clov, long long Vh, double M, do
     const int block = 128;
     k_clover_invert<<<(unsigned)((2 * Vh + block - 1) / block), block, 0, st>>>(clov, Vh, 4.0 + M,
                                                                                inv64, inv32, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clover_point(const CloverApplyParams &p, const Geom &g, const SlotInfo *slots,
+                                int parity, cudaStream_t st)
+{
+    k_clover_point64<<<1, kMaxRhs, 0, st>>>(p, g, slots, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clover_norm(BlasCtx &bc, const CloverApplyParams &p, double *out_dev,
+                               cudaStream_t st)
+{
+    const Cfg c = cfg_wave(bc, k_clover_norm, p.Vh, p.nrhs);
+    k_clover_norm<<<c.grid, c.block, 0, st>>>(c, p, out_dev, bc.partials, bc.counter);
     return cudaGetLastError();
 }
 

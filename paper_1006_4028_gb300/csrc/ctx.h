@@ -106,7 +106,7 @@ struct Ctx {
     std::map<std::string, Stat> stats;
     std::atomic<long> launches{0};
 
-    std::map<TuneKey, std::pair<int, int>> tuned;  // (threads per block, RHS per thread)
+    std::map<TuneKey, Shape> tuned;
 
     std::unique_ptr<Scheduler, SchedDeleter> sched;
 
@@ -118,7 +118,7 @@ struct Ctx {
     void time_end(const char *name, cudaEvent_t a);
     void collect_timing();
     // dslash launch shape for the Schur launches: tuned, else a default
-    void launch_shape(long long Vh, int prec, int link_fmt, int nrhs, int *block, int *rpt);
+    Shape launch_shape(long long Vh, int prec, int link_fmt, int nrhs);
 };
 
 std::shared_ptr<Field> find_field(Ctx *c, dp_field f);

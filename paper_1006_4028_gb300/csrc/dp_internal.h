@@ -75,14 +75,24 @@ struct DslashParams {
 };
 
 // ---- launch wrappers (dslash.cu) ----
-// prec: 0 = FP64 (links LINK_F64_18), 1 = FP32 (links LINK_F32_18 / LINK_F32_12)
-// rpt: RHS per thread (1-4; >1 only for FP32 and the A^-1 / x - A^-1 D
-// epilogues); rpt 0 selects the shared-memory staged kernel (FP32 12-real
-// links, one RHS per thread, `block` ignored)
+// prec: 0 = FP64 (links LINK_F64_18), 1 = FP32 (links LINK_F32_18 / _F32_12
+// / _H16_12 / _B16_12).  rpt: RHS per thread (FP64 1; FP32 2 = one RHS pair,
+// 4 = two pairs, only for the A^-1 and x - A^-1 D epilogues).  stages > 0
+// (2-3, FP32 one pair per thread, 12-real or 16-bit links, the A^-1 and
+// x - A^-1 D epilogues, 64, 96 or 128 threads per block) selects the kernel
+// that stages neighbour spinors and links through shared memory with
+// `stages` directions in flight; 0 = direct loads
 cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi, int block,
-                          int rpt, cudaStream_t st);
-cudaError_t launch_dslash_staged(const DslashParams &p, int epi, cudaStream_t st);
+                          int rpt, cudaStream_t st, int stages = 0);
 bool dslash_rpt_ok(int nrhs, int rpt, int prec, int epi);
+bool dslash_staged_ok(int prec, int link_fmt, int epi, int rpt, int stages, int block);
+
+// launch shape of the Schur dslash launches (tuner result or default)
+struct Shape {
+    int block = 64;
+    int rpt = 1;
+    int stages = 0;
+};
 
 // ---- clover (clover.cu) ----
 // clover term (no mass) for all sites of both parities, FP64, layout above
@@ -109,6 +119,15 @@ struct CloverApplyParams {
     int nrhs;
 };
 cudaError_t launch_clover_apply(const CloverApplyParams &p, int prec, cudaStream_t st);
+// FP64 apply at each masked RHS's source site only (point sources: zero
+// elsewhere; the caller zeroes `out` of those RHS first); parity: that of p.in
+cudaError_t launch_clover_point(const CloverApplyParams &p, const Geom &g, const SlotInfo *slots,
+                                int parity, cudaStream_t st);
+// per-RHS |(mat + diag) in|^2 into out_dev[nrhs]: FP64 spinor, FP32 clover
+// (p.mat), FP32 products, FP64 sums
+struct BlasCtx;
+cudaError_t launch_clover_norm(BlasCtx &bc, const CloverApplyParams &p, double *out_dev,
+                               cudaStream_t st);
 
 // ---- field packing, sources, restore/contract (field.cu) ----
 cudaError_t launch_pack_links(const double2 *lex, const Geom &g, double2 *l64[2], float2 *l32f[2],

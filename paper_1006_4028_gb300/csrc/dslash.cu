@@ -28,6 +28,8 @@
 // their link and clover loads in L1.  Neighbour spinors are re-read by the 8
 // neighbours through L1/L2 (the 129 MB L2 holds several time slices of a
 // 12-RHS field).
+#include <type_traits>
+
 #include "cplx.cuh"
 #include "dp_internal.h"
 #include "pair.cuh"
@@ -302,7 +304,40 @@ __device__ __forceinline__ void accumulate_pair(C2 acc[12], int a, f2 C, f2 MC, 
     }
 }
 
-// one hop for the PPT pairs of this thread
+// acc += c (1 + SG*gamma_mu) U psi (forward) or c (1 + SG*gamma_mu) U^dag psi
+// (backward) from the projected half spinor h (spins 0, 1 of colours 0-2)
+template <int MU, int SG>
+__device__ __forceinline__ void hop_apply(C2 (&acc)[12], const C2 (&h)[6], const Cx<float> (&u)[9],
+                                          f2 C, f2 MC)
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        C2 t0, t1;
+        // forward: (U h)_a = sum_b U_ab h_b; backward: (U^dag h)_a = sum_b conj(U_ba) h_b
+        const Cx<float> e0 = SG < 0 ? u[3 * a] : u[a];
+        const Cx<float> e1 = SG < 0 ? u[3 * a + 1] : u[3 + a];
+        const Cx<float> e2 = SG < 0 ? u[3 * a + 2] : u[6 + a];
+        const B2 b0 = bcast(e0.re, e0.im), b1 = bcast(e1.re, e1.im), b2 = bcast(e2.re, e2.im);
+        if (SG < 0) {
+            t0 = c2_mul(b0, h[0]);
+            t1 = c2_mul(b0, h[3]);
+            t0 = c2_fma(b1, h[1], t0);
+            t1 = c2_fma(b1, h[4], t1);
+            t0 = c2_fma(b2, h[2], t0);
+            t1 = c2_fma(b2, h[5], t1);
+        } else {
+            t0 = c2_cjmul(b0, h[0]);
+            t1 = c2_cjmul(b0, h[3]);
+            t0 = c2_cjfma(b1, h[1], t0);
+            t1 = c2_cjfma(b1, h[4], t1);
+            t0 = c2_cjfma(b2, h[2], t0);
+            t1 = c2_cjfma(b2, h[5], t1);
+        }
+        accumulate_pair<MU, SG>(acc, a, C, MC, t0, t1);
+    }
+}
+
+// one hop for the PPT pairs of this thread, neighbour spinors from global memory
 template <int LF, int MU, int SG, int PPT>
 __device__ __forceinline__ void hop_pair(C2 (&acc)[PPT][12], const float4 *nb, long long cs,
                                          const void *lk, long long Vh, long long lsite, float c,
@@ -327,75 +362,78 @@ __device__ __forceinline__ void hop_pair(C2 (&acc)[PPT][12], const float4 *nb, l
             }
             project_pair<MU, SG>(q[0], q[1], q[2], q[3], h[a], h[3 + a]);
         }
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            C2 t0, t1;
-            // forward: (U h)_a = sum_b U_ab h_b; backward: (U^dag h)_a = sum_b conj(U_ba) h_b
-            const Cx<float> e0 = SG < 0 ? u[3 * a] : u[a];
-            const Cx<float> e1 = SG < 0 ? u[3 * a + 1] : u[3 + a];
-            const Cx<float> e2 = SG < 0 ? u[3 * a + 2] : u[6 + a];
-            const B2 b0 = bcast(e0.re, e0.im), b1 = bcast(e1.re, e1.im), b2 = bcast(e2.re, e2.im);
-            if (SG < 0) {
-                t0 = c2_mul(b0, h[0]);
-                t1 = c2_mul(b0, h[3]);
-                t0 = c2_fma(b1, h[1], t0);
-                t1 = c2_fma(b1, h[4], t1);
-                t0 = c2_fma(b2, h[2], t0);
-                t1 = c2_fma(b2, h[5], t1);
-            } else {
-                t0 = c2_cjmul(b0, h[0]);
-                t1 = c2_cjmul(b0, h[3]);
-                t0 = c2_cjfma(b1, h[1], t0);
-                t1 = c2_cjfma(b1, h[4], t1);
-                t0 = c2_cjfma(b2, h[2], t0);
-                t1 = c2_cjfma(b2, h[5], t1);
-            }
-            accumulate_pair<MU, SG>(acc[k], a, C, MC, t0, t1);
-        }
+        hop_apply<MU, SG>(acc[k], h, u, C, MC);
     }
 }
 
-template <int LF, int EPI, int PPT>
-__global__ void __launch_bounds__(256) k_dslash32(const DslashParams p)
+// links as staged in shared memory next to the spinor (slot components 12-14):
+// 12-real FP32 as three float4; 16-bit as three uint2 and the FP32 scale
+template <int LF>
+__device__ __forceinline__ void link_smem(const float4 *sl, int bd, Cx<float> u[9])
 {
-    const Geom &g = p.g;
-    const int P = p.nrhs / 2;  // RHS pairs
-    const int per_site = P / PPT;
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long s = gid / per_site;
-    const int q0 = (int)(gid - s * per_site) * PPT;
-    if (s >= g.Vh) return;
-    bool act[PPT];
-    bool any = false;
+    if constexpr (LF == LINK_F32_12) {
 #pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        const int r = 2 * (q0 + k);
-        // a pair is computed while either of its RHS is still iterating
-        act[k] = !p.active || p.active[r * p.active_stride] || p.active[(r + 1) * p.active_stride];
-        any = any || act[k];
+        for (int k = 0; k < 3; k++) {
+            const float4 v = sl[k * bd];
+            u[2 * k] = {v.x, v.y};
+            u[2 * k + 1] = {v.z, v.w};
+        }
+    } else {
+        using H2 = typename std::conditional<LF == LINK_H16_12, __half2, __nv_bfloat162>::type;
+        const uint4 a = *reinterpret_cast<const uint4 *>(sl);
+        const uint4 b = *reinterpret_cast<const uint4 *>(sl + bd);
+        const unsigned w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+        const float sc = __uint_as_float(b.z);
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            const float2 f = h2f<H2>(w[k]);
+            u[k] = {sc * f.x, sc * f.y};
+        }
     }
-    if (!any) return;
-    const Nbr nb = neighbours(g, s, p.parity);
-    const long long cs = g.Vh * P;
-    const float4 *in = static_cast<const float4 *>(p.in) + q0;
-    const int grp = p.grp_of[2 * q0];  // the RHS of a thread share their group
-    const float *ht = static_cast<const float *>(p.hop) + (long long)grp * 8 * g.Lmax;
-    const void *lown = p.links[p.parity], *loth = p.links[1 - p.parity];
-    const long long Vh = g.Vh;
-    C2 acc[PPT][12];
-#pragma unroll
-    for (int k = 0; k < PPT; k++)
-#pragma unroll
-        for (int j = 0; j < 12; j++) acc[k][j] = {0ull, 0ull};
-    hop_pair<LF, 0, -1, PPT>(acc, in + nb.f[0] * P, cs, lown, Vh, s, ht[0 * g.Lmax + nb.t], act);
-    hop_pair<LF, 0, +1, PPT>(acc, in + nb.b[0] * P, cs, loth, Vh, nb.b[0], ht[1 * g.Lmax + nb.t], act);
-    hop_pair<LF, 1, -1, PPT>(acc, in + nb.f[1] * P, cs, lown, Vh, s, ht[2 * g.Lmax + nb.x], act);
-    hop_pair<LF, 1, +1, PPT>(acc, in + nb.b[1] * P, cs, loth, Vh, nb.b[1], ht[3 * g.Lmax + nb.x], act);
-    hop_pair<LF, 2, -1, PPT>(acc, in + nb.f[2] * P, cs, lown, Vh, s, ht[4 * g.Lmax + nb.y], act);
-    hop_pair<LF, 2, +1, PPT>(acc, in + nb.b[2] * P, cs, loth, Vh, nb.b[2], ht[5 * g.Lmax + nb.y], act);
-    hop_pair<LF, 3, -1, PPT>(acc, in + nb.f[3] * P, cs, lown, Vh, s, ht[6 * g.Lmax + nb.z], act);
-    hop_pair<LF, 3, +1, PPT>(acc, in + nb.b[3] * P, cs, loth, Vh, nb.b[3], ht[7 * g.Lmax + nb.z], act);
+    Cx<float> a = cmul(u[1], u[5]) - cmul(u[2], u[4]);
+    Cx<float> b = cmul(u[2], u[3]) - cmul(u[0], u[5]);
+    Cx<float> c = cmul(u[0], u[4]) - cmul(u[1], u[3]);
+    u[6] = {a.re, -a.im};
+    u[7] = {b.re, -b.im};
+    u[8] = {c.re, -c.im};
+}
 
+// one hop from a neighbour spinor and link staged in shared memory:
+// component k of this thread's slot at sb[k * bd], the link from k = 12
+template <int LF, int MU, int SG>
+__device__ __forceinline__ void hop_smem(C2 (&acc)[12], const float4 *sb, int bd, float c)
+{
+    Cx<float> u[9];
+    link_smem<LF>(sb + 12 * bd, bd, u);
+    const f2 C = bc(c), MC = bc(-c);
+    C2 h[6];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        C2 q[4];
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++) {
+            const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(sb)[(sp * 3 + a) * bd];
+            q[sp] = {v.x, v.y};
+        }
+        project_pair<MU, SG>(q[0], q[1], q[2], q[3], h[a], h[3 + a]);
+    }
+    hop_apply<MU, SG>(acc, h, u, C, MC);
+}
+
+// ---- asynchronous global -> shared copies: group bookkeeping, L1 prefetch ----
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// epilogue of the FP32 kernels: x + D, x - g5 D, or the A^-1 forms
+template <int EPI, int PPT>
+__device__ __forceinline__ void finish32(const DslashParams &p, C2 (&acc)[PPT][12],
+                                         const bool (&act)[PPT], long long s, int q0, int grp,
+                                         long long cs)
+{
+    const int P = p.nrhs / 2;
+    const long long Vh = p.g.Vh;
     const long long me = s * P + q0;
     float4 *out = static_cast<float4 *>(p.out) + me;
     const float4 *xin = static_cast<const float4 *>(p.x) + me;
@@ -457,6 +495,195 @@ __global__ void __launch_bounds__(256) k_dslash32(const DslashParams p)
     }
 }
 
+template <int LF, int EPI, int PPT>
+__global__ void __launch_bounds__(256) k_dslash32(const DslashParams p)
+{
+    const Geom &g = p.g;
+    const int P = p.nrhs / 2;  // RHS pairs
+    const int per_site = P / PPT;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long s = gid / per_site;
+    const int q0 = (int)(gid - s * per_site) * PPT;
+    if (s >= g.Vh) return;
+    bool act[PPT];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int r = 2 * (q0 + k);
+        // a pair is computed while either of its RHS is still iterating
+        act[k] = !p.active || p.active[r * p.active_stride] || p.active[(r + 1) * p.active_stride];
+        any = any || act[k];
+    }
+    if (!any) return;
+    const Nbr nb = neighbours(g, s, p.parity);
+    const long long cs = g.Vh * P;
+    const float4 *in = static_cast<const float4 *>(p.in) + q0;
+    const int grp = p.grp_of[2 * q0];  // the RHS of a thread share their group
+    const float *ht = static_cast<const float *>(p.hop) + (long long)grp * 8 * g.Lmax;
+    const void *lown = p.links[p.parity], *loth = p.links[1 - p.parity];
+    const long long Vh = g.Vh;
+    C2 acc[PPT][12];
+#pragma unroll
+    for (int k = 0; k < PPT; k++)
+#pragma unroll
+        for (int j = 0; j < 12; j++) acc[k][j] = {0ull, 0ull};
+    hop_pair<LF, 0, -1, PPT>(acc, in + nb.f[0] * P, cs, lown, Vh, s, ht[0 * g.Lmax + nb.t], act);
+    hop_pair<LF, 0, +1, PPT>(acc, in + nb.b[0] * P, cs, loth, Vh, nb.b[0], ht[1 * g.Lmax + nb.t], act);
+    hop_pair<LF, 1, -1, PPT>(acc, in + nb.f[1] * P, cs, lown, Vh, s, ht[2 * g.Lmax + nb.x], act);
+    hop_pair<LF, 1, +1, PPT>(acc, in + nb.b[1] * P, cs, loth, Vh, nb.b[1], ht[3 * g.Lmax + nb.x], act);
+    hop_pair<LF, 2, -1, PPT>(acc, in + nb.f[2] * P, cs, lown, Vh, s, ht[4 * g.Lmax + nb.y], act);
+    hop_pair<LF, 2, +1, PPT>(acc, in + nb.b[2] * P, cs, loth, Vh, nb.b[2], ht[5 * g.Lmax + nb.y], act);
+    hop_pair<LF, 3, -1, PPT>(acc, in + nb.f[3] * P, cs, lown, Vh, s, ht[6 * g.Lmax + nb.z], act);
+    hop_pair<LF, 3, +1, PPT>(acc, in + nb.b[3] * P, cs, loth, Vh, nb.b[3], ht[7 * g.Lmax + nb.z], act);
+
+    finish32<EPI, PPT>(p, acc, act, s, q0, grp, cs);
+}
+
+// ---- FP32, one RHS pair per thread, neighbour spinors and links staged
+// through shared memory: direction d + ST is copied asynchronously (cp.async,
+// no registers held) while direction d is computed, so ST directions' loads
+// are in flight per thread and no global load sits on the hop's critical
+// path; the epilogue's clover inverse (and x) are prefetched into L1 at the
+// start.  Each thread reads only the slots it filled itself: no block barrier.
+// The block size BD is a template parameter so that every shared-memory
+// offset is an immediate; each direction's copies are one asm sequence that
+// walks the global address itself (no per-copy address registers to keep).
+constexpr int kSlot = 15;  // float4 per stage and thread: 12 spinor + 3 link
+
+#define DP_CPA16(OFF) "cp.async.cg.shared.global [%0+" #OFF "*%3], [a], 16;\n\tadd.u64 a, a, %2;\n\t"
+
+// 12 spinor components: shared [sdst + k*BD*16], global src + k*cs_bytes
+template <int BD>
+__device__ __forceinline__ void stage_spinor(unsigned sdst, const void *src, long long cs_bytes)
+{
+    asm volatile("{\n\t.reg .u64 a;\n\tmov.u64 a, %1;\n\t"
+                 DP_CPA16(0) DP_CPA16(1) DP_CPA16(2) DP_CPA16(3) DP_CPA16(4) DP_CPA16(5)
+                 DP_CPA16(6) DP_CPA16(7) DP_CPA16(8) DP_CPA16(9) DP_CPA16(10) DP_CPA16(11)
+                 "}\n" ::"r"(sdst), "l"(src), "l"(cs_bytes), "n"(BD * 16)
+                 : "memory");
+}
+
+// the link of one direction: shared [sdst + k*BD*16] (k = 0..2), global
+// stride vh_bytes between its three chunks
+template <int BD>
+__device__ __forceinline__ void stage_link12(unsigned sdst, const void *src, long long vh_bytes)
+{
+    asm volatile("{\n\t.reg .u64 a;\n\tmov.u64 a, %1;\n\t"
+                 DP_CPA16(0) DP_CPA16(1) DP_CPA16(2)
+                 "}\n" ::"r"(sdst), "l"(src), "l"(vh_bytes), "n"(BD * 16)
+                 : "memory");
+}
+#undef DP_CPA16
+
+// 16-bit link: three 8-byte chunks (stride vh_bytes) and the 4-byte scale,
+// packed as bytes 0-7, 8-15 of slot 12 and 0-7, 8-11 of slot 13
+template <int BD>
+__device__ __forceinline__ void stage_link16(unsigned sdst, const void *src, long long vh_bytes,
+                                             const void *scale)
+{
+    asm volatile("{\n\t.reg .u64 a;\n\tmov.u64 a, %1;\n\t"
+                 "cp.async.ca.shared.global [%0], [a], 8;\n\tadd.u64 a, a, %2;\n\t"
+                 "cp.async.ca.shared.global [%0+8], [a], 8;\n\tadd.u64 a, a, %2;\n\t"
+                 "cp.async.ca.shared.global [%0+%3], [a], 8;\n\t"
+                 "cp.async.ca.shared.global [%0+%4], [%5], 4;\n\t"
+                 "}\n" ::"r"(sdst), "l"(src), "l"(vh_bytes), "n"(BD * 16), "n"(BD * 16 + 8),
+                 "l"(scale)
+                 : "memory");
+}
+
+template <int LF, int BD>
+__device__ __forceinline__ void stage_issue(unsigned sslot, const float4 *src, long long cs,
+                                            const void *lk, long long Vh, long long lsite, int mu)
+{
+    stage_spinor<BD>(sslot, src, cs * 16);
+    const unsigned sl = sslot + 12 * BD * 16;
+    if constexpr (LF == LINK_F32_12) {
+        stage_link12<BD>(sl, static_cast<const float4 *>(lk) + (long long)mu * 3 * Vh + lsite, Vh * 16);
+    } else {
+        const uint2 *l = static_cast<const uint2 *>(lk) + (long long)mu * 3 * Vh + lsite;
+        const float *scl = reinterpret_cast<const float *>(static_cast<const uint2 *>(lk) + 12 * Vh) +
+                           (long long)mu * Vh + lsite;
+        stage_link16<BD>(sl, l, Vh * 8, scl);
+    }
+}
+
+template <int LF, int ST, int BD, int D>
+__device__ __forceinline__ void staged_step(C2 (&acc)[12], const float4 *mine, unsigned smine,
+                                            const int (&nbi)[8], const float4 *in, int P,
+                                            long long cs, const Nbr &nb, long long s,
+                                            const void *lown, const void *loth, long long Vh,
+                                            const float (&hc)[8])
+{
+    constexpr int MU = D / 2;
+    constexpr int SLOT = (D % ST) * kSlot * BD;  // in float4
+    cp_async_wait<ST - 1>();                       // groups 0..D have landed
+    hop_smem<LF, MU, (D & 1) ? +1 : -1>(acc, mine + SLOT, BD, hc[D]);
+    if constexpr (D + ST < 8) {
+        constexpr int E = D + ST, ME = E / 2;
+        stage_issue<LF, BD>(smine + SLOT * 16, in + (long long)nbi[E] * P, cs, (E & 1) ? loth : lown, Vh,
+                            (E & 1) ? (long long)nb.b[ME] : s, ME);
+    }
+    cp_async_commit();  // (possibly empty) group D + ST keeps the count uniform
+}
+
+template <int LF, int EPI, int ST, int BD>
+__global__ void __launch_bounds__(BD) k_dslash32s(const DslashParams p)
+{
+    extern __shared__ float4 sbuf[];
+    const Geom &g = p.g;
+    const int P = p.nrhs / 2;
+    const long long gid = (long long)blockIdx.x * BD + threadIdx.x;
+    const long long s = gid / P;
+    const int q0 = (int)(gid - s * P);
+    if (s >= g.Vh) return;
+    bool act[1];
+    act[0] = !p.active || p.active[2 * q0 * p.active_stride] || p.active[(2 * q0 + 1) * p.active_stride];
+    if (!act[0]) return;
+    const Nbr nb = neighbours(g, s, p.parity);
+    const long long cs = g.Vh * P;
+    const float4 *in = static_cast<const float4 *>(p.in) + q0;
+    const int grp = p.grp_of[2 * q0];
+    const void *lown = p.links[p.parity], *loth = p.links[1 - p.parity];
+    const long long Vh = g.Vh;
+    const float4 *mine = sbuf + threadIdx.x;
+    const unsigned smine = (unsigned)__cvta_generic_to_shared(mine);
+    const int nbi[8] = {nb.f[0], nb.b[0], nb.f[1], nb.b[1], nb.f[2], nb.b[2], nb.f[3], nb.b[3]};
+#pragma unroll
+    for (int d = 0; d < ST; d++) {
+        const int mu = d / 2;
+        stage_issue<LF, BD>(smine + d * kSlot * BD * 16, in + (long long)nbi[d] * P, cs,
+                            (d & 1) ? loth : lown, Vh, (d & 1) ? (long long)nb.b[mu] : s, mu);
+        cp_async_commit();
+    }
+    // the epilogue's operands: into L1 now, read at the end
+    {
+        const float4 *cl = static_cast<const float4 *>(p.clov[grp]) + s;
+#pragma unroll 1
+        for (int k = 0; k < 18; k++) prefetch_l1(cl + k * Vh);
+        if (EPI == EPI_XMY_AINV) {
+            const float4 *xin = static_cast<const float4 *>(p.x) + s * P + q0;
+#pragma unroll 1
+            for (int k = 0; k < 12; k++) prefetch_l1(xin + k * cs);
+        }
+    }
+    const float *ht = static_cast<const float *>(p.hop) + (long long)grp * 8 * g.Lmax;
+    const float hc[8] = {ht[0 * g.Lmax + nb.t], ht[1 * g.Lmax + nb.t], ht[2 * g.Lmax + nb.x],
+                         ht[3 * g.Lmax + nb.x], ht[4 * g.Lmax + nb.y], ht[5 * g.Lmax + nb.y],
+                         ht[6 * g.Lmax + nb.z], ht[7 * g.Lmax + nb.z]};
+    C2 acc[1][12];
+#pragma unroll
+    for (int j = 0; j < 12; j++) acc[0][j] = {0ull, 0ull};
+    staged_step<LF, ST, BD, 0>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    staged_step<LF, ST, BD, 1>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    staged_step<LF, ST, BD, 2>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    staged_step<LF, ST, BD, 3>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    staged_step<LF, ST, BD, 4>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    staged_step<LF, ST, BD, 5>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    staged_step<LF, ST, BD, 6>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    staged_step<LF, ST, BD, 7>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    finish32<EPI, 1>(p, acc, act, s, q0, grp, cs);
+}
+
 template <int EPI>
 cudaError_t launch64(const DslashParams &p, int block, cudaStream_t st)
 {
@@ -492,6 +719,49 @@ cudaError_t launch32(const DslashParams &p, int epi, int block, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// the largest staged shape (3 stages x 128 threads) needs 90 KB of dynamic
+// shared memory; the opt-in is set once per kernel, outside any capture
+template <int LF, int EPI, int ST, int BD>
+cudaError_t launch32s_k(const DslashParams &p, cudaStream_t st)
+{
+    constexpr int smem = ST * kSlot * BD * 16;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_dslash32s<LF, EPI, ST, BD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
+    const long long threads = p.g.Vh * (p.nrhs / 2);
+    const unsigned grid = (unsigned)((threads + BD - 1) / BD);
+    k_dslash32s<LF, EPI, ST, BD><<<grid, BD, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int LF, int EPI, int ST>
+cudaError_t launch32s_b(const DslashParams &p, int block, cudaStream_t st)
+{
+    switch (block) {
+    case 64: return launch32s_k<LF, EPI, ST, 64>(p, st);
+    case 96: return launch32s_k<LF, EPI, ST, 96>(p, st);
+    case 128: return launch32s_k<LF, EPI, ST, 128>(p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LF, int EPI>
+cudaError_t launch32s(const DslashParams &p, int block, int stages, cudaStream_t st)
+{
+    switch (stages) {
+    case 2: return launch32s_b<LF, EPI, 2>(p, block, st);
+    case 3: return launch32s_b<LF, EPI, 3>(p, block, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LF>
+cudaError_t launch32s_epi(const DslashParams &p, int epi, int block, int stages, cudaStream_t st)
+{
+    if (epi == EPI_AINV) return launch32s<LF, EPI_AINV>(p, block, stages, st);
+    return launch32s<LF, EPI_XMY_AINV>(p, block, stages, st);
+}
+
 }  // namespace
 
 bool dslash_rpt_ok(int nrhs, int rpt, int prec, int epi)
@@ -504,8 +774,16 @@ bool dslash_rpt_ok(int nrhs, int rpt, int prec, int epi)
     return rpt == 4 && nrhs % 4 == 0 && (epi == EPI_AINV || epi == EPI_XMY_AINV);
 }
 
+bool dslash_staged_ok(int prec, int link_fmt, int epi, int rpt, int stages, int block)
+{
+    return prec == 1 && rpt == 2 && stages >= 2 && stages <= 3 &&
+           (block == 64 || block == 96 || block == 128) &&
+           (epi == EPI_AINV || epi == EPI_XMY_AINV) &&
+           (link_fmt == LINK_F32_12 || link_fmt == LINK_H16_12 || link_fmt == LINK_B16_12);
+}
+
 cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi, int block,
-                          int rpt, cudaStream_t st)
+                          int rpt, cudaStream_t st, int stages)
 {
     if (block <= 0 || block > 256 || (block & 31)) return cudaErrorInvalidValue;
     if (p.nrhs < 1 || p.nrhs > kMaxRhs || !dslash_rpt_ok(p.nrhs, rpt, prec, epi))
@@ -521,6 +799,12 @@ cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi
         case EPI_XMY_G5: return launch64<EPI_XMY_G5>(p, block, st);
         default: return cudaErrorInvalidValue;
         }
+    }
+    if (stages > 0) {
+        if (!dslash_staged_ok(prec, link_fmt, epi, rpt, stages, block)) return cudaErrorInvalidValue;
+        if (link_fmt == LINK_F32_12) return launch32s_epi<LINK_F32_12>(p, epi, block, stages, st);
+        if (link_fmt == LINK_H16_12) return launch32s_epi<LINK_H16_12>(p, epi, block, stages, st);
+        return launch32s_epi<LINK_B16_12>(p, epi, block, stages, st);
     }
     const int ppt = rpt / 2;
     if (link_fmt == LINK_F32_12)

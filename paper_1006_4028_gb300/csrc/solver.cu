@@ -62,14 +62,24 @@ dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void
     const char *name = op.pr == 0 ? "dslash_fp64" : "dslash_fp32";
     cudaEvent_t ev;
     c->time_begin(name, &ev);
-    const int rpt = (epi == EPI_AINV || epi == EPI_XMY_AINV) ? op.rpt : (op.pr == 0 ? 1 : 2);
-    CK(launch_dslash(P, op.pr, op.lf, epi, op.block, rpt, c->stream));
+    const bool schur = epi == EPI_AINV || epi == EPI_XMY_AINV;
+    const int rpt = schur ? op.rpt : (op.pr == 0 ? 1 : 2);
+    const int stages =
+        schur && dslash_staged_ok(op.pr, op.lf, epi, rpt, op.stages, op.block) ? op.stages : 0;
+    CK(launch_dslash(P, op.pr, op.lf, epi, op.block, rpt, c->stream, stages));
     c->time_end(name, ev);
     c->launches++;
     return DP_OK;
 }
 
 constexpr int kStateStride = (int)(sizeof(RhsState) / sizeof(int));
+
+void set_shape(Op &op, const Shape &sh)
+{
+    op.block = sh.block;
+    op.rpt = sh.rpt;
+    op.stages = sh.stages;
+}
 
 const int *state_mask(const RhsState *st) { return st ? &st[0].active : nullptr; }
 
@@ -209,7 +219,7 @@ dp_status Batch::init()
     op64.links[1] = f->l64[1];
     op64.hop = hop64_d;
     op64.nrhs = n;
-    c->launch_shape(Vh, 0, LINK_F64_18, n, &op64.block, &op64.rpt);
+    set_shape(op64, c->launch_shape(Vh, 0, LINK_F64_18, n));
     opin = op64;
     opin.pr = ipr;
     opin.lf = ilf;
@@ -218,7 +228,7 @@ dp_status Batch::init()
         if (e != DP_OK) return e;
     }
     opin.hop = ipr == 0 ? (const void *)hop64_d : (const void *)hop32_d;
-    c->launch_shape(Vh, ipr, ilf, n, &opin.block, &opin.rpt);
+    set_shape(opin, c->launch_shape(Vh, ipr, ilf, n));
     opin_adj = opin;
     opin_adj.hop = ipr == 0 ? (const void *)hopadj64_d : (const void *)hopadj32_d;
     check_every = opts.check_every > 0 ? opts.check_every : (Vh * n >= (1 << 20) ? 2 : 8);
@@ -357,17 +367,20 @@ dp_status Batch::admit(Job *j)
     cp.nrhs = n;
     const int src_par = (j->grp.src[0] + j->grp.src[1] + j->grp.src[2] + j->grp.src[3]) & 1;
     if (src_par == sp) {
-        // point source on the Schur parity: eta'_q = 0, bhat = A_pp^-1 eta'_p
+        // point source on the Schur parity: eta'_q = 0, bhat = A_pp^-1 eta'_p,
+        // non-zero at the source site only
         for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[sp][k];
         cp.in = y64;
         cp.out = bh;
-        CK(launch_clover_apply(cp, 0, c->stream));
+        CK(blas_zero_masked(bh, Vh, n, mask_d, c->stream));
+        CK(launch_clover_point(cp, g, slots_d, sp, c->stream));
     } else {
-        // to64 <- A_qq^-1 eta'_q (in place), bhat = A_pp^-1 (eta'_p - D_pq to64)
+        // to64 <- A_qq^-1 eta'_q (in place, at the source site), bhat =
+        // A_pp^-1 (eta'_p - D_pq to64)
         for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[1 - sp][k];
         cp.in = to64;
         cp.out = to64;
-        CK(launch_clover_apply(cp, 0, c->stream));
+        CK(launch_clover_point(cp, g, slots_d, 1 - sp, c->stream));
         s = dslash(c, op64, sp, EPI_AINV_XMY, to64, bh, y64, mask_d, 1);
         if (s != DP_OK) return s;
     }
@@ -608,18 +621,18 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
         for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[1 - sp][k];
         cp.in = to64;
         cp.out = to64;
-        CK(launch_clover_apply(cp, 0, c->stream));
+        CK(launch_clover_point(cp, g, slots_d, 1 - sp, c->stream));
         CK(blas_sub64_masked(to64, t64, y64, Vh, n, mask_d, c->stream));
         // residual report: the full residual of (D'+M)S' = eta' is (A_pp rhat, 0)
-        // with x_q rebuilt from x_p, so |A_pp rhat| / |eta'|
+        // with x_q rebuilt from x_p, so |A_pp rhat| / |eta'| (a few digits:
+        // FP32 products, FP64 sums)
         for (int k = 0; k < kMaxGroups; k++) {
-            cp.mat[k] = f->clov[sp];
+            cp.mat[k] = f->clov32[sp];
             cp.diag[k] = jobs[k] ? 4.0 + jobs[k]->grp.M : 0.0;
         }
         cp.in = r64;
-        cp.out = to64;
-        CK(launch_clover_apply(cp, 0, c->stream));
-        CK(blas_norm2(c->bc, 0, to64, Vh, n, nrm_d, c->stream));
+        cp.out = nullptr;
+        CK(launch_clover_norm(c->bc, cp, nrm_d, c->stream));
         double2 *prop_d = nullptr;
         void *prop_tmp = nullptr;
         if (j->prop_host) {
@@ -918,8 +931,11 @@ dp_status dp_schur_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *
     s = get_clover_inv(&c, f, M, &ci);
     if (s != DP_OK) return s;
     for (int q = 0; q < 2; q++) op.inv[q][0] = pr == 0 ? (const void *)ci->inv64[q] : (const void *)ci->inv32[q];
-    c.launch_shape(g.Vh, pr, lf, nrhs, &op.block, &op.rpt);
-    if (!dslash_rpt_ok(nrhs, op.rpt, pr, EPI_AINV)) op.rpt = pr == 0 ? 1 : 2;
+    set_shape(op, c.launch_shape(g.Vh, pr, lf, nrhs));
+    if (!dslash_rpt_ok(nrhs, op.rpt, pr, EPI_AINV)) {
+        op.rpt = pr == 0 ? 1 : 2;
+        op.stages = 0;
+    }
     const size_t tb = hop.size() * (pr == 0 ? sizeof(double) : sizeof(float));
     const size_t vb = (size_t)g.Vh * nrhs * 24 * (pr == 0 ? 8 : 4);
     void *hd = c.alloc(tb), *had = c.alloc(tb), *tp = c.alloc(vb), *tq = c.alloc(vb);

@@ -146,12 +146,18 @@ def test_invalid_arguments_are_errors(ctx):
         dp.dp_field_free(ctx, f)
 
 
-@pytest.mark.parametrize("prec,tol,rpts", [("mixed_fp32", 1e-6, (2, 4)),
-                                           ("fp64", 1e-13, (1,))])
+# (RHS per thread, shared-memory stages, threads per block); 96, 128 and 160
+# threads leave a ragged last block on the 8x4x6x4 lattice (2304 pairs)
+SHAPES32 = [(2, 0, 64), (4, 0, 64), (2, 2, 64), (2, 3, 128), (2, 3, 96), (2, 2, 96),
+            (4, 0, 256), (2, 0, 160)]
+
+
+@pytest.mark.parametrize("prec,tol,rpts", [("mixed_fp32", 1e-6, SHAPES32),
+                                           ("fp64", 1e-13, [(1, 0, 64), (1, 0, 160)])])
 def test_schur_launch_all_rhs_per_thread(ctx, setup, prec, tol, rpts):
     """out_e = A_ee^-1 D_eo psi_o on packed device spinors (the solver's launch),
-    for every launch shape (RHS per thread): equal to each other and, through
-    A_ee out_e = D_eo psi_o, to the oracle."""
+    for every launch shape (RHS per thread, staging, block): bit-identical to
+    each other and, through A_ee out_e = D_eo psi_o, equal to the oracle."""
     torch = pytest.importorskip("torch")
     dims, f, op, _ = setup
     M = 0.2
@@ -178,10 +184,10 @@ def test_schur_launch_all_rhs_per_thread(ctx, setup, prec, tol, rpts):
 
     xin = dev(od)
     outs = []
-    for r in rpts:
+    for r, stages, block in rpts:
         out = torch.zeros_like(xin)
         dp.dp_dslash_dev(ctx, f, M, prof, prec, 1, 0, xin.data_ptr(), out.data_ptr(), 12,
-                         0, r, 1)
+                         block, r, 1, stages=stages)
         torch.cuda.synchronize()
         outs.append(host(out))
     for o in outs[1:]:
