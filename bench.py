@@ -166,9 +166,9 @@ def serve_leg(dp, ctx, field, capacity, rng, n_req, load):
         while time.perf_counter() - t0 < arrivals[k]:
             time.sleep(min(0.002, max(0.0, arrivals[k] - (time.perf_counter() - t0))))
         M = float(rng.uniform(0.01, 0.8))
-        prof = ("cosh_t", 0.4) if M >= 0.3 else ("cosh_4d", 0.2)
+        prof = heavy_or_light(M)
         src = tuple(int(rng.integers(0, d)) for d in DIMS)
-        reqs.append(dp.dp_submit(ctx, field, M, prof, src, 1e-10))
+        reqs.append(dp.dp_submit(ctx, field, M, prof, src, light_residue(1e-10, prof, DIMS)))
     bad = 0
     for t in reqs:
         _, info = dp.dp_wait(ctx, t, DIMS[0], timeout_s=600)
@@ -179,8 +179,9 @@ def serve_leg(dp, ctx, field, capacity, rng, n_req, load):
     return {"requests": n_req, "offered_load": load, "offered_rate_per_s": rate,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
             "solves_per_s": st["solves_per_s"], "wall_s": wall, "not_converged": bad,
-            "mix": "M ~ U[0.01, 0.8]; heavy cosh-t alpha0=0.4 if M >= 0.3 else cosh-4d "
-                   "alpha0=0.2; r = 1e-10; up to 4 requests (48 RHS) per batch"}
+            "mix": "M ~ U[0.01, 0.8]; heavy cosh-t alpha0=0.4 (0.5 above M = 0.65) if M >= 0.3 "
+                   "else cosh-4d alpha0=0.2; r = 1e-10 (light: / profile range, >= 3e-14); up to "
+                   "4 requests (48 RHS) per batch"}
 
 
 def run_reference(args):
@@ -227,6 +228,345 @@ LINKS = {"mixed_fp32": "12-real FP32 links", "mixed_fp16": "12-real FP16 links +
          "mixed_bf16": "12-real BF16 links + FP32 scale"}
 
 
+# ---- the other workloads of the study (each prints one JSON line) ----------
+def heavy_or_light(M):
+    """Profile per mass: heavy (M >= 0.3) cosh-t with alpha0 = min(ln(1+M), 0.5)
+    rounded as 0.4 / 0.5; light cosh-4d with alpha0 = 0.2."""
+    if M >= 0.3:
+        return ("cosh_t", 0.4 if M < 0.65 else 0.5)
+    return ("cosh_4d", 0.2)
+
+
+def profile_range(prof, dims):
+    """max / min of alpha_B over the lattice for a profile (kind, alpha0)."""
+    kind, a0 = prof[0], prof[1]
+    if kind == "cosh_4d":
+        return float(np.prod([np.cosh(a0 * L / 2) for L in dims]))
+    if kind == "cosh_t":
+        return float(np.cosh(a0 * dims[0] / 2))
+    if kind == "exp_t":
+        return float(np.exp(a0 * (dims[0] - 1)))
+    return 1.0
+
+
+def light_residue(r, prof, dims, floor=3e-14):
+    """Residue for a light (cosh-4d) request: the restored far slices carry
+    about r x (the profile's range) relative error, so the residue is divided
+    by that range (not below the FP64 floor) to keep C_PP to T/2 as accurate
+    as an unpreconditioned solve at r.  Heavy profiles need no change: they
+    make the far slices more accurate."""
+    if prof[0] != "cosh_4d":
+        return r
+    return max(r / profile_range(prof, dims), floor)
+
+
+def slice_err(cpp, ref, upto):
+    c, r = np.asarray(cpp)[: upto + 1], np.asarray(ref)[: upto + 1]
+    return float(np.max(np.abs(c / r - 1)))
+
+
+def _timed(fn):
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def config_free16(dp, ctx, args):
+    """Free theory 16x8^3 (U = 1), antiperiodic time, M = 0.5, exp profile
+    alpha0 = 0.4, origin source, r = 1e-11; C_PP against the exact
+    momentum-space values stored under tests/golden."""
+    import lattice_inputs as li
+
+    dims = (16, 8, 8, 8)
+    f = dp.dp_field_load(ctx, li.unit_links(dims), dims, -1)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "free_16x8_M0.5.json")))["cpp"]
+    res = {}
+    for name, o in (("fp64_plain", {"prec": "fp64", "batched": 0, "use_graph": 0}),
+                    ("mixed_batched", {"prec": "mixed_fp32", "batched": 1, "use_graph": 1})):
+        for _ in range(args.warmup):
+            dp.dp_solve_point(ctx, f, 0.5, ("exp_t", 0.4), (0, 0, 0, 0), 1e-11, o, T=16)
+        ts = []
+        for _ in range(args.steps):
+            (cpp, _, info), dt = _timed(
+                lambda: dp.dp_solve_point(ctx, f, 0.5, ("exp_t", 0.4), (0, 0, 0, 0), 1e-11, o, T=16))
+            ts.append(dt)
+        meff = [float(np.log(cpp[t] / cpp[t + 1])) for t in range(8)]
+        res[name] = {"solves_per_s": 1.0 / float(np.median(ts)), "ms_per_solve": 1e3 * float(np.median(ts)),
+                     "iters_inner": info["iters_inner"], "iters_outer": info["iters_outer"],
+                     "true_rel_residue": info["true_rel_residue"],
+                     "per_slice_rel_err_vs_exact_max_to_T2": slice_err(cpp, gold, 8),
+                     "per_slice_rel_err_vs_exact_all": slice_err(cpp, gold, 15),
+                     "effective_mass_0_7": meff}
+    dp.dp_field_free(ctx, f)
+    return {"workload": "free theory 16x8^3 (U = 1), M = 0.5, exp_t alpha0 = 0.4, r = 1e-11",
+            "reference": "exact momentum-space C_PP (tests/golden/free_16x8_M0.5.json)", **res}
+
+
+def config_light64(dp, ctx, args):
+    """Light quarks on 64x32^3 (eps = 0.5, seed 7, c_sw = 1.9): M in {0.02,
+    0.01, 0.005}, cosh-4d profile alpha0 in {0 (unpreconditioned), 0.2, 0.4},
+    16-bit (FP16) links in the FP32 inner solver, FP64 outer loop, r = 1e-10.
+    Iteration counts and solves/s; the restored C_PP of the preconditioned
+    solves against the unpreconditioned one."""
+    import lattice_inputs as li
+
+    dims = (64, 32, 32, 32)
+    U = li.su3_links(dims, 0.5, 7)
+    f = dp.dp_field_load(ctx, U, dims, -1)
+    del U
+    dp.dp_field_set_csw(ctx, f, 1.9)
+    prec = args.prec if args.prec != "mixed_fp32" else "mixed_fp16"
+    dp.dp_autotune(ctx, f, prec, 1, 12)
+    dp.dp_autotune(ctx, f, "fp64", 0, 12)
+    o = {"prec": prec, "batched": 1, "use_graph": 1, "max_iter": 40000}
+    rows = []
+    src = (0, 0, 0, 0)
+    dp.dp_solve_point(ctx, f, 0.02, ("cosh_4d", 0.2), src, 1e-10, o, T=64)  # warm-up
+    for M in (0.02, 0.01, 0.005):
+        base = None
+        for a0 in (0.0, 0.2, 0.4):
+            prof = ("none", 0.0) if a0 == 0 else ("cosh_4d", a0)
+            (cpp, _, info), dt = _timed(lambda: dp.dp_solve_point(ctx, f, M, prof, src, 1e-10, o, T=64))
+            row = {"M": M, "alpha0": a0, "profile": prof[0], "iters_inner": info["iters_inner"],
+                   "iters_outer": info["iters_outer"], "true_rel_residue": info["true_rel_residue"],
+                   "status": info["status"], "seconds": dt}
+            if base is None:
+                base = cpp
+            else:
+                dev = np.abs(np.asarray(cpp)[:33] / np.asarray(base)[:33] - 1)
+                row["cpp_rel_diff_vs_unprec_max_to_T2"] = float(dev.max())
+                over = np.nonzero(dev > 1e-6)[0]
+                row["first_slice_over_1e-6"] = int(over[0]) if len(over) else None
+            rows.append(row)
+    # the 4D profile's range beta_max / beta_min (cosh(a0 L/2) per direction)
+    # sets how far the preconditioned residue must go for the far slices:
+    # one tighter solve at M = 0.005 for each alpha0 and one FP32-link run
+    M = 0.005
+    (ref, _, _), _ = _timed(lambda: dp.dp_solve_point(ctx, f, M, ("none", 0.0), src, 1e-13, o, T=64))
+    for a0, r, pr in ((0.2, 1e-13, prec), (0.4, 1e-13, prec), (0.2, 1e-10, "mixed_fp32")):
+        oo = dict(o, prec=pr)
+        (cpp, _, info), dt = _timed(lambda: dp.dp_solve_point(ctx, f, M, ("cosh_4d", a0), src, r, oo, T=64))
+        dev = np.abs(np.asarray(cpp)[:33] / np.asarray(ref)[:33] - 1)
+        over = np.nonzero(dev > 1e-6)[0]
+        rng_ = float(np.cosh(a0 * 32) * np.cosh(a0 * 16) ** 3)
+        rows.append({"M": M, "alpha0": a0, "profile": "cosh_4d", "r": r, "inner": pr,
+                     "iters_inner": info["iters_inner"], "iters_outer": info["iters_outer"],
+                     "true_rel_residue": info["true_rel_residue"], "status": info["status"],
+                     "seconds": dt, "profile_range": rng_,
+                     "cpp_rel_diff_vs_unprec_r1e-13_max_to_T2": float(dev.max()),
+                     "first_slice_over_1e-6": int(over[0]) if len(over) else None})
+    dp.dp_field_free(ctx, f)
+    return {"workload": "light-quark solves 64x32^3 (eps 0.5, seed 7, c_sw 1.9), r = 1e-10",
+            "inner": "%s (%s) in FP64 defect correction" % (prec, LINKS[prec]), "solves": rows}
+
+
+def config_multimass32(dp, ctx, args):
+    """32x16^3 (eps = 0.4, seed 3, c_sw = 1.7), one point source, 12 RHS x 4
+    masses {0.01, 0.1, 0.5, 0.8} each with its own profile, one 48-RHS batch:
+    default vs autotuned launch shapes, CUDA graphs on and off, and the
+    12-RHS FP32 dslash against the HBM roofline."""
+    import torch
+
+    import lattice_inputs as li
+
+    dims = (32, 16, 16, 16)
+    f = dp.dp_field_load(ctx, li.su3_links(dims, 0.4, 3), dims, -1)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    Ms = [0.01, 0.1, 0.5, 0.8]
+    profs = [heavy_or_light(M) for M in Ms]
+    out = torch.zeros(4 * 32, dtype=torch.float64, device="cuda")
+    src = (3, 5, 7, 9)
+    res = {}
+
+    def run(label, graphs):
+        o = {"prec": "mixed_fp32", "compress12": 1, "batched": 1, "use_graph": graphs}
+        for _ in range(max(1, args.warmup)):
+            dp.dp_solve_point_dev(ctx, f, Ms, profs, src, 1e-10, out.data_ptr(), o)
+        ts = []
+        for _ in range(args.steps):
+            infos, dt = _timed(lambda: dp.dp_solve_point_dev(ctx, f, Ms, profs, src, 1e-10,
+                                                             out.data_ptr(), o))
+            ts.append(dt)
+        res[label] = {"ms_per_48rhs_solve": 1e3 * float(np.median(ts)),
+                      "solves_per_s": 4.0 / float(np.median(ts)),
+                      "iters_inner": [i["iters_inner"] for i in infos],
+                      "true_rel_residue_max": max(i["true_rel_residue"] for i in infos)}
+
+    run("fixed_shape_graphs", 1)
+    shape = dp.dp_autotune(ctx, f, "mixed_fp32", 1, 48)
+    dp.dp_autotune(ctx, f, "fp64", 0, 48)
+    run("autotuned_graphs", 1)
+    run("autotuned_no_graphs", 0)
+    res["tuned_shape_48rhs"] = {"block": shape[0], "rhs_per_thread": shape[1], "stages": shape[2],
+                                "ms": shape[3]}
+    # 12-RHS FP32 dslash in isolation: default vs tuned shape
+    nb = dp.dp_spinor_bytes(ctx, f, "mixed_fp32", 12)
+    a = torch.randn(nb // 4, device="cuda")
+    b = torch.empty_like(a)
+    Vh = int(np.prod(dims)) // 2
+    byt = Vh * (12 * 48 * 4 + 8 * 48 + 72 * 4)
+    hbm, src_pk = peaks()
+    for label, kw in (("dslash12_fixed", dict(block_threads=64, rhs_per_thread=2, stages=0)),
+                      ("dslash12_tuned", dict(block_threads=0, rhs_per_thread=0, stages=-1))):
+        if label == "dslash12_tuned":
+            dp.dp_autotune(ctx, f, "mixed_fp32", 1, 12)
+        dp.dp_dslash_dev(ctx, f, 0.5, ("cosh_t", 0.4), "mixed_fp32", 1, 0, a.data_ptr(), b.data_ptr(),
+                         12, iters=5, **kw)
+        ms = dp.dp_dslash_dev(ctx, f, 0.5, ("cosh_t", 0.4), "mixed_fp32", 1, 0, a.data_ptr(),
+                              b.data_ptr(), 12, iters=50, **kw)
+        res[label] = {"avg_launch_ms": ms, "achieved_gbs": byt / (ms / 1e3) / 1e9,
+                      "frac_of_hbm": byt / (ms / 1e3) / 1e9 / hbm, "peak_source": src_pk,
+                      "note": "inputs %d MB > 129 MB L2 only in part at this volume" % (nb >> 20)}
+    dp.dp_field_free(ctx, f)
+    return {"workload": "multi-mass 32x16^3 (eps 0.4, seed 3), 12 RHS x 4 masses in one batch, "
+                        "r = 1e-10", "masses": Ms, "profiles": [list(p) for p in profs], **res}
+
+
+def config_sf48(dp, ctx, args):
+    """Dirichlet time boundary (the Schroedinger-functional-like setting of
+    the end of Sec. II) on 48x24^3 (eps = 0.3, seed 1, c_sw = 1.7), heavy
+    quark M = 0.5, source on the first time slice: the correlator falls over
+    the whole time extent.  Unpreconditioned and exp-profile (alpha0 = 0.4)
+    solves at the loose residue r = 1e-6 against a tight (r = 1e-12)
+    reference, per time slice over all 48 slices."""
+    import lattice_inputs as li
+
+    dims = (48, 24, 24, 24)
+    f = dp.dp_field_load(ctx, li.su3_links(dims, 0.3, 1), dims, 0)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    dp.dp_autotune(ctx, f, "mixed_fp32", 1, 12)
+    o = {"prec": "mixed_fp32", "batched": 1, "use_graph": 1}
+    src = (0, 0, 0, 0)
+    ref, _, iref = dp.dp_solve_point(ctx, f, 0.5, ("exp_t", 0.4), src, 1e-12, o, T=48)
+    rows = []
+    for prof, r in ((("none", 0.0), 1e-6), (("exp_t", 0.4), 1e-6), (("none", 0.0), 1e-11),
+                    (("exp_t", 0.4), 1e-11)):
+        (cpp, _, info), dt = _timed(lambda: dp.dp_solve_point(ctx, f, 0.5, prof, src, r, o, T=48))
+        dev = np.abs(np.asarray(cpp) / np.asarray(ref) - 1)
+        over = np.nonzero(dev > 1e-6)[0]
+        rows.append({"profile": list(prof), "r": r, "iters_inner": info["iters_inner"],
+                     "iters_outer": info["iters_outer"], "seconds": dt,
+                     "per_slice_rel_dev_max_all_slices": float(dev.max()),
+                     "first_slice_over_1e-6": int(over[0]) if len(over) else None})
+    dp.dp_field_free(ctx, f)
+    return {"workload": "Dirichlet-time heavy quark 48x24^3 (eps 0.3, seed 1), M = 0.5, source on "
+                        "slice 0", "reference": "exp_t alpha0 = 0.4 at r = 1e-12",
+            "cpp_ref_0_over_47": float(ref[0] / ref[47]), "solves": rows}
+
+
+def config_serve(dp, ctx, args):
+    """Serving stream against 4 resident fields (16x8^3, 32x16^3, 48x24^3,
+    64x32^3; eps 0.3, 0.4, 0.45, 0.5; seeds 101-104; c_sw 1.7): Poisson
+    arrivals at 0.5x, 0.9x, 1.2x the measured capacity; each request a random
+    field, source and M ~ U[0.01, 0.8] with its heavy or light profile, r =
+    1e-10 (light: divided by the profile's range, see light_residue).  p50/p99
+    latency and solves/s; the capacity against the plain single-RHS FP64 GPU
+    solver on one sampled request per field, whose C_PP also checks the
+    served results per time slice."""
+    import lattice_inputs as li
+
+    spec = [((16, 8, 8, 8), 0.3, 101), ((32, 16, 16, 16), 0.4, 102),
+            ((48, 24, 24, 24), 0.45, 103), ((64, 32, 32, 32), 0.5, 104)]
+    fields = []
+    for dims, eps, seed in spec:
+        f = dp.dp_field_load(ctx, li.su3_links(dims, eps, seed), dims, -1)
+        dp.dp_field_set_csw(ctx, f, 1.7)
+        dp.dp_autotune(ctx, f, "mixed_fp32", 1, 48)
+        fields.append((f, dims))
+    rng = np.random.default_rng(2024)
+
+    def draw(k=None):
+        k = int(rng.integers(0, 4)) if k is None else k
+        f, dims = fields[k]
+        M = float(rng.uniform(0.01, 0.8))
+        src = tuple(int(rng.integers(0, d)) for d in dims)
+        prof = heavy_or_light(M)
+        return k, f, dims, M, prof, src, light_residue(1e-10, prof, dims)
+
+    # capacity: requests/s of the scheduler fed back to back
+    n_cap = max(12, args.serve_requests)
+    budget = int(200e9)  # of the 288 GB; the four fields take under 10 GB
+    dp.dp_serve_start(ctx, budget, 48)
+    t0 = time.perf_counter()
+    tk = [(dp.dp_submit(ctx, r[1], r[3], r[4], r[5], r[6]), r[2]) for r in (draw() for _ in range(n_cap))]
+    for t, dims in tk:
+        dp.dp_wait(ctx, t, dims[0], timeout_s=1200)
+    cap = n_cap / (time.perf_counter() - t0)
+    dp.dp_serve_stop(ctx, True)
+    legs = []
+    for load in (0.5, 0.9, 1.2):
+        rate = cap * load
+        dp.dp_serve_start(ctx, budget, 48)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.serve_requests))
+        reqs = []
+        t0 = time.perf_counter()
+        for k in range(args.serve_requests):
+            while time.perf_counter() - t0 < arrivals[k]:
+                time.sleep(min(0.002, max(0.0, arrivals[k] - (time.perf_counter() - t0))))
+            r = draw()
+            reqs.append((dp.dp_submit(ctx, r[1], r[3], r[4], r[5], r[6]), r))
+        bad = 0
+        for t, r in reqs:
+            _, info = dp.dp_wait(ctx, t, r[2][0], timeout_s=1200)
+            bad += info["status"] != 0
+        st = dp.dp_serve_stats_get(ctx)
+        dp.dp_serve_stop(ctx, True)
+        legs.append({"offered_load": load, "offered_rate_per_s": rate, "requests": args.serve_requests,
+                     "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                     "solves_per_s": st["solves_per_s"], "not_converged": bad,
+                     "wall_s": time.perf_counter() - t0})
+    # one request per field, served (alone) and through the plain FP64 solver
+    o64 = {"prec": "fp64", "batched": 0, "use_graph": 0, "max_iter": 400000}
+    t64, errs, sample = 0.0, [], []
+    dp.dp_serve_start(ctx, budget, 48)
+    for k in range(4):
+        r = draw(k)
+        _, f, dims, M, prof, src, res = r
+        t = dp.dp_submit(ctx, f, M, prof, src, res)
+        cpp_served, _ = dp.dp_wait(ctx, t, dims[0], timeout_s=1200)
+        (cpp64, _, i64), dt = _timed(lambda: dp.dp_solve_point(ctx, f, M, prof, src, res, o64, T=dims[0]))
+        t64 += dt
+        e = slice_err(cpp_served, cpp64, dims[0] // 2)
+        errs.append(e)
+        sample.append({"dims": list(dims), "M": M, "profile": list(prof), "r": res, "fp64_s": dt,
+                       "fp64_iters": i64["iters_inner"], "per_slice_rel_err_to_T2": e})
+    dp.dp_serve_stop(ctx, True)
+    fp64_rate = 4 / t64
+    for f, _ in fields:
+        dp.dp_field_free(ctx, f)
+    return {"workload": "serving stream, 4 resident fields (16x8^3, 32x16^3, 48x24^3, 64x32^3)",
+            "capacity_requests_per_s": cap, "legs": legs,
+            "fp64_plain": {"solves_per_s": fp64_rate, "sample": sample},
+            "capacity_over_fp64_plain": cap / fp64_rate,
+            "served_vs_fp64_per_slice_rel_err_max_to_T2": max(errs),
+            "note": "request counts scaled down from the study's 2000 to fit a few minutes; "
+                    "light requests use r = 1e-10 / profile range (>= 3e-14)"}
+
+
+def run_config(args):
+    import torch
+
+    import paper_1006_4028_gb300 as dp
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    dp.load()
+    ctx = dp.dp_create(0, torch.cuda.current_stream().cuda_stream)
+    fn = {"free16": config_free16, "light64": config_light64, "multimass32": config_multimass32,
+          "serve": config_serve, "sf48": config_sf48}[args.config]
+    t0 = time.perf_counter()
+    line = fn(dp, ctx, args)
+    line = {"config_mode": args.config, "wall_s": time.perf_counter() - t0, **line}
+    dp.dp_destroy(ctx)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -236,6 +576,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-df", action="store_true",
+                    help="skip the leg with the outer Schur operator in double-float")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-load", type=float, default=0.9,
                     help="offered load as a fraction of the measured batch-solve rate")
@@ -246,6 +588,10 @@ def main():
                     help="inner-solver precision (links: 12 FP32 reals, or 12 16-bit reals "
                          "plus one FP32 scale)")
     ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "cgne"])
+    ap.add_argument("--config", default="heavy48",
+                    choices=["heavy48", "free16", "light64", "multimass32", "serve", "sf48"],
+                    help="heavy48: the headline solves/s line (default); the others run the "
+                         "study's other workloads and print their own JSON line")
     ap.add_argument("--graphs", type=int, default=0,
                     help="capture solver iterations as CUDA graphs in the timed region "
                          "(per-kernel event timing needs them off)")
@@ -260,6 +606,8 @@ def main():
         args.no_cpu_baseline = True
     if args.impl == "reference":
         return run_reference(args)
+    if args.config != "heavy48":
+        return run_config(args)
 
     ws, rank, local = dist_env()
     import torch
@@ -432,6 +780,42 @@ def main():
         line["fp64_plain"] = {"solves_per_s": 1.0 / s64, "ms_per_solve": s64 * 1e3,
                               "iters_inner": i64["iters_inner"],
                               "speedup_of_value": value / ws * s64}
+    if rank == 0 and not args.no_df:
+        # the same solves with the outer loop's Schur operator in double-float
+        # (two FP32 per real) instead of FP64
+        o_df = dict(opts, outer_df=1)
+        for _ in range(2):
+            dp.dp_solve_point_dev(ctx, field, [MASS], [prof], rand_src(), RES, cpp_dev.data_ptr(), o_df)
+        torch.cuda.synchronize()
+        k_df = max(3, min(args.steps, 5))
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        idf = []
+        for _ in range(k_df):
+            idf += dp.dp_solve_point_dev(ctx, field, [MASS], [prof], rand_src(), RES, cpp_dev.data_ptr(),
+                                         o_df)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        ms_df = d0.elapsed_time(d1) / k_df
+        # kernel times of the outer operator, FP64 vs double-float (one
+        # instrumented solve each)
+        dp.dp_timing_reset(ctx)
+        dp.dp_timing_enable(ctx, True)
+        dp.dp_solve_point_dev(ctx, field, [MASS], [prof], rand_src(), RES, cpp_dev.data_ptr(),
+                              dict(o_df, use_graph=0))
+        dp.dp_solve_point_dev(ctx, field, [MASS], [prof], rand_src(), RES, cpp_dev.data_ptr(),
+                              dict(opts, use_graph=0))
+        torch.cuda.synchronize()
+        ndf, tdf = dp.dp_timing_get(ctx, "dslash_df")
+        n64, t64_ = dp.dp_timing_get(ctx, "dslash_fp64")
+        dp.dp_timing_enable(ctx, False)
+        line["outer_double_float"] = {
+            "outer_operator_ms": {"double_float_two_launches": tdf / max(ndf, 1),
+                                  "fp64_two_launches": t64_ / max(n64, 1) * 2},
+            "solves_per_s": 1e3 / ms_df, "ms_per_solve": ms_df,
+            "iters_inner": float(np.mean([i["iters_inner"] for i in idf])),
+            "outer": float(np.mean([i["iters_outer"] for i in idf])),
+            "true_rel_residue_max": float(max(i["true_rel_residue"] for i in idf))}
     if rank == 0 and not args.no_cpu_baseline:
         dt, thr, napp = cpu_sample()
         iters, src = oracle_iters_per_rhs()
@@ -450,6 +834,11 @@ def main():
         ref = np.asarray(g["cpp"])
         line["per_slice_rel_err_vs_oracle_max"] = float(np.max(np.abs(c[:T // 2 + 1] /
                                                                       ref[:T // 2 + 1] - 1)))
+        if "outer_double_float" in line:
+            c, _, _ = dp.dp_solve_point(ctx, field, MASS, prof, (0, 0, 0, 0), RES,
+                                        dict(opts, outer_df=1), T=T)
+            line["outer_double_float"]["per_slice_rel_err_vs_oracle_max"] = float(
+                np.max(np.abs(c[:T // 2 + 1] / ref[:T // 2 + 1] - 1)))
     # serving: Poisson arrivals on the resident field through the
     # continuous-batching scheduler; latency from submit to completion
     if not args.no_serve:

@@ -118,6 +118,10 @@ typedef struct {
     int batched;      /* 1: all RHS in one multi-RHS solve; 0: one RHS at a time    */
     int use_graph;    /* capture one solver iteration as a CUDA graph               */
     int check_every;  /* iterations between convergence reads (0: automatic)        */
+    int outer_df;     /* mixed precisions: 1 = the outer loop's Schur operator in
+                         double-float arithmetic (two FP32 per real, ~48-bit
+                         significands, ~1e-14 relative; for r >= 1e-12) on the
+                         FP32 units instead of FP64; 0 = FP64                       */
 } dp_solve_opts;
 
 typedef struct {
@@ -156,7 +160,12 @@ size_t dp_device_bytes(dp_ctx *ctx);
  * times one FP32 scale per link, the largest modulus of those six entries)
  * are made from the FP64 links the first time a DP_PREC_MIXED_FP16 / _BF16
  * call needs them.
- * bc_t = -1 antiperiodic time (the paper's case, Sec. II), +1 periodic. */
+ * bc_t = -1 antiperiodic time (the paper's case, Sec. II), +1 periodic, 0
+ * Dirichlet: no quark hop across t = T-1 <-> 0, the boundary of the
+ * Schroedinger-functional setting the paper recommends the method for (end of
+ * Sec. II; profile exp: alpha_B = exp(+alpha0 y0)).  Only the quark field sees
+ * the boundary: the clover term is built from the given (periodic) links, and
+ * there are no boundary fields or boundary improvement terms. */
 dp_status dp_field_load(dp_ctx *ctx, const double *links, const int dims[4], int bc_t,
                         dp_field *out);
 /* Build the clover term c_sw (i/4) sigma.Fhat for this field (FP64, two
@@ -276,8 +285,10 @@ dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profi
  * layout, 4 needing nrhs % 4 == 0), 0 the tuned or default choice; stages
  * selects how neighbour spinors and links reach the thread: 0 direct loads,
  * 2-3 staged through shared memory with that many of the 8 directions in
- * flight (FP32 or 16-bit 12-real links, 2 RHS per thread, 64, 96 or 128
- * threads per block), -1 the tuned or default choice.
+ * flight, 4 staged (2 in flight) by one persistent wave of blocks whose
+ * threads walk several sites (staging needs FP32 or 16-bit 12-real links, 2
+ * RHS per thread and 64, 96 or 128 threads per block), -1 the tuned or
+ * default choice.
  * FP32 needs nrhs even.  iters launches back to back; if ms_out is non-NULL
  * it receives the average launch time measured with CUDA events on the
  * context stream. */

@@ -56,7 +56,7 @@ class Profile(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("solver", C.c_int), ("prec", C.c_int),
                 ("compress12", C.c_int), ("inner_tol", C.c_double), ("batched", C.c_int),
-                ("use_graph", C.c_int), ("check_every", C.c_int)]
+                ("use_graph", C.c_int), ("check_every", C.c_int), ("outer_df", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -189,6 +189,7 @@ def _opts(o):
     s.batched = int(o.get("batched", 1))
     s.use_graph = int(o.get("use_graph", 1))
     s.check_every = int(o.get("check_every", 0))
+    s.outer_df = int(o.get("outer_df", 0))
     return s
 
 

@@ -151,6 +151,28 @@ dp_status field_links(Ctx *c, Field &f, int link_fmt, int parity, const void **o
     case LINK_F32_12: *out = f.l32c[parity]; return DP_OK;
     case LINK_H16_12:
     case LINK_B16_12: break;
+    case LINK_DF_18: {
+        std::lock_guard<std::mutex> lk(f.inv_mu);
+        if (!f.ldf[0]) {
+            const long long cnt = f.g.Vh * 36;
+            float4 *d0 = (float4 *)c->alloc(cnt * sizeof(float4)), *d1 = (float4 *)c->alloc(cnt * sizeof(float4));
+            cudaError_t e = (d0 && d1) ? launch_to_df(f.l64[0], d0, cnt, nullptr, 1, 0, c->stream)
+                                       : cudaErrorMemoryAllocation;
+            if (e == cudaSuccess) e = launch_to_df(f.l64[1], d1, cnt, nullptr, 1, 0, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) {
+                c->release(d0);
+                c->release(d1);
+                set_error("double-float links: %s", cudaGetErrorString(e));
+                return e == cudaErrorMemoryAllocation ? DP_ERR_OOM : DP_ERR_CUDA;
+            }
+            c->launches += 2;
+            f.ldf[0] = d0;
+            f.ldf[1] = d1;
+        }
+        *out = f.ldf[parity];
+        return DP_OK;
+    }
     default: set_error("unknown link format %d", link_fmt); return DP_ERR_INVALID_ARG;
     }
     const int k = link_fmt == LINK_H16_12 ? 0 : 1;
@@ -236,7 +258,36 @@ CloverInv::~CloverInv()
     for (int p = 0; p < 2; p++) {
         owner->release(inv64[p]);
         owner->release(inv32[p]);
+        owner->release(invdf[p]);
     }
+}
+
+dp_status clover_inv_df(Ctx *c, Field &f, CloverInv &ci)
+{
+    std::lock_guard<std::mutex> lk(f.inv_mu);
+    if (ci.invdf[0]) return DP_OK;
+    const long long Vh = f.g.Vh;
+    float4 *d[2] = {(float4 *)c->alloc(Vh * 36 * sizeof(float4)), (float4 *)c->alloc(Vh * 36 * sizeof(float4))};
+    if (!d[0] || !d[1]) {
+        c->release(d[0]);
+        c->release(d[1]);
+        set_error("out of device memory (double-float clover inverse)");
+        return DP_ERR_OOM;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < 2 && e == cudaSuccess; p++)
+        e = launch_to_df(ci.inv64[p], d[p], Vh * 36, nullptr, 1, 0, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->release(d[0]);
+        c->release(d[1]);
+        set_error("double-float clover inverse: %s", cudaGetErrorString(e));
+        return DP_ERR_CUDA;
+    }
+    c->launches += 2;
+    ci.invdf[0] = d[0];
+    ci.invdf[1] = d[1];
+    return DP_OK;
 }
 
 dp_status get_clover_inv(Ctx *c, Field &f, double M, std::shared_ptr<CloverInv> *out)
@@ -315,6 +366,11 @@ dp_status check_opts(const dp_solve_opts *in, dp_solve_opts *out)
     // stalls it; two FP64 rounds then reach r = 1e-11
     if (o.inner_tol == 0) o.inner_tol = o.prec == DP_PREC_FP64 ? 0.0 : 1e-6;
     if (o.check_every < 0) o.check_every = 0;
+    if (o.outer_df != 0 && o.outer_df != 1) {
+        set_error("outer_df must be 0 or 1");
+        return DP_ERR_INVALID_ARG;
+    }
+    if (o.prec == DP_PREC_FP64) o.outer_df = 0;  // the FP64 solver has no separate outer operator
     *out = o;
     return DP_OK;
 }
@@ -442,8 +498,8 @@ dp_status dp_field_load(dp_ctx *ctx, const double *links, const int dims[4], int
 {
     CTX_CHECK(ctx);
     Ctx &c = ctx->c;
-    if (!links || !dims || !out || (bc_t != 1 && bc_t != -1)) {
-        set_error("dp_field_load: null pointer or bc_t not +-1");
+    if (!links || !dims || !out || (bc_t != 1 && bc_t != -1 && bc_t != 0)) {
+        set_error("dp_field_load: null pointer or bc_t not -1, 0 or +1");
         return DP_ERR_INVALID_ARG;
     }
     Geom g;
@@ -555,6 +611,7 @@ dp_status dp_field_free(dp_ctx *ctx, dp_field field)
         c.release(f->clov32[p]);
         c.release(f->l16[0][p]);
         c.release(f->l16[1][p]);
+        c.release(f->ldf[p]);
     }
     {
         std::lock_guard<std::mutex> lk(f->inv_mu);
@@ -716,7 +773,7 @@ dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile 
     Field &f = *fp;
     if (!in || !out || nrhs < 1 || nrhs > kMaxRhs || iters < 1 || (out_parity & ~1) ||
         prec < DP_PREC_FP64 || prec > DP_PREC_MIXED_BF16 ||
-        rhs_per_thread < 0 || stages < -1 || stages > 3 ||
+        rhs_per_thread < 0 || stages < -1 || stages > 4 ||
         (block_threads != 0 && (block_threads < 32 || block_threads > 256 || block_threads % 32))) {
         set_error("dp_dslash_dev: invalid argument");
         return DP_ERR_INVALID_ARG;
@@ -820,11 +877,11 @@ dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int
     }
     cudaMemsetAsync(in, 0, vb, c.stream);
     // candidates: four block sizes x RHS per thread (FP64: 1; FP32: one or
-    // two RHS pairs) x shared-memory staging (FP32 one pair per thread: none
-    // or 2-3 directions in flight)
+    // two RHS pairs) x shared-memory staging (FP32 one pair per thread: none,
+    // 2-3 directions in flight, or 2 in a persistent wave)
     const int blocks[] = {64, 96, 128, 192, 256};
     const int rpts[] = {1, 2, 4};
-    const int stage_opts[] = {0, 2, 3};
+    const int stage_opts[] = {0, 2, 3, 4};
     Shape best;
     float bms = 1e30f;
     dp_status st = DP_OK;
@@ -981,7 +1038,7 @@ dp_status dp_restore_contract_dev(dp_ctx *ctx, dp_field field, int n_groups,
 dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profile,
                             const int src[4], double *alpha_out, double *hop_out)
 {
-    if (!dims || !profile || !alpha_out || !hop_out || (bc_t != 1 && bc_t != -1)) {
+    if (!dims || !profile || !alpha_out || !hop_out || (bc_t != 1 && bc_t != -1 && bc_t != 0)) {
         set_error("dp_profile_tables: invalid argument");
         return DP_ERR_INVALID_ARG;
     }

@@ -75,6 +75,9 @@ class Batch {
     dp_status upload_mask(const std::vector<int> &m);
     dp_status bicgstab(int max_iter, int *iters_done);
     dp_status cgne(int max_iter, int *iters_done);
+    // y64 = Mhat x, t64 = A_qq^-1 D_qp x for the active outer RHS (FP64 or
+    // double-float)
+    dp_status outer_mhat();
 
     Ctx *c;
     std::shared_ptr<Field> f;
@@ -89,6 +92,8 @@ class Batch {
     std::vector<void *> owned;
     double2 *bh = nullptr, *x = nullptr, *r64 = nullptr, *y64 = nullptr, *to64 = nullptr,
             *t64 = nullptr;
+    float4 *xdf = nullptr, *tdf = nullptr;  // double-float outer operator (opts.outer_df)
+    float2 *hopdf_d = nullptr;
     InnerVecs in;
     RhsState *outer = nullptr, *inner = nullptr;
     double *alpha_d = nullptr, *hop64_d = nullptr, *hopadj64_d = nullptr;
@@ -96,7 +101,7 @@ class Batch {
     SlotInfo *slots_d = nullptr;
     int *tsrc_d = nullptr, *mask_d = nullptr;
     double *cpp_d = nullptr, *cpart = nullptr, *nrm_d = nullptr;
-    Op op64, opin, opin_adj;
+    Op op64, opin, opin_adj, opdf;
     cudaGraphExec_t graph = nullptr;
     int graph_max_iter = 0;
     Job *jobs[kMaxGroups] = {};

@@ -30,6 +30,7 @@ struct CloverInv {
     double M = 0;
     double2 *inv64[2] = {nullptr, nullptr};
     float4 *inv32[2] = {nullptr, nullptr};
+    float4 *invdf[2] = {nullptr, nullptr};  // double-float copy, on first use
     ~CloverInv();
 };
 
@@ -40,6 +41,7 @@ struct Field {
     float2 *l32f[2] = {nullptr, nullptr};
     float4 *l32c[2] = {nullptr, nullptr};
     void *l16[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [FP16, BF16][parity], lazily
+    float4 *ldf[2] = {nullptr, nullptr};  // double-float links, lazily
     double2 *clov[2] = {nullptr, nullptr};  // clover term, FP64 (no mass)
     float4 *clov32[2] = {nullptr, nullptr}; // clover term, FP32 copy
     bool has_clover = false;
@@ -128,6 +130,8 @@ dp_status field_links(Ctx *c, Field &f, int link_fmt, int parity, const void **o
 int inner_link_format(int prec, int compress12);
 // clover inverse of (4+M) + clover for both parities, cached per mass
 dp_status get_clover_inv(Ctx *c, Field &f, double M, std::shared_ptr<CloverInv> *out);
+// its double-float copy (made on first use)
+dp_status clover_inv_df(Ctx *c, Field &f, CloverInv &ci);
 // FP64 alpha_B tables [4][Lmax] and hop tables [4][2][Lmax] (with the -1/2)
 dp_status profile_tables(const dp_profile &p, const Geom &g, int bc_t, const int src[4],
                          double *alpha, double *hop);

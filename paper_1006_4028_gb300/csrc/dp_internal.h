@@ -41,7 +41,14 @@ enum Epi {
 // link storage formats; the 16-bit ones hold rows 0 and 1 as FP16 or BF16
 // values divided by one FP32 scale per link (max |element| of the two rows):
 // [mu][3][s] uint2 (four 16-bit values each), then [mu][s] float scales
-enum LinkFmt { LINK_F64_18 = 0, LINK_F32_18 = 1, LINK_F32_12 = 2, LINK_H16_12 = 3, LINK_B16_12 = 4 };
+enum LinkFmt {
+    LINK_F64_18 = 0,
+    LINK_F32_18 = 1,
+    LINK_F32_12 = 2,
+    LINK_H16_12 = 3,
+    LINK_B16_12 = 4,
+    LINK_DF_18 = 5  // double-float (two FP32 per real), 18 reals: float4 [4][9][Vh]
+};
 
 // quantise FP64 links of one parity ([mu][9 double2][Vh]) into a 16-bit format
 cudaError_t launch_pack_links16(const double2 *l64, long long Vh, int fmt, void *out,
@@ -78,14 +85,26 @@ struct DslashParams {
 // prec: 0 = FP64 (links LINK_F64_18), 1 = FP32 (links LINK_F32_18 / _F32_12
 // / _H16_12 / _B16_12).  rpt: RHS per thread (FP64 1; FP32 2 = one RHS pair,
 // 4 = two pairs, only for the A^-1 and x - A^-1 D epilogues).  stages > 0
-// (2-3, FP32 one pair per thread, 12-real or 16-bit links, the A^-1 and
+// (FP32 one pair per thread, 12-real or 16-bit links, the A^-1 and
 // x - A^-1 D epilogues, 64, 96 or 128 threads per block) selects the kernel
-// that stages neighbour spinors and links through shared memory with
-// `stages` directions in flight; 0 = direct loads
+// that stages neighbour spinors and links through shared memory: 2-3 =
+// that many directions in flight; 4 = 2 in flight, one persistent wave of
+// blocks whose threads walk several sites; 0 = direct loads
 cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi, int block,
                           int rpt, cudaStream_t st, int stages = 0);
 bool dslash_rpt_ok(int nrhs, int rpt, int prec, int epi);
 bool dslash_staged_ok(int prec, int link_fmt, int epi, int rpt, int stages, int block);
+// double-float Schur launches of the outer loop (dslash_df.cu): EPI_AINV
+// writes double-float, EPI_XMY_AINV reads x as double-float and writes FP64;
+// links LINK_DF_18, clover inverse float4 [36][Vh], hops float2 [grp][8][Lmax]
+cudaError_t launch_dslash_df(const DslashParams &p, int epi, int block, cudaStream_t st);
+// FP64 <-> double-float, element-wise over `count` complex numbers; with a
+// mask only the elements of RHS r with mask[r * mask_stride] != 0 (element
+// i belongs to RHS i % n)
+cudaError_t launch_to_df(const double2 *in, float4 *out, long long count, const int *mask, int n,
+                         int mask_stride, cudaStream_t st);
+cudaError_t launch_from_df(const float4 *in, double2 *out, long long count, const int *mask, int n,
+                           int mask_stride, cudaStream_t st);
 
 // launch shape of the Schur dslash launches (tuner result or default)
 struct Shape {

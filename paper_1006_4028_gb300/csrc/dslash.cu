@@ -31,6 +31,7 @@
 #include <type_traits>
 
 #include "cplx.cuh"
+#include "sites.cuh"
 #include "dp_internal.h"
 #include "pair.cuh"
 
@@ -127,43 +128,6 @@ __device__ __forceinline__ void hop64(Cx<double> acc[12], const double2 *nb, lon
             uh[3 * sp + a] = t;
         }
     accumulate<MU, SG>(acc, uh, c);
-}
-
-// site coordinates and the half-site indices of its 8 neighbours
-// (half-site indices fit in 32 bits: V/2 < 2^31 for every allowed geometry)
-struct Nbr {
-    int t, x, y, z;
-    int f[4], b[4];  // forward / backward neighbour per direction
-};
-
-__device__ __forceinline__ Nbr neighbours(const Geom &g, long long s64, int parity)
-{
-    Nbr o;
-    const unsigned s = (unsigned)s64;
-    const int xh = (int)(s % (unsigned)g.Lxh);
-    unsigned q = s / (unsigned)g.Lxh;
-    o.y = (int)(q % (unsigned)g.Ly);
-    q /= (unsigned)g.Ly;
-    o.z = (int)(q % (unsigned)g.Lz);
-    o.t = (int)(q / (unsigned)g.Lz);
-    o.x = 2 * xh + ((o.t + o.y + o.z + parity) & 1);
-    auto row = [&](int tt, int zz, int yy) -> int {
-        return ((tt * g.Lz + zz) * g.Ly + yy) * g.Lxh;
-    };
-    const int tp = (o.t + 1 == g.T) ? 0 : o.t + 1, tm = (o.t == 0) ? g.T - 1 : o.t - 1;
-    const int xp = (o.x + 1 == g.Lx) ? 0 : o.x + 1, xm = (o.x == 0) ? g.Lx - 1 : o.x - 1;
-    const int yp = (o.y + 1 == g.Ly) ? 0 : o.y + 1, ym = (o.y == 0) ? g.Ly - 1 : o.y - 1;
-    const int zp = (o.z + 1 == g.Lz) ? 0 : o.z + 1, zm = (o.z == 0) ? g.Lz - 1 : o.z - 1;
-    const int r0 = row(o.t, o.z, o.y);
-    o.f[0] = row(tp, o.z, o.y) + xh;
-    o.b[0] = row(tm, o.z, o.y) + xh;
-    o.f[1] = r0 + (xp >> 1);
-    o.b[1] = r0 + (xm >> 1);
-    o.f[2] = row(o.t, o.z, yp) + xh;
-    o.b[2] = row(o.t, o.z, ym) + xh;
-    o.f[3] = row(o.t, zp, o.y) + xh;
-    o.b[3] = row(o.t, zm, o.y) + xh;
-    return o;
 }
 
 template <int EPI>
@@ -684,6 +648,107 @@ __global__ void __launch_bounds__(BD) k_dslash32s(const DslashParams p)
     finish32<EPI, 1>(p, acc, act, s, q0, grp, cs);
 }
 
+// ---- persistent staged variant: one wave of blocks, each thread walks the
+// (site, pair) items w, w + G, w + 2G, ... (G = threads in the grid) with two
+// stages; the next item's first two directions are copied while the current
+// item finishes its last two directions and its epilogue, so neither the
+// start-up nor the epilogue of an item waits on memory.  8 directions per
+// item and 2 slots keep every direction in the same slot for all items.
+template <int LF, int BD, int D>
+__device__ __forceinline__ void pstep(C2 (&acc)[12], const float4 *mine, unsigned smine,
+                                      const Nbr &nb, long long s, const float4 *in, int P,
+                                      long long cs, const void *lown, const void *loth,
+                                      long long Vh, float c, bool next, const Nbr &nbn,
+                                      long long sn, const float4 *inn)
+{
+    constexpr int MU = D / 2;
+    constexpr int SLOT = (D % 2) * kSlot * BD;
+    cp_async_wait<1>();
+    hop_smem<LF, MU, (D & 1) ? +1 : -1>(acc, mine + SLOT, BD, c);
+    if constexpr (D + 2 < 8) {
+        constexpr int E = D + 2, ME = E / 2;
+        const int ni = (E & 1) ? nb.b[ME] : nb.f[ME];
+        stage_issue<LF, BD>(smine + SLOT * 16, in + (long long)ni * P, cs, (E & 1) ? loth : lown, Vh,
+                            (E & 1) ? (long long)nb.b[ME] : s, ME);
+    } else {
+        constexpr int E = D + 2 - 8;  // direction 0 or 1 (mu = 0) of the next item
+        if (next)
+            stage_issue<LF, BD>(smine + SLOT * 16, inn + (long long)(E ? nbn.b[0] : nbn.f[0]) * P, cs,
+                                E ? loth : lown, Vh, E ? (long long)nbn.b[0] : sn, 0);
+    }
+    cp_async_commit();
+}
+
+template <int LF, int EPI, int BD>
+__global__ void __launch_bounds__(BD) k_dslash32p(const DslashParams p)
+{
+    extern __shared__ float4 sbuf[];
+    const Geom &g = p.g;
+    const int P = p.nrhs / 2;
+    const long long items = g.Vh * P;
+    const long long G = (long long)gridDim.x * BD;
+    auto live = [&](long long w) {
+        const int q = (int)(w % P);
+        return !p.active || p.active[2 * q * p.active_stride] || p.active[(2 * q + 1) * p.active_stride];
+    };
+    long long w = (long long)blockIdx.x * BD + threadIdx.x;
+    while (w < items && !live(w)) w += G;
+    if (w >= items) return;
+    const long long cs = g.Vh * P;
+    const long long Vh = g.Vh;
+    const void *lown = p.links[p.parity], *loth = p.links[1 - p.parity];
+    const float4 *mine = sbuf + threadIdx.x;
+    const unsigned smine = (unsigned)__cvta_generic_to_shared(mine);
+    long long s = w / P;
+    int q0 = (int)(w - s * P);
+    Nbr nb = neighbours(g, s, p.parity);
+    const float4 *in = static_cast<const float4 *>(p.in) + q0;
+    stage_issue<LF, BD>(smine, in + (long long)nb.f[0] * P, cs, lown, Vh, s, 0);
+    cp_async_commit();
+    stage_issue<LF, BD>(smine + kSlot * BD * 16, in + (long long)nb.b[0] * P, cs, loth, Vh, nb.b[0], 0);
+    cp_async_commit();
+    for (;;) {
+        long long wn = w + G;
+        while (wn < items && !live(wn)) wn += G;
+        const bool next = wn < items;
+        const long long sn = next ? wn / P : s;
+        const int qn = next ? (int)(wn - sn * P) : q0;
+        const Nbr nbn = next ? neighbours(g, sn, p.parity) : nb;
+        const float4 *inn = static_cast<const float4 *>(p.in) + qn;
+        const int grp = p.grp_of[2 * q0];
+        {
+            const float4 *cl = static_cast<const float4 *>(p.clov[grp]) + s;
+#pragma unroll 1
+            for (int k = 0; k < 18; k++) prefetch_l1(cl + k * Vh);
+            if (EPI == EPI_XMY_AINV) {
+                const float4 *xin = static_cast<const float4 *>(p.x) + s * P + q0;
+#pragma unroll 1
+                for (int k = 0; k < 12; k++) prefetch_l1(xin + k * cs);
+            }
+        }
+        const float *ht = static_cast<const float *>(p.hop) + (long long)grp * 8 * g.Lmax;
+        C2 acc[1][12];
+#pragma unroll
+        for (int j = 0; j < 12; j++) acc[0][j] = {0ull, 0ull};
+        pstep<LF, BD, 0>(acc[0], mine, smine, nb, s, in, P, cs, lown, loth, Vh, ht[0 * g.Lmax + nb.t], next, nbn, sn, inn);
+        pstep<LF, BD, 1>(acc[0], mine, smine, nb, s, in, P, cs, lown, loth, Vh, ht[1 * g.Lmax + nb.t], next, nbn, sn, inn);
+        pstep<LF, BD, 2>(acc[0], mine, smine, nb, s, in, P, cs, lown, loth, Vh, ht[2 * g.Lmax + nb.x], next, nbn, sn, inn);
+        pstep<LF, BD, 3>(acc[0], mine, smine, nb, s, in, P, cs, lown, loth, Vh, ht[3 * g.Lmax + nb.x], next, nbn, sn, inn);
+        pstep<LF, BD, 4>(acc[0], mine, smine, nb, s, in, P, cs, lown, loth, Vh, ht[4 * g.Lmax + nb.y], next, nbn, sn, inn);
+        pstep<LF, BD, 5>(acc[0], mine, smine, nb, s, in, P, cs, lown, loth, Vh, ht[5 * g.Lmax + nb.y], next, nbn, sn, inn);
+        pstep<LF, BD, 6>(acc[0], mine, smine, nb, s, in, P, cs, lown, loth, Vh, ht[6 * g.Lmax + nb.z], next, nbn, sn, inn);
+        pstep<LF, BD, 7>(acc[0], mine, smine, nb, s, in, P, cs, lown, loth, Vh, ht[7 * g.Lmax + nb.z], next, nbn, sn, inn);
+        bool act[1] = {true};
+        finish32<EPI, 1>(p, acc, act, s, q0, grp, cs);
+        if (!next) break;
+        w = wn;
+        s = sn;
+        q0 = qn;
+        nb = nbn;
+        in = inn;
+    }
+}
+
 template <int EPI>
 cudaError_t launch64(const DslashParams &p, int block, cudaStream_t st)
 {
@@ -745,12 +810,44 @@ cudaError_t launch32s_b(const DslashParams &p, int block, cudaStream_t st)
     }
 }
 
+// persistent: one wave, sized from the occupancy calculator (cached)
+template <int LF, int EPI, int BD>
+cudaError_t launch32p_k(const DslashParams &p, cudaStream_t st)
+{
+    constexpr int smem = 2 * kSlot * BD * 16;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_dslash32p<LF, EPI, BD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
+    static const int per_sm = [] {
+        int n = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dslash32p<LF, EPI, BD>, BD, smem) !=
+                cudaSuccess || n < 1)
+            n = 1;
+        cudaGetLastError();
+        return n * (sms > 0 ? sms : 1);
+    }();
+    const long long threads = p.g.Vh * (p.nrhs / 2);
+    const long long need = (threads + BD - 1) / BD;
+    const unsigned grid = (unsigned)(need < per_sm ? need : per_sm);
+    k_dslash32p<LF, EPI, BD><<<grid, BD, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <int LF, int EPI>
 cudaError_t launch32s(const DslashParams &p, int block, int stages, cudaStream_t st)
 {
     switch (stages) {
     case 2: return launch32s_b<LF, EPI, 2>(p, block, st);
     case 3: return launch32s_b<LF, EPI, 3>(p, block, st);
+    case 4:
+        switch (block) {
+        case 64: return launch32p_k<LF, EPI, 64>(p, st);
+        case 96: return launch32p_k<LF, EPI, 96>(p, st);
+        case 128: return launch32p_k<LF, EPI, 128>(p, st);
+        default: return cudaErrorInvalidValue;
+        }
     default: return cudaErrorInvalidValue;
     }
 }
@@ -776,7 +873,7 @@ bool dslash_rpt_ok(int nrhs, int rpt, int prec, int epi)
 
 bool dslash_staged_ok(int prec, int link_fmt, int epi, int rpt, int stages, int block)
 {
-    return prec == 1 && rpt == 2 && stages >= 2 && stages <= 3 &&
+    return prec == 1 && rpt == 2 && stages >= 2 && stages <= 4 &&
            (block == 64 || block == 96 || block == 128) &&
            (epi == EPI_AINV || epi == EPI_XMY_AINV) &&
            (link_fmt == LINK_F32_12 || link_fmt == LINK_H16_12 || link_fmt == LINK_B16_12);

@@ -231,6 +231,23 @@ dp_status Batch::init()
     set_shape(opin, c->launch_shape(Vh, ipr, ilf, n));
     opin_adj = opin;
     opin_adj.hop = ipr == 0 ? (const void *)hopadj64_d : (const void *)hopadj32_d;
+    if (mixed && opts.outer_df) {
+        xdf = (float4 *)get(v64);
+        tdf = (float4 *)get(v64);
+        hopdf_d = (float2 *)get(sizeof(float2) * kMaxGroups * 8 * Lm);
+        if (!xdf || !tdf || !hopdf_d) {
+            set_error("out of device memory for the double-float outer operator");
+            return DP_ERR_OOM;
+        }
+        CK(cudaMemsetAsync(hopdf_d, 0, sizeof(float2) * kMaxGroups * 8 * Lm, c->stream));
+        opdf = op64;
+        opdf.lf = LINK_DF_18;
+        for (int p = 0; p < 2; p++) {
+            dp_status e = field_links(c, *f, LINK_DF_18, p, &opdf.links[p]);
+            if (e != DP_OK) return e;
+        }
+        opdf.hop = hopdf_d;
+    }
     check_every = opts.check_every > 0 ? opts.check_every : (Vh * n >= (1 << 20) ? 2 : 8);
     return DP_OK;
 }
@@ -313,6 +330,19 @@ dp_status Batch::admit(Job *j)
     std::vector<float> hopaf(hopa.begin(), hopa.end());
     CK(cudaMemcpyAsync(hopadj64_d + (size_t)tab * 8 * Lm, hopa.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(hopadj32_d + (size_t)tab * 8 * Lm, hopaf.data(), sizeof(float) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
+    if (hopdf_d) {
+        // double-float hop factors: nearest float, then the nearest float of the rest
+        std::vector<float2> hd(hop.size());
+        for (size_t k = 0; k < hop.size(); k++) {
+            const float hi = (float)hop[k];
+            hd[k] = make_float2(hi, (float)(hop[k] - (double)hi));
+        }
+        CK(cudaMemcpyAsync(hopdf_d + (size_t)tab * 8 * Lm, hd.data(), sizeof(float2) * 8 * Lm,
+                           cudaMemcpyHostToDevice, c->stream));
+        s = clover_inv_df(c, *f, *ci);
+        if (s != DP_OK) return s;
+        for (int p = 0; p < 2; p++) opdf.inv[p][tab] = ci->invdf[p];
+    }
     CK(cudaMemcpyAsync(alpha_d + (size_t)tab * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(hop64_d + (size_t)tab * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(hop32_d + (size_t)tab * 8 * Lm, hopf.data(), sizeof(float) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
@@ -333,7 +363,8 @@ dp_status Batch::admit(Job *j)
         sl.y = j->grp.src[2];
         sl.z = j->grp.src[3];
         sl.scale = scale;
-        op64.grp_of[s0 + k] = opin.grp_of[s0 + k] = opin_adj.grp_of[s0 + k] = (int8_t)tab;
+        op64.grp_of[s0 + k] = opin.grp_of[s0 + k] = opin_adj.grp_of[s0 + k] = opdf.grp_of[s0 + k] =
+            (int8_t)tab;
         slot_job[s0 + k] = j;
         slot_inner[s0 + k] = 0;
         slot_outer[s0 + k] = 0;
@@ -462,6 +493,43 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
     return DP_OK;
 }
 
+dp_status Batch::outer_mhat()
+{
+    if (!xdf) return apply_mhat(c, op64, sp, x, y64, t64, outer);
+    // double-float: x -> xdf, tdf = A_qq^-1 D_qp xdf, y64 = x - A_pp^-1 D_pq tdf,
+    // t64 <- tdf (reconstruction of the other parity)
+    const Geom &g = f->g;
+    const long long cnt = g.Vh * 12 * n;
+    const int *mask = state_mask(outer);
+    CK(launch_to_df(x, xdf, cnt, mask, n, kStateStride, c->stream));
+    DslashParams P{};
+    P.links[0] = opdf.links[0];
+    P.links[1] = opdf.links[1];
+    P.hop = opdf.hop;
+    P.active = mask;
+    P.active_stride = kStateStride;
+    P.g = g;
+    P.nrhs = n;
+    memcpy(P.grp_of, opdf.grp_of, sizeof P.grp_of);
+    cudaEvent_t ev;
+    c->time_begin("dslash_df", &ev);
+    P.parity = 1 - sp;
+    for (int k = 0; k < kMaxGroups; k++) P.clov[k] = opdf.inv[1 - sp][k];
+    P.in = xdf;
+    P.out = tdf;
+    CK(launch_dslash_df(P, EPI_AINV, 128, c->stream));
+    P.parity = sp;
+    for (int k = 0; k < kMaxGroups; k++) P.clov[k] = opdf.inv[sp][k];
+    P.in = tdf;
+    P.x = xdf;
+    P.out = y64;
+    CK(launch_dslash_df(P, EPI_XMY_AINV, 128, c->stream));
+    c->time_end("dslash_df", ev);
+    CK(launch_from_df(tdf, t64, cnt, mask, n, kStateStride, c->stream));
+    c->launches += 4;
+    return DP_OK;
+}
+
 // CG on the normal equations Mhat^dag Mhat x = Mhat^dag b, stopping on the
 // residual of Mhat x = b itself (recursively updated r = b - Mhat x)
 dp_status Batch::cgne(int max_iter, int *iters_done)
@@ -582,7 +650,7 @@ dp_status Batch::round()
         CK(blas_acc64(x, (const double2 *)in.x, Vh, n, outer, c->stream));
     // t64 keeps A_qq^-1 D_qp x of this (final, once converged) x: the
     // reconstruction of the other parity reuses it
-    s = apply_mhat(c, op64, sp, x, y64, t64, outer);
+    s = outer_mhat();
     if (s != DP_OK) return s;
     CK(blas_residual64(c->bc, bh, y64, r64, Vh, n, outer, nullptr, c->stream));
     c->launches += 3;

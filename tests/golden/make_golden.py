@@ -9,7 +9,11 @@ a JSON file in this directory with the inputs that produced it.
       oracle's full-lattice FP64 BiCGStab to relative residue 1e-13, restored
       (Sec. II eq. backcorrection), plus the oracle's iteration counts.
 
-Run:  python tests/golden/make_golden.py
+  free_16x8_M0.5.json : C_PP(y0) of the free theory (U = 1) on 16x8^3,
+      antiperiodic time, M = 0.5, from the exact momentum-space propagator
+      (no solve; it is independent of any profile after the restore).
+
+Run:  python tests/golden/make_golden.py [heavy|free]
 """
 import json
 import os
@@ -46,5 +50,20 @@ def heavy_48x24():
         json.dump(out, fh, indent=1)
 
 
+def free_16x8():
+    dims, M = (16, 8, 8, 8), 0.5
+    cpp = oracle.free_cpp(dims, M, -1)
+    out = {
+        "what": "exact momentum-space free C_PP(y0), point source at the origin",
+        "dims": list(dims), "bc_t": -1, "M": M, "cpp": [float(v) for v in cpp],
+    }
+    with open(os.path.join(HERE, "free_16x8_M0.5.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
 if __name__ == "__main__":
-    heavy_48x24()
+    which = sys.argv[1:] or ["heavy", "free"]
+    if "free" in which:
+        free_16x8()
+    if "heavy" in which:
+        heavy_48x24()

@@ -149,7 +149,7 @@ def test_invalid_arguments_are_errors(ctx):
 # (RHS per thread, shared-memory stages, threads per block); 96, 128 and 160
 # threads leave a ragged last block on the 8x4x6x4 lattice (2304 pairs)
 SHAPES32 = [(2, 0, 64), (4, 0, 64), (2, 2, 64), (2, 3, 128), (2, 3, 96), (2, 2, 96),
-            (4, 0, 256), (2, 0, 160)]
+            (4, 0, 256), (2, 0, 160), (2, 4, 64), (2, 4, 96), (2, 4, 128)]
 
 
 @pytest.mark.parametrize("prec,tol,rpts", [("mixed_fp32", 1e-6, SHAPES32),
@@ -215,4 +215,22 @@ def test_full_size_48x24_fp32_hop(ctx):
     assert per_site_rel(got, ref) < 1e-6
     got64 = dp.dp_apply(ctx, f, "hop", 0.0, prof, (0, 0, 0, 0), "fp64", psi[:1])
     assert per_site_rel(got64, ref[:1]) < 1e-13
+    dp.dp_field_free(ctx, f)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("mixed_fp32", 1e-6)])
+def test_dirichlet_time_boundary_operator(ctx, prec, tol):
+    """bc_t = 0: no quark hop across t = T-1 <-> 0 (Schroedinger-functional-like
+    setting), hopping term and full operator with the exp profile."""
+    dims = (8, 4, 6, 4)
+    U = field(dims, 0.5, 13)
+    f = dp.dp_field_load(ctx, U, dims, 0)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    op = oracle.WilsonClover(U, dims, 1.7, 0)
+    psi = li.random_spinor(dims, 2, 14)
+    prof = ("exp_t", 0.4, (0, 1, 2, 3))
+    got = dp.dp_apply(ctx, f, "hop", 0.0, prof[:2], prof[2], prec, psi)
+    assert per_site_rel(got, op.hop(psi, prof)) < tol
+    got = dp.dp_apply(ctx, f, "full", 0.2, prof[:2], prof[2], prec, psi)
+    assert per_site_rel(got, op.apply(psi, 0.2, prof)) < tol
     dp.dp_field_free(ctx, f)

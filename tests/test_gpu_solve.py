@@ -25,6 +25,8 @@ MIXED_BF16 = {"prec": "mixed_bf16", "batched": 1, "use_graph": 0}
 # CG on the normal equations (the alternative Krylov solver)
 CGNE_MIXED = {"prec": "mixed_fp32", "solver": "cgne", "batched": 1, "use_graph": 1}
 CGNE_FP64 = {"prec": "fp64", "solver": "cgne", "batched": 1, "use_graph": 0}
+# the outer loop's Schur operator in double-float (two FP32 per real)
+MIXED_DF = {"prec": "mixed_fp32", "batched": 1, "use_graph": 1, "outer_df": 1}
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +71,7 @@ CASES = [(0.5, ("cosh_t", 0.4), (0, 0, 0, 0)), (0.8, ("cosh_t", 0.5), (3, 1, 2, 
 
 @pytest.mark.parametrize("M,prof,src", CASES)
 @pytest.mark.parametrize("opts", [MIXED, MIXED_NOGRAPH, PLAIN, MIXED_FP16, MIXED_BF16, CGNE_MIXED,
-                                  CGNE_FP64])
+                                  CGNE_FP64, MIXED_DF])
 def test_interacting_solve_matches_oracle(ctx, inter, M, prof, src, opts):
     dims, f, op = inter
     T, V = dims[0], int(np.prod(dims))
@@ -81,6 +83,47 @@ def test_interacting_solve_matches_oracle(ctx, inter, M, prof, src, opts):
     # the restored propagator itself
     got = prop.reshape((12,) + oracle.array_shape(dims) + (4, 3))
     assert per_site_rel(got, Sref) < 1e-5
+
+
+@pytest.mark.parametrize("r", [1e-10, 1e-12])
+def test_double_float_outer_true_residual_fp64(ctx, inter, r):
+    """The double-float outer operator decides convergence; the oracle's FP64
+    operator then measures the true residual of the returned propagator:
+    |eta - (D+M) S| / |eta| <= 1.5 r per source component (no profile, so the
+    restored S solves the unpreconditioned system of the same residue)."""
+    dims, f, op = inter
+    T, V = dims[0], int(np.prod(dims))
+    src = (2, 1, 0, 3)
+    cpp, prop, info = dp.dp_solve_point(ctx, f, 0.3, ("none", 0.0), src, r, MIXED_DF, T=T, V=V,
+                                        want_prop=True)
+    assert info["status"] == 0
+    S = prop.reshape((12,) + oracle.array_shape(dims) + (4, 3))
+    eta = oracle.point_sources(dims, src)
+    res = eta - op.apply(S, 0.3)
+    rel = np.linalg.norm(res.reshape(12, -1), axis=1) / np.linalg.norm(eta.reshape(12, -1), axis=1)
+    assert rel.max() < 1.5 * r
+    # and the same solve with the FP64 outer operator agrees per time slice
+    cpp64, _, _ = dp.dp_solve_point(ctx, f, 0.3, ("none", 0.0), src, r, MIXED, T=T)
+    assert slice_rel(cpp, cpp64, T // 2) < 1e3 * r
+
+
+@pytest.mark.parametrize("opts", [MIXED, PLAIN])
+def test_dirichlet_time_boundary_solve(ctx, opts):
+    """Dirichlet time boundary with the exp profile (the Schroedinger-functional
+    use the paper recommends), source on the first slice: C_PP over the whole
+    time extent against the oracle."""
+    dims = (12, 4, 4, 6)
+    U = field(dims, 0.3, 8)
+    f = dp.dp_field_load(ctx, U, dims, 0)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    op = oracle.WilsonClover(U, dims, 1.7, 0)
+    src = (0, 1, 2, 3)
+    ref, _, oinfo = oracle.solve_point(op, 0.5, "exp_t", 0.4, src, tol=1e-13)
+    assert oinfo["converged"]
+    cpp, _, info = dp.dp_solve_point(ctx, f, 0.5, ("exp_t", 0.4), src, 1e-11, opts, T=12)
+    assert info["status"] == 0
+    assert slice_rel(cpp, ref, 11) < 1e-6
+    dp.dp_field_free(ctx, f)
 
 
 def test_multi_mass_batch_equals_single_solves(ctx, inter):

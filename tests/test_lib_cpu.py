@@ -41,7 +41,7 @@ KINDS = [("none", 0.0), ("exp_t", 0.4), ("cosh_t", 0.3), ("cosh_4d", 0.2)]
 
 @pytest.mark.parametrize("kind,alpha0", KINDS)
 @pytest.mark.parametrize("src", [(0, 0, 0, 0), (5, 3, 1, 2)])
-@pytest.mark.parametrize("bc_t", [-1, 1])
+@pytest.mark.parametrize("bc_t", [-1, 1, 0])
 def test_host_profile_tables_match_oracle(lib, kind, alpha0, src, bc_t):
     dims = (16, 8, 4, 6)
     alpha, hop = dp.dp_profile_tables(dims, bc_t, (kind, alpha0), src)
@@ -78,7 +78,7 @@ def test_host_rejects_bad_profiles(lib):
     with pytest.raises(dp.DpError):
         dp.dp_profile_tables((8, 4, 4, 4), -1, ("table", 0.0, [np.zeros(8)] + [np.ones(4)] * 3))
     with pytest.raises(dp.DpError):
-        dp.dp_profile_tables((8, 4, 4, 4), 0, ("none", 0.0))
+        dp.dp_profile_tables((8, 4, 4, 4), 2, ("none", 0.0))
     with pytest.raises(dp.DpError):
         dp.dp_profile_tables((8, 4, 4, 4), -1, ("none", 0.0), (8, 0, 0, 0))
 

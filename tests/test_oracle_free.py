@@ -87,3 +87,15 @@ def test_free_propagator_solves_point_source():
         want = np.zeros_like(out)
         want[0, 0, 0, 0, sp, 0] = 1
         assert np.abs(out - want).max() < 1e-14
+
+
+def test_stored_free_golden_is_the_oracles():
+    """tests/golden/free_16x8_M0.5.json (read by the benchmark's free-theory
+    check) holds exactly the oracle's momentum-space C_PP."""
+    import json
+    import os
+
+    p = os.path.join(os.path.dirname(__file__), "golden", "free_16x8_M0.5.json")
+    d = json.load(open(p))
+    np.testing.assert_allclose(d["cpp"], oracle.free_cpp(tuple(d["dims"]), d["M"], d["bc_t"]),
+                               rtol=1e-14, atol=0)
