@@ -194,6 +194,18 @@ dp_status dp_solve_point_multi(dp_ctx *ctx, dp_field field, int n_mass, const do
                                const dp_solve_opts *opts, double *cpp_out, double *prop_out,
                                dp_solve_info *info);
 
+/* dp_solve_point plus the axial-pseudoscalar correlator of the same pair of
+ * degenerate quarks, from the same restored propagator:
+ *   cap_out[y0] = C_AP(y0) = sum_{y vec} tr[gamma_0 S(y) S(y)^dag]
+ * (= -tr[gamma_0 gamma_5 S(y,x) gamma_5 S(x,y)] by gamma_5-hermiticity), y0
+ * relative to the source time, host [T], caller-owned, non-NULL.  The PCAC
+ * mass the paper labels its quark masses with (Sec. II) is then
+ * [C_AP(y0+1) - C_AP(y0-1)] / (4 C_PP(y0)).  Other arguments as
+ * dp_solve_point (no propagator output). */
+dp_status dp_solve_point_corr(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
+                              const int src[4], double r, const dp_solve_opts *opts, double *cpp_out,
+                              double *cap_out, dp_solve_info *info);
+
 /* As dp_solve_point_multi, but cpp_out is DEVICE memory ([n_mass][T] doubles)
  * written on the context stream; nothing is copied to the host except the
  * convergence flags the iteration loop reads. */

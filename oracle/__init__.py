@@ -336,6 +336,32 @@ def contract_cpp(S, dims, t_src):
     return -np.roll(per_t, -int(t_src))
 
 
+def contract_cap(S, dims, t_src):
+    """C_AP(y0) = sum_{y vec} tr[gamma_0 S S^dag], y0 relative to t_src.
+
+    The axial-pseudoscalar correlator of the pair of degenerate quarks whose
+    pseudoscalar correlator is C_PP: with S(x, y) = gamma_5 S(y, x)^dag
+    gamma_5, -tr[gamma_0 gamma_5 S(y,x) gamma_5 S(x,y)] = tr[gamma_0 S S^dag]
+    (gamma_5 gamma_0 gamma_5 = -gamma_0); same orientation and normalisation as
+    contract_cpp.  S: (12, T, Lz, Ly, Lx, 4, 3).
+    """
+    g0 = _c128(gammas()[0])
+    # tr[gamma_0 S S^dag] = sum_{j, c, s1, s2} g0[s1, s2] S_j(s2, c) conj(S_j(s1, c))
+    per_t = np.einsum("ab,jtzyxbc,jtzyxac->t", g0, S, np.conj(S)).real
+    return np.roll(per_t, -int(t_src))
+
+
+def pcac_mass(cpp, cap):
+    """m_PCAC(y0) = [C_AP(y0+1) - C_AP(y0-1)] / 2 / (2 C_PP(y0)), y0 = 1..T-2
+    (the unimproved local-current ratio; the paper quotes am_PCAC to label its
+    quark masses, Sec. II).  Returns an array of length T, NaN at the ends."""
+    cpp = np.asarray(cpp, float)
+    cap = np.asarray(cap, float)
+    m = np.full(len(cpp), np.nan)
+    m[1:-1] = (cap[2:] - cap[:-2]) / 2.0 / (2.0 * cpp[1:-1])
+    return m
+
+
 def solve_point(op, M, profile_kind="none", alpha0=0.0, src=(0, 0, 0, 0), tol=1e-13,
                 maxit=20000, tables=None):
     """Full method for a point source: eta' = alpha_B(x_src) eta, solve
@@ -353,7 +379,8 @@ def solve_point(op, M, profile_kind="none", alpha0=0.0, src=(0, 0, 0, 0), tol=1e
     Sp, iters, rel, ok = op.solve(eta_p, M, prof, tol=tol, maxit=maxit)
     S = restore(Sp, al, dims)
     cpp = contract_cpp(S, dims, src[0])
-    return cpp, S, {"iters": iters, "relres": rel, "converged": ok, "Sprime": Sp}
+    return cpp, S, {"iters": iters, "relres": rel, "converged": ok, "Sprime": Sp,
+                    "cap": contract_cap(S, dims, src[0])}
 
 
 def effective_mass(cpp):

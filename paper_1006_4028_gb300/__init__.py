@@ -26,7 +26,7 @@ __all__ = [
     "dp_create", "dp_destroy", "dp_last_error", "dp_device_bytes",
     "dp_field_load", "dp_field_set_csw", "dp_field_free",
     "dp_solve_point", "dp_solve_point_multi", "dp_solve_point_dev",
-    "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
+    "dp_solve_point_corr", "pcac_mass", "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
     "dp_autotune",
     "dp_timing_enable", "dp_timing_reset", "dp_timing_get", "dp_launch_count",
     "dp_serve_start", "dp_submit", "dp_wait", "dp_cancel", "dp_serve_stats_get", "dp_serve_stop",
@@ -116,6 +116,8 @@ def load(build_if_missing=False):
         "dp_solve_point_multi": ([vp, up, ip, vp, vp, P(C.c_int * 4), dp, P(SolveOpts), vp, vp,
                                   vp], ip),
         "dp_solve_point_dev": ([vp, up, ip, vp, vp, P(C.c_int * 4), dp, P(SolveOpts), vp, vp], ip),
+        "dp_solve_point_corr": ([vp, up, dp, P(Profile), P(C.c_int * 4), dp, P(SolveOpts), vp, vp,
+                                 P(SolveInfo)], ip),
         "dp_apply": ([vp, up, ip, dp, P(Profile), P(C.c_int * 4), ip, ip, vp, vp, ip], ip),
         "dp_profile_tables": ([P(C.c_int * 4), ip, P(Profile), P(C.c_int * 4), vp, vp], ip),
         "dp_restore_contract_dev": ([vp, up, ip, vp, vp, vp, vp, vp], ip),
@@ -250,6 +252,29 @@ def dp_solve_point(ctx, field, M, profile, src, r, opts=None, T=None, V=None, wa
                                C.byref(info))
     _check(st, allow)
     return cpp, prop, info.as_dict()
+
+
+def dp_solve_point_corr(ctx, field, M, profile, src, r, opts=None, T=None, allow=(3,)):
+    """Point-source solve returning C_PP and C_AP: (cpp[T], cap[T], info)."""
+    pr, keep = _profile(profile)
+    cpp = np.zeros(int(T))
+    cap = np.zeros(int(T))
+    info = SolveInfo()
+    st = load().dp_solve_point_corr(ctx, int(field), float(M), C.byref(pr), C.byref(_i4(src)),
+                                    float(r), C.byref(_opts(opts)), _ptr(cpp), _ptr(cap),
+                                    C.byref(info))
+    _check(st, allow)
+    return cpp, cap, info.as_dict()
+
+
+def pcac_mass(cpp, cap):
+    """m_PCAC(y0) = [C_AP(y0+1) - C_AP(y0-1)] / (4 C_PP(y0)) for y0 = 1..T-2 (host
+    arithmetic on the two returned correlators; NaN at the ends)."""
+    cpp = np.asarray(cpp, float)
+    cap = np.asarray(cap, float)
+    m = np.full(len(cpp), np.nan)
+    m[1:-1] = (cap[2:] - cap[:-2]) / (4.0 * cpp[1:-1])
+    return m
 
 
 def dp_solve_point_multi(ctx, field, Ms, profiles, src, r, opts=None, T=None, V=None,

@@ -17,6 +17,7 @@ struct Job {
     double *cpp_dst = nullptr;   // device [T], written (or added to) on completion
     int accumulate = 0;
     double *cpp_host = nullptr;  // host [T], written on completion
+    double *cap_dst = nullptr;   // device [T] C_AP, written (or added to) on completion, or NULL
     double *prop_host = nullptr; // host [ncomp][V][12] complex128 or NULL
     SolveResult res;
     bool done = false;
@@ -100,7 +101,7 @@ class Batch {
     float *hop32_d = nullptr, *hopadj32_d = nullptr;  // adj: the reciprocal profile (CGNE)
     SlotInfo *slots_d = nullptr;
     int *tsrc_d = nullptr, *mask_d = nullptr;
-    double *cpp_d = nullptr, *cpart = nullptr, *nrm_d = nullptr;
+    double *cpp_d = nullptr, *cap_d = nullptr, *cpart = nullptr, *nrm_d = nullptr;
     Op op64, opin, opin_adj, opdf;
     cudaGraphExec_t graph = nullptr;
     int graph_max_iter = 0;

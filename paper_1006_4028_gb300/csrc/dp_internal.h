@@ -167,10 +167,13 @@ cudaError_t launch_point_source(const Geom &g, const SlotInfo *slots_dev, int nr
 // [nrhs][V][12] complex128 of the restored propagator
 int contract_blocks_per_slice(const Geom &g);
 // only RHS with mask[r] != 0 contribute (mask NULL: all)
+// cap_dev (optional): C_AP(y0) = sum tr[gamma_0 S S^dag] per group, same
+// layout as cpp_dev; partials then needs 2 * T * P * n_mass doubles
 cudaError_t launch_restore_contract(const double2 *xe, const double2 *xo, const Geom &g, int nrhs,
                                     const double *alpha, const SlotInfo *slots_dev, int ngroups,
                                     const int *t_src_dev, const int *mask, double *cpp_dev,
-                                    double *partials, double2 *prop_lex, cudaStream_t st);
+                                    double *partials, double2 *prop_lex, cudaStream_t st,
+                                    double *cap_dev = nullptr);
 // dst[k] (+)= src[k], k < T (accumulate != 0: add)
 cudaError_t launch_cpp_commit(const double *src, double *dst, int T, int accumulate, cudaStream_t st);
 

@@ -177,10 +177,14 @@ __global__ void k_point_source(Geom g, const SlotInfo *slots, int n, const int *
 constexpr int kContractBlock = 256;
 
 // grid (P, T): block (p, t) sums |S'|^2/alpha_B^2 over its share of slice t,
-// per group; partials[(t*P + p)*ng + grp]
+// per group; partials[(t*P + p)*ng + grp].  With `ap`, also the gamma_0
+// bilinear tr[gamma_0 S S^dag] (chiral basis: gamma_0 = -1 between spins 0,2
+// and 1,3, i.e. -2 Re sum_c [S(0,c) S(2,c)* + S(1,c) S(3,c)*] per RHS) into
+// partials[T*P*ng + (t*P + p)*ng + grp]
 __global__ void __launch_bounds__(kContractBlock)
     k_contract(const double2 *xe, const double2 *xo, Geom g, int n, const double *alpha,
-               const SlotInfo *slots, const int *mask, int ng, double *partials, double2 *prop)
+               const SlotInfo *slots, const int *mask, int ng, double *partials, double2 *prop,
+               int ap)
 {
     const int P = gridDim.x, p = blockIdx.x, t = blockIdx.y;
     const long long Vs = g.Vh / g.T;  // half-sites per slice per parity
@@ -188,8 +192,8 @@ __global__ void __launch_bounds__(kContractBlock)
     const long long j0 = p * chunk, j1 = min(Vs, j0 + chunk);
     const int nm = ng;
     const long long cs = g.Vh * n;
-    double loc[kMaxGroups];
-    for (int m = 0; m < kMaxGroups; m++) loc[m] = 0;
+    double loc[kMaxGroups], lap[kMaxGroups];
+    for (int m = 0; m < kMaxGroups; m++) loc[m] = lap[m] = 0;
     const long long work = (j1 > j0 ? j1 - j0 : 0) * n;
     for (long long e = threadIdx.x; e < work; e += blockDim.x) {
         const long long s = (long long)t * Vs + j0 + e / n;
@@ -203,26 +207,38 @@ __global__ void __launch_bounds__(kContractBlock)
         const int grp = slots[r].group;
         const double *al = alpha + (long long)grp * 4 * g.Lmax;
         const double base = al[0 * g.Lmax + t] * al[2 * g.Lmax + y] * al[3 * g.Lmax + z];
-        double acc = 0;
+        double acc = 0, acc_ap = 0;
         for (int par = 0; par < 2; par++) {
             const int x = 2 * xh + ((t + y + z + par) & 1);
             const double inv = 1.0 / (base * al[1 * g.Lmax + x]);
             const double2 *v = (par ? xo : xe) + s * n + r;
             double2 *pd = prop ? prop + ((long long)r * g.V + 2 * s + (x & 1)) * 12 : nullptr;
             double sp = 0;
+            double2 c[12];
             for (int k = 0; k < 12; k++) {
-                double2 c = v[k * cs];
-                c.x *= inv;
-                c.y *= inv;
-                sp = fmx(c.x, c.x, sp);
-                sp = fmx(c.y, c.y, sp);
-                if (pd) pd[k] = c;
+                c[k] = v[k * cs];
+                c[k].x *= inv;
+                c[k].y *= inv;
+                sp = fmx(c[k].x, c[k].x, sp);
+                sp = fmx(c[k].y, c[k].y, sp);
+                if (pd) pd[k] = c[k];
             }
             acc += sp;
+            if (ap) {
+                double b = 0;  // Re sum_c [S(0,c) S(2,c)* + S(1,c) S(3,c)*]
+                for (int k = 0; k < 6; k++) {
+                    b = fmx(c[k].x, c[k + 6].x, b);
+                    b = fmx(c[k].y, c[k + 6].y, b);
+                }
+                acc_ap -= 2.0 * b;
+            }
         }
 #pragma unroll
         for (int m = 0; m < kMaxGroups; m++)
-            if (m == grp) loc[m] += acc;
+            if (m == grp) {
+                loc[m] += acc;
+                lap[m] += acc_ap;
+            }
     }
     __shared__ double sh[kContractBlock];
     for (int m = 0; m < nm; m++) {
@@ -234,12 +250,23 @@ __global__ void __launch_bounds__(kContractBlock)
         }
         if (threadIdx.x == 0) partials[((long long)t * P + p) * nm + m] = sh[0];
         __syncthreads();
+        if (!ap) continue;
+        sh[threadIdx.x] = lap[m];
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            partials[(long long)g.T * P * nm + ((long long)t * P + p) * nm + m] = sh[0];
+        __syncthreads();
     }
 }
 
-// cpp[m][(t - t_src[m]) mod T] = -sum_p partials[t][p][m], summed in p order
+// cpp[m][(t - t_src[m]) mod T] = -sum_p partials[t][p][m], summed in p order;
+// cap (if non-null) from the second half of partials, with a + sign
 __global__ void k_contract_final(const double *partials, int P, int T, int nm, const int *t_src,
-                                 double *cpp)
+                                 double *cpp, double *cap)
 {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= T * nm) return;
@@ -248,6 +275,12 @@ __global__ void k_contract_final(const double *partials, int P, int T, int nm, c
     for (int p = 0; p < P; p++) s += partials[((long long)t * P + p) * nm + m];
     const int rel = ((t - t_src[m]) % T + T) % T;
     cpp[m * T + rel] = -s;
+    if (cap) {
+        const double *pa = partials + (long long)T * P * nm;
+        double a = 0;
+        for (int p = 0; p < P; p++) a += pa[((long long)t * P + p) * nm + m];
+        cap[m * T + rel] = a;
+    }
 }
 
 __global__ void k_cpp_commit(const double *src, double *dst, int T, int accumulate)
@@ -323,17 +356,19 @@ int contract_blocks_per_slice(const Geom &g)
 cudaError_t launch_restore_contract(const double2 *xe, const double2 *xo, const Geom &g, int nrhs,
                                     const double *alpha, const SlotInfo *slots_dev, int ngroups,
                                     const int *t_src_dev, const int *mask, double *cpp_dev,
-                                    double *partials, double2 *prop_lex, cudaStream_t st)
+                                    double *partials, double2 *prop_lex, cudaStream_t st,
+                                    double *cap_dev)
 {
     if (ngroups < 1 || ngroups > kMaxGroups) return cudaErrorInvalidValue;
     const int P = contract_blocks_per_slice(g);
     dim3 grid(P, g.T);
     k_contract<<<grid, kContractBlock, 0, st>>>(xe, xo, g, nrhs, alpha, slots_dev, mask, ngroups,
-                                                partials, prop_lex);
+                                                partials, prop_lex, cap_dev ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int tot = g.T * ngroups;
-    k_contract_final<<<(tot + 127) / 128, 128, 0, st>>>(partials, P, g.T, ngroups, t_src_dev, cpp_dev);
+    k_contract_final<<<(tot + 127) / 128, 128, 0, st>>>(partials, P, g.T, ngroups, t_src_dev, cpp_dev,
+                                                         cap_dev);
     return cudaGetLastError();
 }
 
@@ -482,12 +517,13 @@ extern "C" dp_status dp_restore_contract_noalloc(dp_ctx *ctx, dp_field field, in
         dim3 grid(P, g.T);
         k_contract<<<grid, kContractBlock, 0, c.stream>>>((const double2 *)xe, (const double2 *)xo, g, n,
                                                           alpha_d, slots_d, nullptr, n_groups, part_d,
-                                                          nullptr);
+                                                          nullptr, 0);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
         const int tot = g.T * n_groups;
-        k_contract_final<<<(tot + 127) / 128, 128, 0, c.stream>>>(part_d, P, g.T, n_groups, tsrc_d, cpp_dev);
+        k_contract_final<<<(tot + 127) / 128, 128, 0, c.stream>>>(part_d, P, g.T, n_groups, tsrc_d, cpp_dev,
+                                                                   nullptr);
         e = cudaGetLastError();
     }
     // the host tables live on this stack frame: wait for the copies (and the

@@ -186,11 +186,12 @@ dp_status Batch::init()
     tsrc_d = (int *)get(sizeof(int) * kMaxGroups);
     mask_d = (int *)get(sizeof(int) * kMaxRhs);
     cpp_d = (double *)get(sizeof(double) * kMaxGroups * g.T);
-    cpart = (double *)get(sizeof(double) * (size_t)g.T * contract_blocks_per_slice(g) * kMaxGroups);
+    cap_d = (double *)get(sizeof(double) * kMaxGroups * g.T);
+    cpart = (double *)get(sizeof(double) * 2 * (size_t)g.T * contract_blocks_per_slice(g) * kMaxGroups);
     nrm_d = (double *)get(sizeof(double) * kMaxRhs);
     ok = ok && outer && inner && alpha_d && hop64_d && hop32_d && hopadj64_d && hopadj32_d &&
          slots_d && tsrc_d && mask_d &&
-         cpp_d && cpart && nrm_d;
+         cpp_d && cap_d && cpart && nrm_d;
     if (!ok) {
         set_error("out of device memory for a %d-slot solver batch (%zu bytes per FP64 vector)", n, v64);
         return DP_ERR_OOM;
@@ -712,8 +713,10 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
             prop_d = (double2 *)prop_tmp;
         }
         CK(launch_restore_contract(sp == 0 ? x : y64, sp == 0 ? y64 : x, g, n, alpha_d, slots_d,
-                                   kMaxGroups, tsrc_d, mask_d, cpp_d, cpart, prop_d, c->stream));
+                                   kMaxGroups, tsrc_d, mask_d, cpp_d, cpart, prop_d, c->stream,
+                                   j->cap_dst ? cap_d : nullptr));
         if (j->cpp_dst) CK(launch_cpp_commit(cpp_d + (size_t)tab * g.T, j->cpp_dst, g.T, j->accumulate, c->stream));
+        if (j->cap_dst) CK(launch_cpp_commit(cap_d + (size_t)tab * g.T, j->cap_dst, g.T, j->accumulate, c->stream));
         if (j->cpp_host) CK(cudaMemcpyAsync(j->cpp_host, cpp_d + (size_t)tab * g.T, sizeof(double) * g.T, cudaMemcpyDeviceToHost, c->stream));
         if (prop_d)
             CK(cudaMemcpyAsync(j->prop_host, prop_d + (size_t)j->slot0 * g.V * 12,
@@ -747,7 +750,7 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
 
 dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group> &groups,
                        double r_target, const dp_solve_opts &o, double *cpp_dev, double *prop_host,
-                       std::vector<SolveResult> &res)
+                       std::vector<SolveResult> &res, double *cap_dev)
 {
     const Geom &g = f->g;
     const int ng = (int)groups.size();
@@ -791,6 +794,7 @@ dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group
         j.ncomp = batched ? 12 : 1;
         j.r = r_target;
         j.cpp_dst = cpp_dev + (size_t)gi * g.T;
+        if (cap_dev) j.cap_dst = cap_dev + (size_t)gi * g.T;
         j.accumulate = batched ? 0 : (j.comp0 > 0);
         if (prop_host) j.prop_host = prop_host + ((size_t)gi * 12 + j.comp0) * g.V * 24;
     }
@@ -839,7 +843,7 @@ using namespace dp;
 static dp_status solve_common(dp_ctx *ctx, dp_field field, int n_mass, const double *M,
                               const dp_profile *profiles, const int src[4], double r,
                               const dp_solve_opts *opts, double *cpp_out, int cpp_on_device,
-                              double *prop_out, dp_solve_info *info)
+                              double *prop_out, dp_solve_info *info, double *cap_out = nullptr)
 {
     if (!ctx) {
         set_error("null context");
@@ -882,23 +886,30 @@ static dp_status solve_common(dp_ctx *ctx, dp_field field, int n_mass, const dou
     }
     fp->users++;
     double *cpp_dev = cpp_out;
-    void *tmp = nullptr;
+    void *tmp = nullptr, *tmp_ap = nullptr;
     if (!cpp_on_device) {
         tmp = c.alloc(sizeof(double) * n_mass * fp->g.T);
         cpp_dev = (double *)tmp;
     }
+    if (cap_out) tmp_ap = c.alloc(sizeof(double) * n_mass * fp->g.T);
     std::vector<SolveResult> res;
-    if (!cpp_dev) {
+    if (!cpp_dev || (cap_out && !tmp_ap)) {
         fp->users--;
+        c.release(tmp);
+        c.release(tmp_ap);
         set_error("out of device memory");
         return DP_ERR_OOM;
     }
-    s = solve_groups(&c, fp, groups, r, o, cpp_dev, prop_out, res);
-    if (!cpp_on_device && (s == DP_OK || s == DP_ERR_NOT_CONVERGED || s == DP_ERR_BREAKDOWN)) {
-        cudaMemcpyAsync(cpp_out, cpp_dev, sizeof(double) * n_mass * fp->g.T, cudaMemcpyDeviceToHost, c.stream);
+    s = solve_groups(&c, fp, groups, r, o, cpp_dev, prop_out, res, (double *)tmp_ap);
+    if (s == DP_OK || s == DP_ERR_NOT_CONVERGED || s == DP_ERR_BREAKDOWN) {
+        if (!cpp_on_device)
+            cudaMemcpyAsync(cpp_out, cpp_dev, sizeof(double) * n_mass * fp->g.T, cudaMemcpyDeviceToHost, c.stream);
+        if (cap_out)
+            cudaMemcpyAsync(cap_out, tmp_ap, sizeof(double) * n_mass * fp->g.T, cudaMemcpyDeviceToHost, c.stream);
     }
     cudaStreamSynchronize(c.stream);
     if (tmp) c.release(tmp);
+    if (tmp_ap) c.release(tmp_ap);
     fp->users--;
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info)
@@ -936,6 +947,20 @@ dp_status dp_solve_point_multi(dp_ctx *ctx, dp_field field, int n_mass, const do
                                dp_solve_info *info)
 {
     return solve_common(ctx, field, n_mass, M, profiles, src, r, opts, cpp_out, 0, prop_out, info);
+}
+
+dp_status dp_solve_point_corr(dp_ctx *ctx, dp_field field, double M, const dp_profile *profile,
+                              const int src[4], double r, const dp_solve_opts *opts, double *cpp_out,
+                              double *cap_out, dp_solve_info *info)
+{
+    if (!cap_out) {
+        set_error("dp_solve_point_corr: cap_out is NULL");
+        return DP_ERR_INVALID_ARG;
+    }
+    dp_profile none{};
+    none.kind = DP_PROF_NONE;
+    return solve_common(ctx, field, 1, &M, profile ? profile : &none, src, r, opts, cpp_out, 0,
+                        nullptr, info, cap_out);
 }
 
 dp_status dp_solve_point_dev(dp_ctx *ctx, dp_field field, int n_mass, const double *M,

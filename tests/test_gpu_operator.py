@@ -123,8 +123,8 @@ def test_invalid_arguments_are_errors(ctx):
     with pytest.raises(dp.DpError) as e:  # odd extent: no even-odd split
         dp.dp_field_load(ctx, li.unit_links((4, 3, 4, 4)), (4, 3, 4, 4), -1)
     assert e.value.status == 1
-    with pytest.raises(dp.DpError) as e:
-        dp.dp_field_load(ctx, U, dims, 0)
+    with pytest.raises(dp.DpError) as e:  # bc_t must be -1, 0 (Dirichlet) or +1
+        dp.dp_field_load(ctx, U, dims, 2)
     assert e.value.status == 1
     bad = U.copy()
     bad[0, 0, 0, 0, 0, 0, 0] = np.nan

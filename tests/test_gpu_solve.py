@@ -126,6 +126,25 @@ def test_dirichlet_time_boundary_solve(ctx, opts):
     dp.dp_field_free(ctx, f)
 
 
+@pytest.mark.parametrize("opts", [MIXED, PLAIN])
+def test_cap_and_pcac_mass_match_oracle(ctx, inter, opts):
+    """C_AP from the same restored propagator as C_PP, against the oracle's
+    contraction of its tight solve; the PCAC mass formed from both."""
+    dims, f, op = inter
+    T = dims[0]
+    src = (3, 1, 2, 0)
+    ref_cpp, _, oinfo = oracle.solve_point(op, 0.5, "cosh_t", 0.4, src, tol=1e-13)
+    ref_cap = oinfo["cap"]
+    cpp, cap, info = dp.dp_solve_point_corr(ctx, f, 0.5, ("cosh_t", 0.4), src, 1e-11, opts, T=T)
+    assert info["status"] == 0
+    assert slice_rel(cpp, ref_cpp, T // 2) < 1e-6
+    scale = np.abs(ref_cap[: T // 2 + 1]).max()
+    assert np.abs(cap[: T // 2 + 1] - ref_cap[: T // 2 + 1]).max() < 1e-6 * scale
+    m_gpu = dp.pcac_mass(cpp, cap)[2: T // 2]
+    m_ref = oracle.pcac_mass(ref_cpp, ref_cap)[2: T // 2]
+    assert np.abs(m_gpu - m_ref).max() < 1e-5 * np.abs(m_ref).max()
+
+
 def test_multi_mass_batch_equals_single_solves(ctx, inter):
     dims, f, op = inter
     T = dims[0]
