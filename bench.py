@@ -592,7 +592,7 @@ def main():
                     choices=["mixed_fp32", "mixed_fp16", "mixed_bf16"],
                     help="inner-solver precision (links: 12 FP32 reals, or 12 16-bit reals "
                          "plus one FP32 scale)")
-    ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "cgne"])
+    ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "cgne", "sap_gcr"])
     ap.add_argument("--config", default="heavy48",
                     choices=["heavy48", "free16", "light64", "multimass32", "serve", "sf48"],
                     help="heavy48: the headline solves/s line (default); the others run the "
@@ -753,7 +753,7 @@ def main():
                        l2="working set ~%.1f GB >> 129 MB L2 (no flush needed)"
                           % (dp.dp_device_bytes(ctx) / 1e9),
                        solver="%s FP32 inner (%s) in FP64 defect correction"
-                              % ({"bicgstab": "BiCGStab", "cgne": "CGNE"}[args.solver],
+                              % ({"bicgstab": "BiCGStab", "cgne": "CGNE", "sap_gcr": "SAP+GCR"}[args.solver],
                                  LINKS[args.prec]),
                        graphs=bool(args.graphs), tuned_launch=tuned),
         "gpu_launches": launches,

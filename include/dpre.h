@@ -104,9 +104,11 @@ typedef enum {
 } dp_prec;
 
 /* BiCGStab on Mhat x = b (Sec. I, eqs. linsysunprec/linsysprec solved
- * iteratively), or CG on the normal equations Mhat^dag Mhat x = Mhat^dag b
- * (CGNE), both stopping on |b - Mhat x| / |b|. */
-typedef enum { DP_SOLVER_BICGSTAB = 0, DP_SOLVER_CGNE = 1 } dp_solver;
+ * iteratively), CG on the normal equations Mhat^dag Mhat x = Mhat^dag b
+ * (CGNE), or GCR preconditioned by the Schwarz alternating procedure
+ * (SAP+GCR, the solver of the paper's Table I, Sec. III; mixed precisions
+ * only), all stopping on |b - Mhat x| / |b|. */
+typedef enum { DP_SOLVER_BICGSTAB = 0, DP_SOLVER_CGNE = 1, DP_SOLVER_SAP_GCR = 2 } dp_solver;
 
 typedef struct {
     int max_iter;     /* total inner iterations allowed (0: 20000)                  */
@@ -118,6 +120,9 @@ typedef struct {
     int batched;      /* 1: all RHS in one multi-RHS solve; 0: one RHS at a time    */
     int use_graph;    /* capture one solver iteration as a CUDA graph               */
     int check_every;  /* iterations between convergence reads (0: automatic)        */
+    int sap_ncy;      /* SAP+GCR: Schwarz cycles per preconditioning (0: 4)          */
+    int sap_nmr;      /* SAP+GCR: minimal-residual steps per block solve (0: 4)      */
+    int gcr_nkv;      /* SAP+GCR: Krylov vectors before a GCR restart (0: 8)         */
     int outer_df;     /* mixed precisions: 1 = the outer loop's Schur operator in
                          double-float arithmetic (two FP32 per real, ~48-bit
                          significands, ~1e-14 relative; for r >= 1e-12) on the

@@ -35,7 +35,7 @@ __all__ = [
 
 PROFILE_KINDS = {"none": 0, "exp_t": 1, "cosh_t": 2, "cosh_4d": 3, "table": 4}
 PREC = {"fp64": 0, "mixed_fp32": 1, "mixed_fp16": 2, "mixed_bf16": 3}
-SOLVER = {"bicgstab": 0, "cgne": 1}
+SOLVER = {"bicgstab": 0, "cgne": 1, "sap_gcr": 2}
 APPLY = {"hop": 0, "clover": 1, "full": 2, "clover_inv": 3}
 STATUS = {0: "DP_OK", 1: "DP_ERR_INVALID_ARG", 2: "DP_ERR_OOM", 3: "DP_ERR_NOT_CONVERGED",
           4: "DP_ERR_BREAKDOWN", 5: "DP_ERR_NONFINITE", 6: "DP_ERR_TIMEOUT", 7: "DP_ERR_REJECTED",
@@ -56,7 +56,8 @@ class Profile(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("solver", C.c_int), ("prec", C.c_int),
                 ("compress12", C.c_int), ("inner_tol", C.c_double), ("batched", C.c_int),
-                ("use_graph", C.c_int), ("check_every", C.c_int), ("outer_df", C.c_int)]
+                ("use_graph", C.c_int), ("check_every", C.c_int), ("sap_ncy", C.c_int),
+                ("sap_nmr", C.c_int), ("gcr_nkv", C.c_int), ("outer_df", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -192,6 +193,9 @@ def _opts(o):
     s.use_graph = int(o.get("use_graph", 1))
     s.check_every = int(o.get("check_every", 0))
     s.outer_df = int(o.get("outer_df", 0))
+    s.sap_ncy = int(o.get("sap_ncy", 0))
+    s.sap_nmr = int(o.get("sap_nmr", 0))
+    s.gcr_nkv = int(o.get("gcr_nkv", 0))
     return s
 
 

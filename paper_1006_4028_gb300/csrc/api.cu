@@ -354,10 +354,22 @@ dp_status check_opts(const dp_solve_opts *in, dp_solve_opts *out)
         set_error("invalid precision %d", o.prec);
         return DP_ERR_INVALID_ARG;
     }
-    if (o.solver != DP_SOLVER_BICGSTAB && o.solver != DP_SOLVER_CGNE) {
+    if (o.solver != DP_SOLVER_BICGSTAB && o.solver != DP_SOLVER_CGNE && o.solver != DP_SOLVER_SAP_GCR) {
         set_error("unknown solver %d", o.solver);
         return DP_ERR_INVALID_ARG;
     }
+    if (o.solver == DP_SOLVER_SAP_GCR && o.prec == DP_PREC_FP64) {
+        set_error("SAP+GCR runs as the FP32 inner solver: choose a mixed precision");
+        return DP_ERR_INVALID_ARG;
+    }
+    if (o.sap_ncy < 0 || o.sap_ncy > 64 || o.sap_nmr < 0 || o.sap_nmr > 64 || o.gcr_nkv < 0 ||
+        o.gcr_nkv > 32) {
+        set_error("sap_ncy, sap_nmr in [0, 64], gcr_nkv in [0, 32]");
+        return DP_ERR_INVALID_ARG;
+    }
+    if (o.sap_ncy == 0) o.sap_ncy = 4;
+    if (o.sap_nmr == 0) o.sap_nmr = 4;
+    if (o.gcr_nkv == 0) o.gcr_nkv = 8;
     if (!(o.inner_tol >= 0) || o.inner_tol >= 1) {
         set_error("inner_tol must be in [0, 1)");
         return DP_ERR_INVALID_ARG;

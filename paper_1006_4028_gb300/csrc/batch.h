@@ -76,6 +76,9 @@ class Batch {
     dp_status upload_mask(const std::vector<int> &m);
     dp_status bicgstab(int max_iter, int *iters_done);
     dp_status cgne(int max_iter, int *iters_done);
+    dp_status sap_gcr(int max_iter, int *iters_done);
+    // z = SAP(r): the Schwarz alternating procedure as a preconditioner
+    dp_status sap(const void *r, void *z);
     // y64 = Mhat x, t64 = A_qq^-1 D_qp x for the active outer RHS (FP64 or
     // double-float)
     dp_status outer_mhat();
@@ -94,6 +97,11 @@ class Batch {
     double2 *bh = nullptr, *x = nullptr, *r64 = nullptr, *y64 = nullptr, *to64 = nullptr,
             *t64 = nullptr;
     float4 *xdf = nullptr, *tdf = nullptr;  // double-float outer operator (opts.outer_df)
+    static constexpr int kMaxNkv = 32;
+    void *zk[kMaxNkv] = {}, *wk[kMaxNkv] = {};  // SAP+GCR directions and their images
+    double2 *coef_d = nullptr;
+    double *nrm2_d = nullptr;
+    int sap_bs[4] = {0, 0, 0, 0}, sap_nb[4] = {0, 0, 0, 0};
     float2 *hopdf_d = nullptr;
     InnerVecs in;
     RhsState *outer = nullptr, *inner = nullptr;

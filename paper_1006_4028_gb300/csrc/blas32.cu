@@ -348,6 +348,154 @@ k32_cg_update(Cfg c, void *xv, void *rv, const void *pv, const void *wv, long lo
     finish_cg_update(st[2 * q + 1], acc[1], max_iter);
 }
 
+// ---- GCR (the Krylov part of SAP+GCR): per-RHS dot products into device
+// arrays, and updates with per-RHS coefficients read from them ----
+
+// out[r] = <a, b> = sum conj(a) b (complex) per RHS
+__global__ void __launch_bounds__(kMaxBlock)
+k32_dotv(Cfg c, const void *av, const void *bv, long long Vh, int nrhs, const RhsState *st,
+         double2 *out, double *partials, unsigned int *counter)
+{
+    double acc[4] = {0, 0, 0, 0};
+    {
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            f2 re = 0ull, im = 0ull;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                const C2 x = ld1(av, cs, me, k), y = ld1(bv, cs, me, k);
+                re = ffma2(x.re, y.re, re);
+                re = ffma2(x.im, y.im, re);
+                im = ffma2(x.re, y.im, im);
+                im = ffma2(fneg2(x.im), y.re, im);
+            }
+            add_lanes(acc[0], acc[2], re, a0, a1);
+            add_lanes(acc[1], acc[3], im, a0, a1);
+        }
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<2, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    out[2 * q] = make_double2(acc[0], acc[1]);
+    out[2 * q + 1] = make_double2(acc[2], acc[3]);
+}
+
+// out[r] = |a|^2 per RHS
+__global__ void __launch_bounds__(kMaxBlock)
+k32_norm2v(Cfg c, const void *av, long long Vh, int nrhs, const RhsState *st, double *out,
+           double *partials, unsigned int *counter)
+{
+    double acc[2] = {0, 0};
+    {
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            f2 nn = 0ull;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                const C2 x = ld1(av, cs, me, k);
+                nn = ffma2(x.re, x.re, nn);
+                nn = ffma2(x.im, x.im, nn);
+            }
+            add_lanes(acc[0], acc[1], nn, a0, a1);
+        }
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    out[2 * q] = acc[0];
+    out[2 * q + 1] = acc[1];
+}
+
+__device__ __forceinline__ C2 coef_lanes(const double2 *cf, int q, double sign)
+{
+    const double2 c0 = cf[2 * q], c1 = cf[2 * q + 1];
+    return {pk((float)(sign * c0.x), (float)(sign * c1.x)), pk((float)(sign * c0.y), (float)(sign * c1.y))};
+}
+
+// w -= c wi, z -= c zi (modified Gram-Schmidt step, c per RHS)
+__global__ void __launch_bounds__(kMaxBlock)
+k32_mgs(Cfg c, void *wv, void *zv, const void *wiv, const void *ziv, long long Vh, int nrhs,
+        const RhsState *st, const double2 *cf)
+{
+    const int qq = threadIdx.x % (nrhs / 2);
+    const C2 mc = coef_lanes(cf, qq, -1.0);
+    PAIR_LOOP
+    {
+        const long long me = s * P + q;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            st1(wv, cs, me, k, c2_lanefma(mc, ld1(wiv, cs, me, k), ld1(wv, cs, me, k)));
+            st1(zv, cs, me, k, c2_lanefma(mc, ld1(ziv, cs, me, k), ld1(zv, cs, me, k)));
+        }
+    }
+}
+
+// w /= |w|, z /= |w| (nrm = |w|^2 per RHS)
+__global__ void __launch_bounds__(kMaxBlock)
+k32_normalise(Cfg c, void *wv, void *zv, long long Vh, int nrhs, const RhsState *st,
+              const double *nrm)
+{
+    const int qq = threadIdx.x % (nrhs / 2);
+    const double n0 = nrm[2 * qq], n1 = nrm[2 * qq + 1];
+    const f2 sc = pk(n0 > 0 ? (float)(1.0 / sqrt(n0)) : 0.f, n1 > 0 ? (float)(1.0 / sqrt(n1)) : 0.f);
+    PAIR_LOOP
+    {
+        const long long me = s * P + q;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            const C2 w = ld1(wv, cs, me, k), z = ld1(zv, cs, me, k);
+            st1(wv, cs, me, k, {fmul2(sc, w.re), fmul2(sc, w.im)});
+            st1(zv, cs, me, k, {fmul2(sc, z.re), fmul2(sc, z.im)});
+        }
+    }
+}
+
+// x += a z (active lanes), r -= a w, |r|^2 -> convergence (a = <w, r> per RHS)
+__global__ void __launch_bounds__(kMaxBlock)
+k32_gcr_update(Cfg c, void *xv, void *rv, const void *zv, const void *wv, long long Vh, int nrhs,
+               RhsState *st, const double2 *cf, int max_iter, double *partials,
+               unsigned int *counter)
+{
+    double acc[2] = {0, 0};
+    {
+        const int qq = threadIdx.x % (nrhs / 2);
+        const C2 a = coef_lanes(cf, qq, 1.0), ma = coef_lanes(cf, qq, -1.0);
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            const f2 m = (a0 ? 0x00000000ffffffffull : 0ull) | (a1 ? 0xffffffff00000000ull : 0ull);
+            f2 nn = 0ull;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                const C2 x = ld1(xv, cs, me, k);
+                C2 xn = c2_lanefma(a, ld1(zv, cs, me, k), x);
+                xn.re = blend(xn.re, x.re, m);
+                xn.im = blend(xn.im, x.im, m);
+                st1(xv, cs, me, k, xn);
+                const C2 r = c2_lanefma(ma, ld1(wv, cs, me, k), ld1(rv, cs, me, k));
+                st1(rv, cs, me, k, r);
+                nn = ffma2(r.re, r.re, nn);
+                nn = ffma2(r.im, r.im, nn);
+            }
+            add_lanes(acc[0], acc[1], nn, a0, a1);
+        }
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    finish_cg_update(st[2 * q], acc[0], max_iter);
+    finish_cg_update(st[2 * q + 1], acc[1], max_iter);
+}
+
+// out = a - b (every pair)
+__global__ void k32_xmy(const float4 *a, const float4 *b, float4 *out, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const ulonglong2 x = reinterpret_cast<const ulonglong2 *>(a)[i];
+    const ulonglong2 y = reinterpret_cast<const ulonglong2 *>(b)[i];
+    reinterpret_cast<ulonglong2 *>(out)[i] = make_ulonglong2(fsub2(x.x, y.x), fsub2(x.y, y.y));
+}
+
 // r32 (paired) = r64 / |r| per RHS (zero for inactive RHS)
 __global__ void k32_from64(const double2 *r64, float4 *r32, long long Vh, int n, const RhsState *st)
 {
@@ -491,6 +639,64 @@ cudaError_t blas32_cg_update(BlasCtx &bc, void *x, void *r, const void *p, const
     const Cfg c = cfg_wave(bc, k32_cg_update, Vh, nrhs / 2);
     k32_cg_update<<<c.grid, c.block, 0, s>>>(c, x, r, p, w, Vh, nrhs, st, max_iter, bc.partials,
                                              bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_dotv(BlasCtx &bc, const void *a, const void *b, long long Vh, int nrhs,
+                        const RhsState *st, double2 *out, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_dotv, Vh, nrhs / 2);
+    k32_dotv<<<c.grid, c.block, 0, s>>>(c, a, b, Vh, nrhs, st, out, bc.partials, bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_norm2v(BlasCtx &bc, const void *a, long long Vh, int nrhs, const RhsState *st,
+                          double *out, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_norm2v, Vh, nrhs / 2);
+    k32_norm2v<<<c.grid, c.block, 0, s>>>(c, a, Vh, nrhs, st, out, bc.partials, bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_mgs(BlasCtx &bc, void *w, void *z, const void *wi, const void *zi, long long Vh,
+                       int nrhs, const RhsState *st, const double2 *cf, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_mgs, Vh, nrhs / 2);
+    k32_mgs<<<c.grid, c.block, 0, s>>>(c, w, z, wi, zi, Vh, nrhs, st, cf);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_normalise(BlasCtx &bc, void *w, void *z, long long Vh, int nrhs,
+                             const RhsState *st, const double *nrm, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_normalise, Vh, nrhs / 2);
+    k32_normalise<<<c.grid, c.block, 0, s>>>(c, w, z, Vh, nrhs, st, nrm);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_gcr_update(BlasCtx &bc, void *x, void *r, const void *z, const void *w,
+                              long long Vh, int nrhs, RhsState *st, const double2 *cf, int max_iter,
+                              cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_gcr_update, Vh, nrhs / 2);
+    k32_gcr_update<<<c.grid, c.block, 0, s>>>(c, x, r, z, w, Vh, nrhs, st, cf, max_iter, bc.partials,
+                                              bc.counter);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return blas_count_active(bc, st, nrhs, s);
+}
+
+cudaError_t blas32_xmy(const void *a, const void *b, void *out, long long Vh, int nrhs, cudaStream_t s)
+{
+    const long long n = Vh * 12 * (nrhs / 2);
+    k32_xmy<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(static_cast<const float4 *>(a),
+                                                         static_cast<const float4 *>(b),
+                                                         static_cast<float4 *>(out), n);
     return cudaGetLastError();
 }
 

@@ -246,6 +246,43 @@ cudaError_t blas32_cg_alpha(BlasCtx &bc, const void *w, long long Vh, int nrhs, 
                             cudaStream_t s);
 cudaError_t blas32_cg_update(BlasCtx &bc, void *x, void *r, const void *p, const void *w,
                              long long Vh, int nrhs, RhsState *st, int max_iter, cudaStream_t s);
+// GCR on the paired FP32 layout (blas32.cu): per-RHS <a, b> and |a|^2 into
+// device arrays; w -= c wi and z -= c zi; w, z /= |w|; x += a z, r -= a w
+// with |r|^2 deciding convergence (finish_cg_update); out = a - b
+cudaError_t blas32_dotv(BlasCtx &bc, const void *a, const void *b, long long Vh, int nrhs,
+                        const RhsState *st, double2 *out, cudaStream_t s);
+cudaError_t blas32_norm2v(BlasCtx &bc, const void *a, long long Vh, int nrhs, const RhsState *st,
+                          double *out, cudaStream_t s);
+cudaError_t blas32_mgs(BlasCtx &bc, void *w, void *z, const void *wi, const void *zi, long long Vh,
+                       int nrhs, const RhsState *st, const double2 *cf, cudaStream_t s);
+cudaError_t blas32_normalise(BlasCtx &bc, void *w, void *z, long long Vh, int nrhs,
+                             const RhsState *st, const double *nrm, cudaStream_t s);
+cudaError_t blas32_gcr_update(BlasCtx &bc, void *x, void *r, const void *z, const void *w,
+                              long long Vh, int nrhs, RhsState *st, const double2 *cf, int max_iter,
+                              cudaStream_t s);
+cudaError_t blas32_xmy(const void *a, const void *b, void *out, long long Vh, int nrhs, cudaStream_t s);
+
+// Schwarz block solves of SAP+GCR (sap.cu)
+struct SapParams {
+    const void *res;                  // global residual, parity `parity`, paired FP32
+    void *z;                          // global correction, += the block solutions
+    const void *links[2];             // per parity, FP32 or 16-bit format
+    const void *clov[2][kMaxGroups];  // FP32 clover inverses per parity and group
+    const void *hop;                  // FP32 hop tables [group][8][Lmax]
+    int8_t grp_of[kMaxRhs];
+    const int *active;                // RhsState rows (stride active_stride) or NULL
+    int active_stride;
+    Geom g;
+    int parity;                       // the Schur parity p
+    int nrhs;
+    int bs[4], nb[4];                 // block extents and blocks per direction (t, x, y, z)
+    int colour;                       // blocks with (bt + bx + by + bz) % 2 == colour
+    int n_mr;                         // minimal-residual steps per block
+};
+// block extents: 4 where the extent allows, else 2; false if an extent is odd
+bool sap_blocks(const Geom &g, int bs[4], int nb[4]);
+cudaError_t launch_sap_block(const SapParams &p, int link_fmt, cudaStream_t st);
+
 // FP64 outer loop helpers
 // r = b - y (r = b for `fresh` RHS); |r|^2 -> st.rr; st.scale = |r|;
 // convergence vs st.tol2 -> active

@@ -232,6 +232,26 @@ dp_status Batch::init()
     set_shape(opin, c->launch_shape(Vh, ipr, ilf, n));
     opin_adj = opin;
     opin_adj.hop = ipr == 0 ? (const void *)hopadj64_d : (const void *)hopadj32_d;
+    if (mixed && opts.solver == DP_SOLVER_SAP_GCR) {
+        if (!sap_blocks(g, sap_bs, sap_nb)) {
+            set_error("SAP+GCR needs even lattice extents");
+            return DP_ERR_INVALID_ARG;
+        }
+        for (int k = 0; k < opts.gcr_nkv; k++) {
+            zk[k] = get(vin);
+            wk[k] = get(vin);
+            if (!zk[k] || !wk[k]) {
+                set_error("out of device memory for the GCR Krylov vectors");
+                return DP_ERR_OOM;
+            }
+        }
+        coef_d = (double2 *)get(sizeof(double2) * kMaxRhs);
+        nrm2_d = (double *)get(sizeof(double) * kMaxRhs);
+        if (!coef_d || !nrm2_d) {
+            set_error("out of device memory");
+            return DP_ERR_OOM;
+        }
+    }
     if (mixed && opts.outer_df) {
         xdf = (float4 *)get(v64);
         tdf = (float4 *)get(v64);
@@ -494,6 +514,90 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
     return DP_OK;
 }
 
+dp_status Batch::sap(const void *r, void *z)
+{
+    const long long Vh = f->g.Vh;
+    CK(cudaMemsetAsync(z, 0, vin, c->stream));
+    CK(cudaMemcpyAsync(in.s, r, vin, cudaMemcpyDeviceToDevice, c->stream));
+    SapParams P{};
+    P.res = in.s;
+    P.z = z;
+    P.links[0] = opin.links[0];
+    P.links[1] = opin.links[1];
+    for (int p = 0; p < 2; p++)
+        for (int k = 0; k < kMaxGroups; k++) P.clov[p][k] = opin.inv[p][k];
+    P.hop = opin.hop;
+    memcpy(P.grp_of, opin.grp_of, sizeof P.grp_of);
+    P.active = state_mask(inner);
+    P.active_stride = kStateStride;
+    P.g = f->g;
+    P.parity = sp;
+    P.nrhs = n;
+    for (int mu = 0; mu < 4; mu++) {
+        P.bs[mu] = sap_bs[mu];
+        P.nb[mu] = sap_nb[mu];
+    }
+    P.n_mr = opts.sap_nmr;
+    for (int cyc = 0; cyc < opts.sap_ncy; cyc++)
+        for (int colour = 0; colour < 2; colour++) {
+            P.colour = colour;
+            cudaEvent_t ev;
+            c->time_begin("sap_block", &ev);
+            CK(launch_sap_block(P, opin.lf, c->stream));
+            c->time_end("sap_block", ev);
+            c->launches++;
+            if (cyc == opts.sap_ncy - 1 && colour == 1) break;
+            // global residual of the correction so far: res = r - Mhat z
+            dp_status s = apply_mhat(c, opin, sp, z, in.v, in.to, inner);
+            if (s != DP_OK) return s;
+            CK(blas32_xmy(r, in.v, in.s, Vh, n, c->stream));
+            c->launches++;
+        }
+    return DP_OK;
+}
+
+// GCR preconditioned by SAP, restarted every gcr_nkv directions; per RHS:
+// z_k = SAP(r), w_k = Mhat z_k orthonormalised against w_0..w_{k-1} (the same
+// combinations applied to z_k), then x += <w_k, r> z_k, r -= <w_k, r> w_k
+dp_status Batch::sap_gcr(int max_iter, int *iters_done)
+{
+    BlasCtx &bc = c->bc;
+    const long long Vh = f->g.Vh;
+    CK(blas_bicg_init(bc, 1, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, c->stream));
+    c->launches += 2;
+    CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *iters_done = 0;
+    if (*c->h_nactive == 0) return DP_OK;
+    int it = 0;
+    while (it < max_iter) {
+        for (int k = 0; k < opts.gcr_nkv && it < max_iter; k++) {
+            dp_status s = sap(in.r, zk[k]);
+            if (s != DP_OK) return s;
+            s = apply_mhat(c, opin, sp, zk[k], wk[k], in.to, inner);
+            if (s != DP_OK) return s;
+            for (int i = 0; i < k; i++) {
+                CK(blas32_dotv(bc, wk[i], wk[k], Vh, n, inner, coef_d, c->stream));
+                CK(blas32_mgs(bc, wk[k], zk[k], wk[i], zk[i], Vh, n, inner, coef_d, c->stream));
+            }
+            CK(blas32_norm2v(bc, wk[k], Vh, n, inner, nrm2_d, c->stream));
+            CK(blas32_normalise(bc, wk[k], zk[k], Vh, n, inner, nrm2_d, c->stream));
+            CK(blas32_dotv(bc, wk[k], in.r, Vh, n, inner, coef_d, c->stream));
+            CK(blas32_gcr_update(bc, in.x, in.r, zk[k], wk[k], Vh, n, inner, coef_d, max_iter, c->stream));
+            c->launches += 2 * k + 5;
+            it++;
+            CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (*c->h_nactive == 0) {
+                *iters_done = it;
+                return DP_OK;
+            }
+        }
+    }
+    *iters_done = it;
+    return DP_OK;
+}
+
 dp_status Batch::outer_mhat()
 {
     if (!xdf) return apply_mhat(c, op64, sp, x, y64, t64, outer);
@@ -630,7 +734,9 @@ dp_status Batch::round()
     // inner budget of this round
     int budget = round_iters > 0 ? round_iters : opts.max_iter;
     int done = 0;
-    dp_status s = opts.solver == DP_SOLVER_CGNE ? cgne(budget, &done) : bicgstab(budget, &done);
+    dp_status s = opts.solver == DP_SOLVER_CGNE      ? cgne(budget, &done)
+                  : opts.solver == DP_SOLVER_SAP_GCR ? sap_gcr(budget, &done)
+                                                     : bicgstab(budget, &done);
     if (s != DP_OK) return s;
     CK(cudaMemcpyAsync(hin.data(), inner, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));

@@ -27,6 +27,8 @@ CGNE_MIXED = {"prec": "mixed_fp32", "solver": "cgne", "batched": 1, "use_graph":
 CGNE_FP64 = {"prec": "fp64", "solver": "cgne", "batched": 1, "use_graph": 0}
 # the outer loop's Schur operator in double-float (two FP32 per real)
 MIXED_DF = {"prec": "mixed_fp32", "batched": 1, "use_graph": 1, "outer_df": 1}
+# the paper's solver: GCR preconditioned by the Schwarz alternating procedure
+SAP_GCR = {"prec": "mixed_fp32", "solver": "sap_gcr", "batched": 1, "use_graph": 0}
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +39,7 @@ def ctx():
     dp.dp_destroy(c)
 
 
-@pytest.mark.parametrize("opts", [MIXED, PLAIN, FP64_BATCHED])
+@pytest.mark.parametrize("opts", [MIXED, PLAIN, FP64_BATCHED, SAP_GCR])
 def test_free_16x8_exp_profile_matches_momentum_space(ctx, opts):
     """Free field 16x8^3, antiperiodic time, M = 0.5, exp(alpha0 y0) with
     alpha0 = 0.4, point source at the origin, r = 1e-11."""
@@ -71,7 +73,7 @@ CASES = [(0.5, ("cosh_t", 0.4), (0, 0, 0, 0)), (0.8, ("cosh_t", 0.5), (3, 1, 2, 
 
 @pytest.mark.parametrize("M,prof,src", CASES)
 @pytest.mark.parametrize("opts", [MIXED, MIXED_NOGRAPH, PLAIN, MIXED_FP16, MIXED_BF16, CGNE_MIXED,
-                                  CGNE_FP64, MIXED_DF])
+                                  CGNE_FP64, MIXED_DF, SAP_GCR])
 def test_interacting_solve_matches_oracle(ctx, inter, M, prof, src, opts):
     dims, f, op = inter
     T, V = dims[0], int(np.prod(dims))
