@@ -360,8 +360,22 @@ def config_light64(dp, ctx, args):
                      "seconds": dt, "profile_range": rng_,
                      "cpp_rel_diff_vs_unprec_r1e-13_max_to_T2": float(dev.max()),
                      "first_slice_over_1e-6": int(over[0]) if len(over) else None})
+    # the paper's Table I comparison with its own solver: SAP+GCR iterations
+    # against alpha0 (FP32 links, r = 1e-10)
+    sap_rows = []
+    for ncy in (4, 2):
+        for a0 in (0.0, 0.2, 0.4):
+            prof = ("none", 0.0) if a0 == 0 else ("cosh_4d", a0)
+            osap = {"prec": "mixed_fp32", "solver": "sap_gcr", "batched": 1, "use_graph": 0,
+                    "sap_ncy": ncy, "sap_nmr": 4, "gcr_nkv": 8, "max_iter": 4000}
+            (cpp, _, info), dt = _timed(lambda: dp.dp_solve_point(ctx, f, 0.005, prof, src, 1e-10, osap,
+                                                                  T=64))
+            sap_rows.append({"M": 0.005, "alpha0": a0, "sap_ncy": ncy, "gcr_iters": info["iters_inner"],
+                             "iters_outer": info["iters_outer"], "status": info["status"],
+                             "true_rel_residue": info["true_rel_residue"], "seconds": dt})
     dp.dp_field_free(ctx, f)
     return {"workload": "light-quark solves 64x32^3 (eps 0.5, seed 7, c_sw 1.9), r = 1e-10",
+            "sap_gcr": sap_rows,
             "inner": "%s (%s) in FP64 defect correction" % (prec, LINKS[prec]), "solves": rows}
 
 

@@ -437,7 +437,9 @@ k32_normalise(Cfg c, void *wv, void *zv, long long Vh, int nrhs, const RhsState 
 {
     const int qq = threadIdx.x % (nrhs / 2);
     const double n0 = nrm[2 * qq], n1 = nrm[2 * qq + 1];
-    const f2 sc = pk(n0 > 0 ? (float)(1.0 / sqrt(n0)) : 0.f, n1 > 0 ? (float)(1.0 / sqrt(n1)) : 0.f);
+    // a vanishing direction (|w|^2 below FP32 range) is dropped rather than
+    // scaled to overflow
+    const f2 sc = pk(n0 > 1e-60 ? (float)(1.0 / sqrt(n0)) : 0.f, n1 > 1e-60 ? (float)(1.0 / sqrt(n1)) : 0.f);
     PAIR_LOOP
     {
         const long long me = s * P + q;

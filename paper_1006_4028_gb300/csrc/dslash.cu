@@ -753,8 +753,10 @@ cudaError_t launch32s(const DslashParams &p, int block, int stages, cudaStream_t
 }
 
 template <int LF>
-cudaError_t launch32s_epi(const DslashParams &p, int epi, int block, int stages, cudaStream_t st)
+cudaError_t launch32s_epi(const DslashParams &p, int epi, int block, int stages, int rpt,
+                          cudaStream_t st)
 {
+    (void)rpt;
     if (epi == EPI_AINV) return launch32s<LF, EPI_AINV>(p, block, stages, st);
     return launch32s<LF, EPI_XMY_AINV>(p, block, stages, st);
 }
@@ -799,9 +801,9 @@ cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi
     }
     if (stages > 0) {
         if (!dslash_staged_ok(prec, link_fmt, epi, rpt, stages, block)) return cudaErrorInvalidValue;
-        if (link_fmt == LINK_F32_12) return launch32s_epi<LINK_F32_12>(p, epi, block, stages, st);
-        if (link_fmt == LINK_H16_12) return launch32s_epi<LINK_H16_12>(p, epi, block, stages, st);
-        return launch32s_epi<LINK_B16_12>(p, epi, block, stages, st);
+        if (link_fmt == LINK_F32_12) return launch32s_epi<LINK_F32_12>(p, epi, block, stages, rpt, st);
+        if (link_fmt == LINK_H16_12) return launch32s_epi<LINK_H16_12>(p, epi, block, stages, rpt, st);
+        return launch32s_epi<LINK_B16_12>(p, epi, block, stages, rpt, st);
     }
     const int ppt = rpt / 2;
     if (link_fmt == LINK_F32_12)

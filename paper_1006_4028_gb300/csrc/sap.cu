@@ -226,9 +226,12 @@ __global__ void __launch_bounds__(128) k_sap_block(const SapParams p)
         }
         block_sum6(d, red);
         if (live) {
-            // omega = <q, rho> / |q|^2 per lane; delta += omega rho, rho -= omega q
-            const float n0 = d[4] > 0.f ? 1.f / d[4] : 0.f, n1 = d[5] > 0.f ? 1.f / d[5] : 0.f;
-            const C2 om = {pk(d[0] * n0, d[1] * n1), pk(d[2] * n0, d[3] * n1)};
+            // omega = <q, rho> / |q|^2 per lane; delta += omega rho, rho -= omega q.
+            // Far from a point source a block's residual can be so small that
+            // |q|^2 is subnormal: such a block is left alone (omega = 0)
+            const bool ok0 = d[4] > 1e-30f, ok1 = d[5] > 1e-30f;
+            const C2 om = {pk(ok0 ? d[0] / d[4] : 0.f, ok1 ? d[1] / d[5] : 0.f),
+                           pk(ok0 ? d[2] / d[4] : 0.f, ok1 ? d[3] / d[5] : 0.f)};
             const C2 mom = {fneg2(om.re), fneg2(om.im)};
 #pragma unroll
             for (int k = 0; k < 12; k++) {
