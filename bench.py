@@ -746,6 +746,15 @@ def main():
     del buf_in, buf_out
     iso_gbs = Vh * b_ainv / (iso_ms / 1e3) / 1e9
 
+    # DRAM bytes of one launch of the tuned kernel, from an ncu capture of this
+    # workload (dram__bytes_read.sum + dram__bytes_write.sum, A^-1 D launch,
+    # all 12 RHS active, 12-real FP32 links, staged 2 stages x 96 threads):
+    # valid only while the tuner picks that kernel
+    traffic, traffic_note = None, "tuned shape differs from the captured kernel"
+    if args.prec == "mixed_fp32" and list(tuned.get("mixed_fp32_n12", [])[:3]) == [96, 2, 2]:
+        traffic = 642086144 + 351439872
+        traffic_note = ("ncu dram bytes of one A^-1 D launch (algorithmic %.0f bytes); "
+                        "profiles/dslash_fp32_12rhs_32x16.md" % (Vh * b_ainv))
     # ---- end to end: host-buffer C-ABI call per solve (wall clock) ----
     e2e_steps = max(3, min(args.steps, 5))
     torch.cuda.synchronize()
@@ -775,7 +784,8 @@ def main():
                        "outer_mean": float(np.mean([i["iters_outer"] for i in infos])),
                        "true_rel_residue_max": float(max(i["true_rel_residue"] for i in infos))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "traffic_note": traffic_note,
                      "kernel": "dslash_fp32 (12 RHS, %s, fused A^-1 epilogue)" % LINKS[args.prec],
                      "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                      "launches": d32_n, "peak_source": peak_src,

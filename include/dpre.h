@@ -211,6 +211,19 @@ dp_status dp_solve_point_corr(dp_ctx *ctx, dp_field field, double M, const dp_pr
                               const int src[4], double r, const dp_solve_opts *opts, double *cpp_out,
                               double *cap_out, dp_solve_info *info);
 
+/* A heavy and a light quark from the same point source, each with its own
+ * mass and profile, in one batch; besides each one's C_PP (cpp_out
+ * [2][T], heavy first) the heavy-light pseudoscalar correlator
+ *   hl_out[2 y0 + {0, 1}] = (re, im) of -sum_{y vec} tr[S_h(y) S_l(y)^dag]
+ * (= -tr[gamma_5 S_h(y,x) gamma_5 S_l(x,y)]), each propagator restored by its
+ * own profile before the contraction (Sec. III); y0 relative to the source
+ * time, host [T][2], caller-owned.  With equal masses and profiles it
+ * equals C_PP.  info: [2].  Always one batched solve. */
+dp_status dp_solve_point_hl(dp_ctx *ctx, dp_field field, double M_h, const dp_profile *profile_h,
+                            double M_l, const dp_profile *profile_l, const int src[4], double r,
+                            const dp_solve_opts *opts, double *cpp_out, double *hl_out,
+                            dp_solve_info *info);
+
 /* As dp_solve_point_multi, but cpp_out is DEVICE memory ([n_mass][T] doubles)
  * written on the context stream; nothing is copied to the host except the
  * convergence flags the iteration loop reads. */

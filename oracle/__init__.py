@@ -351,6 +351,15 @@ def contract_cap(S, dims, t_src):
     return np.roll(per_t, -int(t_src))
 
 
+def contract_hl(Sh, Sl, dims, t_src):
+    """Heavy-light pseudoscalar correlator C(y0) = -sum_{y vec} tr[S_h S_l^dag]
+    (= -tr[gamma_5 S_h(y,x) gamma_5 S_l(x,y)] by gamma_5-hermiticity), complex,
+    y0 relative to t_src.  Sh, Sl: (12, T, Lz, Ly, Lx, 4, 3), each restored by
+    its own profile (Sec. III: restore before contracting)."""
+    per_t = np.einsum("jtzyxsc,jtzyxsc->t", Sh, np.conj(Sl))
+    return -np.roll(per_t, -int(t_src))
+
+
 def pcac_mass(cpp, cap):
     """m_PCAC(y0) = [C_AP(y0+1) - C_AP(y0-1)] / 2 / (2 C_PP(y0)), y0 = 1..T-2
     (the unimproved local-current ratio; the paper quotes am_PCAC to label its

@@ -26,7 +26,7 @@ __all__ = [
     "dp_create", "dp_destroy", "dp_last_error", "dp_device_bytes",
     "dp_field_load", "dp_field_set_csw", "dp_field_free",
     "dp_solve_point", "dp_solve_point_multi", "dp_solve_point_dev",
-    "dp_solve_point_corr", "pcac_mass", "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
+    "dp_solve_point_corr", "dp_solve_point_hl", "pcac_mass", "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
     "dp_autotune",
     "dp_timing_enable", "dp_timing_reset", "dp_timing_get", "dp_launch_count",
     "dp_serve_start", "dp_submit", "dp_wait", "dp_cancel", "dp_serve_stats_get", "dp_serve_stop",
@@ -119,6 +119,8 @@ def load(build_if_missing=False):
         "dp_solve_point_dev": ([vp, up, ip, vp, vp, P(C.c_int * 4), dp, P(SolveOpts), vp, vp], ip),
         "dp_solve_point_corr": ([vp, up, dp, P(Profile), P(C.c_int * 4), dp, P(SolveOpts), vp, vp,
                                  P(SolveInfo)], ip),
+        "dp_solve_point_hl": ([vp, up, dp, P(Profile), dp, P(Profile), P(C.c_int * 4), dp,
+                               P(SolveOpts), vp, vp, vp], ip),
         "dp_apply": ([vp, up, ip, dp, P(Profile), P(C.c_int * 4), ip, ip, vp, vp, ip], ip),
         "dp_profile_tables": ([P(C.c_int * 4), ip, P(Profile), P(C.c_int * 4), vp, vp], ip),
         "dp_restore_contract_dev": ([vp, up, ip, vp, vp, vp, vp, vp], ip),
@@ -269,6 +271,21 @@ def dp_solve_point_corr(ctx, field, M, profile, src, r, opts=None, T=None, allow
                                     C.byref(info))
     _check(st, allow)
     return cpp, cap, info.as_dict()
+
+
+def dp_solve_point_hl(ctx, field, Mh, prof_h, Ml, prof_l, src, r, opts=None, T=None,
+                      allow=(3,)):
+    """Heavy and light quark from one source: (cpp[2, T], hl[T] complex, [info h, info l])."""
+    ph, kh = _profile(prof_h)
+    pl, kl = _profile(prof_l)
+    cpp = np.zeros((2, int(T)))
+    hl = np.zeros((int(T), 2))
+    infos = (SolveInfo * 2)()
+    st = load().dp_solve_point_hl(ctx, int(field), float(Mh), C.byref(ph), float(Ml), C.byref(pl),
+                                  C.byref(_i4(src)), float(r), C.byref(_opts(opts)), _ptr(cpp), _ptr(hl),
+                                  infos)
+    _check(st, allow)
+    return cpp, hl[:, 0] + 1j * hl[:, 1], [infos[0].as_dict(), infos[1].as_dict()]
 
 
 def pcac_mass(cpp, cap):

@@ -65,6 +65,10 @@ class Batch {
     dp_status round();
     // finish jobs whose RHS are all done: odd sites, residual, restore, C_PP
     dp_status harvest(std::vector<Job *> &finished);
+    // after harvest: heavy-light correlator of two finished jobs of this
+    // batch (both parities of their solutions stay in place until the next
+    // admission): out_dev [T][2] (re, im)
+    dp_status contract_hl(const Job &h, const Job &l, double *out_dev);
     int active_jobs() const;
     // at most this many jobs at once (0: as many as the slots hold)
     void set_max_jobs(int m) { max_jobs = m; }

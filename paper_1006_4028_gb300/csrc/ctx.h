@@ -146,7 +146,8 @@ struct SolveResult {
 // cap_dev (optional, device [n_groups][T]): also C_AP(y0)
 dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group> &groups, double r_target,
                        const dp_solve_opts &opts, double *cpp_dev, double *prop_host,
-                       std::vector<SolveResult> &res, double *cap_dev = nullptr);
+                       std::vector<SolveResult> &res, double *cap_dev = nullptr,
+                       double *hl_dev = nullptr);
 
 dp_status check_opts(const dp_solve_opts *in, dp_solve_opts *out);
 

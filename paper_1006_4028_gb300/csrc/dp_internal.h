@@ -174,6 +174,12 @@ cudaError_t launch_restore_contract(const double2 *xe, const double2 *xo, const 
                                     const int *t_src_dev, const int *mask, double *cpp_dev,
                                     double *partials, double2 *prop_lex, cudaStream_t st,
                                     double *cap_dev = nullptr);
+// heavy-light C(y0) = -sum_{y vec} tr[S_h S_l^dag] of two groups' propagators
+// (slots slot_h.. and slot_l.., 12 each, groups gh, gl for their profiles);
+// out_dev [T][2] (re, im), y0 relative to t_src; partials: 2 * T * P doubles
+cudaError_t launch_contract_hl(const double2 *xe, const double2 *xo, const Geom &g, int nrhs,
+                               const double *alpha, int gh, int gl, int slot_h, int slot_l, int t_src,
+                               double *partials, double *out_dev, cudaStream_t st);
 // dst[k] (+)= src[k], k < T (accumulate != 0: add)
 cudaError_t launch_cpp_commit(const double *src, double *dst, int T, int accumulate, cudaStream_t st);
 

@@ -283,6 +283,79 @@ __global__ void k_contract_final(const double *partials, int P, int T, int nm, c
     }
 }
 
+// grid (P, T): the heavy-light bilinear sum_{k, j} S_h(k, j) conj(S_l(k, j))
+// over block p's share of slice t (j: the 12 source components, k: sink spin
+// and colour), each propagator restored by its own group's profile;
+// partials[((t*P + p)) * 2 + {0: re, 1: im}]
+__global__ void __launch_bounds__(kContractBlock)
+    k_contract_hl(const double2 *xe, const double2 *xo, Geom g, int n, const double *alpha, int gh,
+                  int gl, int sh, int sl, double *partials)
+{
+    const int P = gridDim.x, p = blockIdx.x, t = blockIdx.y;
+    const long long Vs = g.Vh / g.T;
+    const long long chunk = (Vs + P - 1) / P;
+    const long long j0 = p * chunk, j1 = min(Vs, j0 + chunk);
+    const long long cs = g.Vh * n;
+    const double *ah = alpha + (long long)gh * 4 * g.Lmax, *al = alpha + (long long)gl * 4 * g.Lmax;
+    double re = 0, im = 0;
+    const long long work = (j1 > j0 ? j1 - j0 : 0) * 12;
+    for (long long e = threadIdx.x; e < work; e += blockDim.x) {
+        const long long s = (long long)t * Vs + j0 + e / 12;
+        const int j = (int)(e % 12);
+        const int xh = (int)(s % g.Lxh);
+        long long q = s / g.Lxh;
+        const int y = (int)(q % g.Ly);
+        q /= g.Ly;
+        const int z = (int)(q % g.Lz);
+        const double bh = ah[0 * g.Lmax + t] * ah[2 * g.Lmax + y] * ah[3 * g.Lmax + z];
+        const double bl = al[0 * g.Lmax + t] * al[2 * g.Lmax + y] * al[3 * g.Lmax + z];
+        for (int par = 0; par < 2; par++) {
+            const int x = 2 * xh + ((t + y + z + par) & 1);
+            const double inv = 1.0 / (bh * ah[1 * g.Lmax + x] * bl * al[1 * g.Lmax + x]);
+            const double2 *vh = (par ? xo : xe) + s * n + sh + j;
+            const double2 *vl = (par ? xo : xe) + s * n + sl + j;
+            double sr = 0, si = 0;
+            for (int k = 0; k < 12; k++) {
+                const double2 a = vh[k * cs], b = vl[k * cs];
+                sr = fmx(a.x, b.x, fmx(a.y, b.y, sr));
+                si = fmx(a.y, b.x, fmx(-a.x, b.y, si));
+            }
+            re += sr * inv;
+            im += si * inv;
+        }
+    }
+    __shared__ double sh_re[kContractBlock], sh_im[kContractBlock];
+    sh_re[threadIdx.x] = re;
+    sh_im[threadIdx.x] = im;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sh_re[threadIdx.x] += sh_re[threadIdx.x + w];
+            sh_im[threadIdx.x] += sh_im[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[((long long)t * P + p) * 2] = sh_re[0];
+        partials[((long long)t * P + p) * 2 + 1] = sh_im[0];
+    }
+}
+
+// out[2 rel + {0, 1}] = -(re, im) summed over p in order, rel = (t - t_src) mod T
+__global__ void k_contract_hl_final(const double *partials, int P, int T, int t_src, double *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    double re = 0, im = 0;
+    for (int p = 0; p < P; p++) {
+        re += partials[((long long)t * P + p) * 2];
+        im += partials[((long long)t * P + p) * 2 + 1];
+    }
+    const int rel = ((t - t_src) % T + T) % T;
+    out[2 * rel] = -re;
+    out[2 * rel + 1] = -im;
+}
+
 __global__ void k_cpp_commit(const double *src, double *dst, int T, int accumulate)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -340,6 +413,20 @@ cudaError_t launch_point_source(const Geom &g, const SlotInfo *slots_dev, int nr
                                 const int *mask, double2 *even, double2 *odd, cudaStream_t st)
 {
     k_point_source<<<1, kMaxRhs, 0, st>>>(g, slots_dev, nrhs, mask, even, odd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract_hl(const double2 *xe, const double2 *xo, const Geom &g, int nrhs,
+                               const double *alpha, int gh, int gl, int slot_h, int slot_l, int t_src,
+                               double *partials, double *out_dev, cudaStream_t st)
+{
+    const int P = contract_blocks_per_slice(g);
+    dim3 grid(P, g.T);
+    k_contract_hl<<<grid, kContractBlock, 0, st>>>(xe, xo, g, nrhs, alpha, gh, gl, slot_h, slot_l,
+                                                   partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_contract_hl_final<<<(g.T + 127) / 128, 128, 0, st>>>(partials, P, g.T, t_src, out_dev);
     return cudaGetLastError();
 }
 

@@ -598,6 +598,19 @@ dp_status Batch::sap_gcr(int max_iter, int *iters_done)
     return DP_OK;
 }
 
+dp_status Batch::contract_hl(const Job &h, const Job &l, double *out_dev)
+{
+    if (h.slot0 < 0 || l.slot0 < 0 || h.ncomp != 12 || l.ncomp != 12) {
+        set_error("heavy-light contraction needs two whole 12-RHS jobs of this batch");
+        return DP_ERR_INVALID_ARG;
+    }
+    const Geom &g = f->g;
+    CK(launch_contract_hl(sp == 0 ? x : y64, sp == 0 ? y64 : x, g, n, alpha_d, h.tab, l.tab, h.slot0,
+                          l.slot0, h.grp.src[0], cpart, out_dev, c->stream));
+    c->launches += 2;
+    return DP_OK;
+}
+
 dp_status Batch::outer_mhat()
 {
     if (!xdf) return apply_mhat(c, op64, sp, x, y64, t64, outer);
@@ -784,8 +797,10 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
         // other parity q = 1 - p: x_q = A_qq^-1 (eta'_q - D_qp x_p)
         //                           = A_qq^-1 eta'_q - t64, t64 = A_qq^-1 D_qp x_p
         // from the last FP64 Schur application (x_p final): no extra dslash
-        CK(cudaMemsetAsync(y64, 0, v64, c->stream));
-        CK(cudaMemsetAsync(to64, 0, v64, c->stream));
+        // only this job's slots: the other parity of jobs finished earlier
+        // stays in y64 (heavy-light contractions read it)
+        CK(blas_zero_masked(y64, Vh, n, mask_d, c->stream));
+        CK(blas_zero_masked(to64, Vh, n, mask_d, c->stream));
         CK(launch_point_source(g, slots_d, n, mask_d, sp == 0 ? y64 : to64, sp == 0 ? to64 : y64,
                                c->stream));
         CloverApplyParams cp{};
@@ -856,7 +871,7 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
 
 dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group> &groups,
                        double r_target, const dp_solve_opts &o, double *cpp_dev, double *prop_host,
-                       std::vector<SolveResult> &res, double *cap_dev)
+                       std::vector<SolveResult> &res, double *cap_dev, double *hl_dev)
 {
     const Geom &g = f->g;
     const int ng = (int)groups.size();
@@ -919,6 +934,14 @@ dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group
         s = B.harvest(fin);
         if (s != DP_OK) return s;
     }
+    if (hl_dev) {
+        if (!batched || ng != 2) {
+            set_error("heavy-light contraction needs one batched solve of two masses");
+            return DP_ERR_INVALID_ARG;
+        }
+        s = B.contract_hl(jobs[0], jobs[1], hl_dev);
+        if (s != DP_OK) return s;
+    }
     dp_status ret = DP_OK;
     for (int gi = 0; gi < ng; gi++) {
         SolveResult &R = res[gi];
@@ -949,7 +972,8 @@ using namespace dp;
 static dp_status solve_common(dp_ctx *ctx, dp_field field, int n_mass, const double *M,
                               const dp_profile *profiles, const int src[4], double r,
                               const dp_solve_opts *opts, double *cpp_out, int cpp_on_device,
-                              double *prop_out, dp_solve_info *info, double *cap_out = nullptr)
+                              double *prop_out, dp_solve_info *info, double *cap_out = nullptr,
+                              double *hl_out = nullptr)
 {
     if (!ctx) {
         set_error("null context");
@@ -998,24 +1022,29 @@ static dp_status solve_common(dp_ctx *ctx, dp_field field, int n_mass, const dou
         cpp_dev = (double *)tmp;
     }
     if (cap_out) tmp_ap = c.alloc(sizeof(double) * n_mass * fp->g.T);
+    void *tmp_hl = hl_out ? c.alloc(sizeof(double) * 2 * fp->g.T) : nullptr;
     std::vector<SolveResult> res;
-    if (!cpp_dev || (cap_out && !tmp_ap)) {
+    if (!cpp_dev || (cap_out && !tmp_ap) || (hl_out && !tmp_hl)) {
         fp->users--;
         c.release(tmp);
         c.release(tmp_ap);
+        c.release(tmp_hl);
         set_error("out of device memory");
         return DP_ERR_OOM;
     }
-    s = solve_groups(&c, fp, groups, r, o, cpp_dev, prop_out, res, (double *)tmp_ap);
+    s = solve_groups(&c, fp, groups, r, o, cpp_dev, prop_out, res, (double *)tmp_ap, (double *)tmp_hl);
     if (s == DP_OK || s == DP_ERR_NOT_CONVERGED || s == DP_ERR_BREAKDOWN) {
         if (!cpp_on_device)
             cudaMemcpyAsync(cpp_out, cpp_dev, sizeof(double) * n_mass * fp->g.T, cudaMemcpyDeviceToHost, c.stream);
         if (cap_out)
             cudaMemcpyAsync(cap_out, tmp_ap, sizeof(double) * n_mass * fp->g.T, cudaMemcpyDeviceToHost, c.stream);
+        if (hl_out)
+            cudaMemcpyAsync(hl_out, tmp_hl, sizeof(double) * 2 * fp->g.T, cudaMemcpyDeviceToHost, c.stream);
     }
     cudaStreamSynchronize(c.stream);
     if (tmp) c.release(tmp);
     if (tmp_ap) c.release(tmp_ap);
+    if (tmp_hl) c.release(tmp_hl);
     fp->users--;
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info)
@@ -1067,6 +1096,26 @@ dp_status dp_solve_point_corr(dp_ctx *ctx, dp_field field, double M, const dp_pr
     none.kind = DP_PROF_NONE;
     return solve_common(ctx, field, 1, &M, profile ? profile : &none, src, r, opts, cpp_out, 0,
                         nullptr, info, cap_out);
+}
+
+dp_status dp_solve_point_hl(dp_ctx *ctx, dp_field field, double M_h, const dp_profile *profile_h,
+                            double M_l, const dp_profile *profile_l, const int src[4], double r,
+                            const dp_solve_opts *opts, double *cpp_out, double *hl_out,
+                            dp_solve_info *info)
+{
+    if (!hl_out || !cpp_out) {
+        set_error("dp_solve_point_hl: NULL output");
+        return DP_ERR_INVALID_ARG;
+    }
+    dp_solve_opts o{};
+    if (opts) o = *opts;
+    o.batched = 1;  // both masses in one batch: the contraction reads both propagators
+    const double M[2] = {M_h, M_l};
+    dp_profile none{};
+    none.kind = DP_PROF_NONE;
+    const dp_profile prof[2] = {profile_h ? *profile_h : none, profile_l ? *profile_l : none};
+    return solve_common(ctx, field, 2, M, prof, src, r, &o, cpp_out, 0, nullptr, info, nullptr,
+                        hl_out);
 }
 
 dp_status dp_solve_point_dev(dp_ctx *ctx, dp_field field, int n_mass, const double *M,

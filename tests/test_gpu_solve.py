@@ -147,6 +147,27 @@ def test_cap_and_pcac_mass_match_oracle(ctx, inter, opts):
     assert np.abs(m_gpu - m_ref).max() < 1e-5 * np.abs(m_ref).max()
 
 
+def test_heavy_light_correlator_matches_oracle(ctx, inter):
+    """Heavy (cosh profile) and light (cosh-4d profile) quark from one source:
+    each C_PP and the complex heavy-light correlator against the oracle."""
+    dims, f, op = inter
+    T = dims[0]
+    src = (3, 1, 2, 0)
+    ch, Sh, _ = oracle.solve_point(op, 0.6, "cosh_t", 0.4, src, tol=1e-13)
+    cl, Sl, _ = oracle.solve_point(op, 0.1, "cosh_4d", 0.2, src, tol=1e-13)
+    ref = oracle.contract_hl(Sh, Sl, dims, src[0])
+    cpp, hl, infos = dp.dp_solve_point_hl(ctx, f, 0.6, ("cosh_t", 0.4), 0.1, ("cosh_4d", 0.2), src,
+                                          1e-12, MIXED, T=T)
+    assert all(i["status"] == 0 for i in infos)
+    assert slice_rel(cpp[0], ch, T // 2) < 1e-6 and slice_rel(cpp[1], cl, T // 2) < 1e-6
+    scale = np.abs(ref[: T // 2 + 1]).max()
+    assert np.abs(hl[: T // 2 + 1] - ref[: T // 2 + 1]).max() < 1e-6 * scale
+    # equal masses and profiles: the heavy-light correlator is C_PP
+    cpp2, hl2, _ = dp.dp_solve_point_hl(ctx, f, 0.6, ("cosh_t", 0.4), 0.6, ("cosh_t", 0.4), src,
+                                        1e-12, MIXED, T=T)
+    assert np.abs(hl2 - cpp2[0]).max() < 1e-12 * np.abs(cpp2[0]).max()
+
+
 def test_multi_mass_batch_equals_single_solves(ctx, inter):
     dims, f, op = inter
     T = dims[0]

@@ -55,3 +55,28 @@ def test_cap_gauge_invariant_and_profile_independent():
     scale = np.abs(a["cap"]).max()
     assert np.abs(b["cap"] - a["cap"]).max() < 1e-10 * scale
     assert np.abs(c["cap"] - a["cap"]).max() < 1e-10 * scale
+
+
+def test_heavy_light_reduces_to_cpp_and_is_gauge_invariant():
+    """Equal masses: the heavy-light correlator is C_PP (real); unequal
+    masses: gauge invariant, independent of each quark's profile."""
+    dims = (8, 4, 4, 4)
+    U = li.su3_links(dims, 0.4, seed=3)
+    G = li.random_gauge_transform(dims, seed=4)
+    src = (2, 1, 0, 3)
+    op = oracle.WilsonClover(U, dims, 1.7)
+    opg = oracle.WilsonClover(gauge_transform(U, G), dims, 1.7)
+    cpp, Sh, _ = oracle.solve_point(op, 0.5, "cosh_t", 0.4, src)
+    same = oracle.contract_hl(Sh, Sh, dims, src[0])
+    assert np.abs(same - cpp).max() < 1e-13 * np.abs(cpp).max()
+    _, Sl, _ = oracle.solve_point(op, 0.1, "none", 0.0, src)
+    _, Sl2, _ = oracle.solve_point(op, 0.1, "cosh_4d", 0.2, src)
+    _, Shg, _ = oracle.solve_point(opg, 0.5, "cosh_t", 0.4, src)
+    _, Slg, _ = oracle.solve_point(opg, 0.1, "none", 0.0, src)
+    hl = oracle.contract_hl(Sh, Sl, dims, src[0])
+    scale = np.abs(hl).max()
+    assert np.abs(oracle.contract_hl(Sh, Sl2, dims, src[0]) - hl).max() < 1e-10 * scale
+    assert np.abs(oracle.contract_hl(Shg, Slg, dims, src[0]) - hl).max() < 1e-10 * scale
+    # a genuinely different correlator from either C_PP
+    cl, _, _ = oracle.solve_point(op, 0.1, "none", 0.0, src)
+    assert np.abs(hl.real - cpp).max() > 1e-3 * scale and np.abs(hl.real - cl).max() > 1e-3 * scale
