@@ -139,8 +139,11 @@ typedef struct {
 } dp_solve_info;
 
 /* Optional device allocator.  alloc returns device memory of >= bytes, 256-byte
- * aligned, usable on `stream`; free releases it.  NULL hooks: cudaMallocAsync
- * / cudaFreeAsync on the context stream. */
+ * aligned, usable on `stream`; free releases it.  NULL hooks: stream-ordered
+ * allocation from a memory pool the context owns, which keeps memory freed
+ * inside the context reserved for reuse (a solve's work vectors are
+ * allocated and freed per call: re-mapping gigabytes each time would leave
+ * the GPU idle) until dp_trim or dp_destroy. */
 typedef struct {
     void *(*alloc)(size_t bytes, void *stream, void *user);
     void (*free)(void *ptr, size_t bytes, void *stream, void *user);
@@ -154,8 +157,12 @@ typedef struct {
 dp_status dp_create(dp_ctx **out, int device, const dp_alloc_hooks *hooks, void *stream);
 void dp_destroy(dp_ctx *ctx);
 const char *dp_last_error(void);
-/* Device memory the library holds for this context, in bytes. */
+/* Device memory the library holds for this context, in bytes (memory the
+ * context's pool keeps reserved after a free is not counted). */
 size_t dp_device_bytes(dp_ctx *ctx);
+/* Return the memory the context's pool keeps reserved to the device (waits
+ * for the context stream first).  No effect with allocation hooks. */
+dp_status dp_trim(dp_ctx *ctx);
 
 /* ---- gauge fields (Sec. I: D[U]; Sec. II: O(a)-improved operator) -------- */
 
@@ -316,9 +323,10 @@ dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profi
  * selects how neighbour spinors and links reach the thread: 0 direct loads,
  * 2-3 staged through shared memory with that many of the 8 directions in
  * flight, 4 staged (2 in flight) by one persistent wave of blocks whose
- * threads walk several sites (staging needs FP32 or 16-bit 12-real links, 2
- * RHS per thread and 64, 96 or 128 threads per block), -1 the tuned or
- * default choice.
+ * threads walk several sites (staging needs 64, 96 or 128 threads per
+ * block), 5 direct loads with an L1 prefetch 2 directions ahead (all of
+ * 2-5 need FP32 or 16-bit 12-real links and 2 RHS per thread), -1 the tuned
+ * or default choice.
  * FP32 needs nrhs even.  iters launches back to back; if ms_out is non-NULL
  * it receives the average launch time measured with CUDA events on the
  * context stream. */

@@ -23,7 +23,7 @@ from . import build as _build
 
 __all__ = [
     "DpError", "load", "lib_path",
-    "dp_create", "dp_destroy", "dp_last_error", "dp_device_bytes",
+    "dp_create", "dp_destroy", "dp_last_error", "dp_device_bytes", "dp_trim",
     "dp_field_load", "dp_field_set_csw", "dp_field_free",
     "dp_solve_point", "dp_solve_point_multi", "dp_solve_point_dev",
     "dp_solve_point_corr", "dp_solve_point_hl", "pcac_mass", "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
@@ -109,6 +109,7 @@ def load(build_if_missing=False):
         "dp_destroy": ([vp], None),
         "dp_last_error": ([], C.c_char_p),
         "dp_device_bytes": ([vp], sz),
+        "dp_trim": ([vp], ip),
         "dp_field_load": ([vp, vp, P(C.c_int * 4), ip, P(up)], ip),
         "dp_field_set_csw": ([vp, up, dp], ip),
         "dp_field_free": ([vp, up], ip),
@@ -220,6 +221,11 @@ def dp_destroy(ctx):
 
 def dp_device_bytes(ctx):
     return int(load().dp_device_bytes(ctx))
+
+
+def dp_trim(ctx):
+    """Return the device memory the context's pool keeps reserved."""
+    _check(load().dp_trim(ctx))
 
 
 # ---- fields -----------------------------------------------------------------

@@ -37,7 +37,7 @@ void *Ctx::alloc(size_t n)
     void *p = nullptr;
     if (has_hooks) {
         p = hooks.alloc(n, (void *)stream, hooks.user);
-    } else if (cudaMallocAsync(&p, n, stream) != cudaSuccess) {
+    } else if (cudaMallocFromPoolAsync(&p, n, pool, stream) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
     }
@@ -448,6 +448,21 @@ dp_status dp_create(dp_ctx **out, int device, const dp_alloc_hooks *hooks, void 
         c.hooks = *hooks;
         c.has_hooks = true;
     }
+    if (!hooks) {
+        cudaMemPoolProps pp{};
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.location.type = cudaMemLocationTypeDevice;
+        pp.location.id = device;
+        uint64_t keep = ~0ull;
+        if (cudaMemPoolCreate(&c.pool, &pp) != cudaSuccess ||
+            cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaGetLastError();
+            if (c.pool) cudaMemPoolDestroy(c.pool);
+            delete ctx;
+            set_error("cannot create the device memory pool");
+            return DP_ERR_CUDA;
+        }
+    }
     if (stream) {
         c.stream = (cudaStream_t)stream;
     } else {
@@ -495,7 +510,19 @@ void dp_destroy(dp_ctx *ctx)
     for (auto e : c.event_pool) cudaEventDestroy(e);
     if (c.h_nactive) cudaFreeHost(c.h_nactive);
     if (c.own_stream) cudaStreamDestroy(c.stream);
+    if (c.pool) cudaMemPoolDestroy(c.pool);
     delete ctx;
+}
+
+dp_status dp_trim(dp_ctx *ctx)
+{
+    CTX_CHECK(ctx);
+    Ctx &c = ctx->c;
+    if (!c.pool) return DP_OK;
+    CUDA_OK(cudaSetDevice(c.device));
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    CUDA_OK(cudaMemPoolTrimTo(c.pool, 0));
+    return DP_OK;
 }
 
 size_t dp_device_bytes(dp_ctx *ctx)
@@ -785,7 +812,7 @@ dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile 
     Field &f = *fp;
     if (!in || !out || nrhs < 1 || nrhs > kMaxRhs || iters < 1 || (out_parity & ~1) ||
         prec < DP_PREC_FP64 || prec > DP_PREC_MIXED_BF16 ||
-        rhs_per_thread < 0 || stages < -1 || stages > 4 ||
+        rhs_per_thread < 0 || stages < -1 || stages > 5 ||
         (block_threads != 0 && (block_threads < 32 || block_threads > 256 || block_threads % 32))) {
         set_error("dp_dslash_dev: invalid argument");
         return DP_ERR_INVALID_ARG;
@@ -889,11 +916,12 @@ dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int
     }
     cudaMemsetAsync(in, 0, vb, c.stream);
     // candidates: four block sizes x RHS per thread (FP64: 1; FP32: one or
-    // two RHS pairs) x shared-memory staging (FP32 one pair per thread: none,
-    // 2-3 directions in flight, or 2 in a persistent wave)
+    // two RHS pairs) x how neighbour data arrives (FP32 one pair per thread:
+    // direct, shared-memory staging 2-3 directions ahead or in a persistent
+    // wave, or direct with an L1 prefetch 2 directions ahead)
     const int blocks[] = {64, 96, 128, 192, 256};
     const int rpts[] = {1, 2, 4};
-    const int stage_opts[] = {0, 2, 3, 4};
+    const int stage_opts[] = {0, 2, 3, 4, 5};
     Shape best;
     float bms = 1e30f;
     dp_status st = DP_OK;

@@ -92,6 +92,7 @@ struct Ctx {
     bool own_stream = false;
     dp_alloc_hooks hooks{};
     bool has_hooks = false;
+    cudaMemPool_t pool = nullptr;  // without hooks: stream-ordered pool that keeps freed memory
 
     std::mutex mu;  // fields, allocations, tuner
     std::map<uint64_t, std::shared_ptr<Field>> fields;

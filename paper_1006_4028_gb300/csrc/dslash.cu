@@ -548,6 +548,97 @@ __global__ void __launch_bounds__(BD) k_dslash32s(const DslashParams p)
     finish32<EPI, 1>(p, acc, act, s, q0, grp, cs);
 }
 
+// ---- direct loads with an L1 prefetch DIST (= 2) directions ahead: the neighbour
+// spinor's 12 components and the link of direction d + DIST are requested
+// into L1 (no registers, no shared memory) while direction d is loaded and
+// computed from L1.
+#define DP_PF "prefetch.global.L1 [a];\n\tadd.u64 a, a, %1;\n\t"
+__device__ __forceinline__ void prefetch12(const void *src, long long stride_bytes)
+{
+    asm volatile("{\n\t.reg .u64 a;\n\tmov.u64 a, %0;\n\t" DP_PF DP_PF DP_PF DP_PF DP_PF DP_PF DP_PF
+                 DP_PF DP_PF DP_PF DP_PF DP_PF "}\n" ::"l"(src), "l"(stride_bytes));
+}
+__device__ __forceinline__ void prefetch3(const void *src, long long stride_bytes)
+{
+    asm volatile("{\n\t.reg .u64 a;\n\tmov.u64 a, %0;\n\t" DP_PF DP_PF DP_PF "}\n" ::"l"(src),
+                 "l"(stride_bytes));
+}
+#undef DP_PF
+
+template <int LF>
+__device__ __forceinline__ void prefetch_dir(const float4 *nbp, long long cs, const void *lk,
+                                             long long Vh, long long lsite, int mu)
+{
+    prefetch12(nbp, cs * 16);
+    if constexpr (LF == LINK_F32_12)
+        prefetch3(static_cast<const float4 *>(lk) + (long long)mu * 3 * Vh + lsite, Vh * 16);
+    else
+        prefetch3(static_cast<const uint2 *>(lk) + (long long)mu * 3 * Vh + lsite, Vh * 8);
+}
+
+template <int LF, int DIST, int D>
+__device__ __forceinline__ void pf_step(C2 (&acc)[1][12], const bool (&act)[1], const float4 *in, int P,
+                                        long long cs, const Nbr &nb, long long s, const void *lown,
+                                        const void *loth, long long Vh, const float *ht, int Lmax)
+{
+    if constexpr (D + DIST < 8) {
+        constexpr int E = D + DIST, ME = E / 2;
+        prefetch_dir<LF>(in + (long long)((E & 1) ? nb.b[ME] : nb.f[ME]) * P, cs, (E & 1) ? loth : lown, Vh,
+                         (E & 1) ? (long long)nb.b[ME] : s, ME);
+    }
+    constexpr int MU = D / 2;
+    const int crd = MU == 0 ? nb.t : MU == 1 ? nb.x : MU == 2 ? nb.y : nb.z;
+    if (D & 1)
+        hop_pair<LF, MU, +1, 1>(acc, in + (long long)nb.b[MU] * P, cs, loth, Vh, nb.b[MU],
+                                ht[D * Lmax + crd], act);
+    else
+        hop_pair<LF, MU, -1, 1>(acc, in + (long long)nb.f[MU] * P, cs, lown, Vh, s, ht[D * Lmax + crd], act);
+}
+
+template <int LF, int EPI, int DIST>
+__global__ void __launch_bounds__(256) k_dslash32f(const DslashParams p)
+{
+    const Geom &g = p.g;
+    const int P = p.nrhs / 2;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long s = gid / P;
+    const int q0 = (int)(gid - s * P);
+    if (s >= g.Vh) return;
+    bool act[1];
+    act[0] = !p.active || p.active[2 * q0 * p.active_stride] || p.active[(2 * q0 + 1) * p.active_stride];
+    if (!act[0]) return;
+    const Nbr nb = neighbours(g, s, p.parity);
+    const long long cs = g.Vh * P;
+    const float4 *in = static_cast<const float4 *>(p.in) + q0;
+    const int grp = p.grp_of[2 * q0];
+    const float *ht = static_cast<const float *>(p.hop) + (long long)grp * 8 * g.Lmax;
+    const void *lown = p.links[p.parity], *loth = p.links[1 - p.parity];
+    const long long Vh = g.Vh;
+#pragma unroll
+    for (int d = 0; d < DIST; d++) {
+        const int mu = d / 2;
+        prefetch_dir<LF>(in + (long long)((d & 1) ? nb.b[mu] : nb.f[mu]) * P, cs, (d & 1) ? loth : lown, Vh,
+                         (d & 1) ? (long long)nb.b[mu] : s, mu);
+    }
+    {
+        const float4 *cl = static_cast<const float4 *>(p.clov[grp]) + s;
+#pragma unroll 1
+        for (int k = 0; k < 18; k++) prefetch_l1(cl + k * Vh);
+    }
+    C2 acc[1][12];
+#pragma unroll
+    for (int j = 0; j < 12; j++) acc[0][j] = {0ull, 0ull};
+    pf_step<LF, DIST, 0>(acc, act, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    pf_step<LF, DIST, 1>(acc, act, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    pf_step<LF, DIST, 2>(acc, act, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    pf_step<LF, DIST, 3>(acc, act, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    pf_step<LF, DIST, 4>(acc, act, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    pf_step<LF, DIST, 5>(acc, act, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    pf_step<LF, DIST, 6>(acc, act, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    pf_step<LF, DIST, 7>(acc, act, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    finish32<EPI, 1>(p, acc, act, s, q0, grp, cs);
+}
+
 // ---- persistent staged variant: one wave of blocks, each thread walks the
 // (site, pair) items w, w + G, w + 2G, ... (G = threads in the grid) with two
 // stages; the next item's first two directions are copied while the current
@@ -752,11 +843,24 @@ cudaError_t launch32s(const DslashParams &p, int block, int stages, cudaStream_t
     }
 }
 
+template <int LF, int DIST>
+cudaError_t launch32f(const DslashParams &p, int epi, int block, cudaStream_t st)
+{
+    const long long threads = p.g.Vh * (p.nrhs / 2);
+    const unsigned grid = (unsigned)((threads + block - 1) / block);
+    if (epi == EPI_AINV)
+        k_dslash32f<LF, EPI_AINV, DIST><<<grid, block, 0, st>>>(p);
+    else
+        k_dslash32f<LF, EPI_XMY_AINV, DIST><<<grid, block, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <int LF>
 cudaError_t launch32s_epi(const DslashParams &p, int epi, int block, int stages, int rpt,
                           cudaStream_t st)
 {
     (void)rpt;
+    if (stages == 5) return launch32f<LF, 2>(p, epi, block, st);
     if (epi == EPI_AINV) return launch32s<LF, EPI_AINV>(p, block, stages, st);
     return launch32s<LF, EPI_XMY_AINV>(p, block, stages, st);
 }
@@ -775,6 +879,10 @@ bool dslash_rpt_ok(int nrhs, int rpt, int prec, int epi)
 
 bool dslash_staged_ok(int prec, int link_fmt, int epi, int rpt, int stages, int block)
 {
+    if (prec == 1 && rpt == 2 && stages == 5 && block >= 32 && block <= 256 &&
+        block % 32 == 0 && (epi == EPI_AINV || epi == EPI_XMY_AINV) &&
+        (link_fmt == LINK_F32_12 || link_fmt == LINK_H16_12 || link_fmt == LINK_B16_12))
+        return true;
     return prec == 1 && rpt == 2 && stages >= 2 && stages <= 4 &&
            (block == 64 || block == 96 || block == 128) &&
            (epi == EPI_AINV || epi == EPI_XMY_AINV) &&

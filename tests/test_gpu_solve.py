@@ -249,3 +249,18 @@ def test_device_output_and_timing(ctx, inter):
                                          (0, 0, 0, 0), 1e-10, MIXED, T=T)
     np.testing.assert_array_equal(out.cpu().numpy().reshape(2, T), host)
     assert all(i["status"] == 0 for i in infos)
+
+
+def test_pool_keeps_memory_and_trim(ctx, inter):
+    """The context's pool reuses a solve's freed work vectors; results do not
+    depend on whether the memory was trimmed in between (deterministic)."""
+    dims, f, op = inter
+    held = dp.dp_device_bytes(ctx)
+    a, _, ia = dp.dp_solve_point(ctx, f, 0.5, ("cosh_t", 0.4), (0, 0, 0, 0), 1e-10, MIXED, T=dims[0])
+    assert dp.dp_device_bytes(ctx) <= held + (1 << 30)  # work vectors returned after the call
+    dp.dp_trim(ctx)
+    b, _, ib = dp.dp_solve_point(ctx, f, 0.5, ("cosh_t", 0.4), (0, 0, 0, 0), 1e-10, MIXED, T=dims[0])
+    c, _, _ = dp.dp_solve_point(ctx, f, 0.5, ("cosh_t", 0.4), (0, 0, 0, 0), 1e-10, MIXED, T=dims[0])
+    assert ia["status"] == 0 and ib["status"] == 0
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(b, c)
