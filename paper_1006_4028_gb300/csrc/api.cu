@@ -474,7 +474,7 @@ dp_status dp_create(dp_ctx **out, int device, const dp_alloc_hooks *hooks, void 
         c.own_stream = true;
     }
     c.bc.blocks = 2048;
-    c.bc.partials = (double *)c.alloc((size_t)c.bc.blocks * kMaxRhs * 4 * sizeof(double));
+    c.bc.partials = (double *)c.alloc((size_t)c.bc.blocks * kMaxRhs * kRedWidth * sizeof(double));
     c.bc.counter = (unsigned int *)c.alloc(256);
     c.bc.n_active = (int *)c.alloc(256);
     if (!c.bc.partials || !c.bc.counter || !c.bc.n_active ||

@@ -193,10 +193,13 @@ struct RhsState {        // per RHS, device resident
     int iters;
     int status;           // 0 running, 1 converged, 2 breakdown, 3 non-finite, 4 max-iter
     int fresh;            // 1: x = 0, next residual call sets |b|^2 and tol2
+    int brk;              // fused FP32 BiCGStab: breakdown found by the omega reduction
 };
 
+constexpr int kRedWidth = 8;  // values per RHS in a block's reduction partials
+
 struct BlasCtx {
-    double *partials;     // [max_blocks][kMaxRhs][4]
+    double *partials;     // [max_blocks][kMaxRhs][kRedWidth]
     unsigned int *counter;
     int *n_active;        // device counter of active RHS
     int blocks;
@@ -219,7 +222,17 @@ cudaError_t blas_bicg_update(BlasCtx &bc, int prec, void *x, void *r, const void
                              int nrhs, RhsState *st, int max_iter, cudaStream_t s);
 // FP32 inner solver on the paired layout (blas32.cu); nrhs even
 cudaError_t blas32_init(BlasCtx &bc, const void *b, void *r, void *rh, long long Vh, int nrhs,
-                        RhsState *st, cudaStream_t s);
+                        RhsState *st, cudaStream_t s, void *p = nullptr);
+// BiCGStab with the p update fused into the x, r update (FP32 inner solver):
+// init r = rhat = p = b (x = 0); per iteration v = Mhat p, alpha, s = r -
+// alpha v, t = Mhat s, then omega_rho (omega, rho' = <rhat,s> - omega
+// <rhat,t>, beta) and update_p (x += alpha p + omega s, r = s - omega t,
+// p = r + beta (p - omega v), |r|^2 decides convergence)
+cudaError_t blas32_omega_rho(BlasCtx &bc, const void *t, const void *sv, const void *rh,
+                             long long Vh, int nrhs, RhsState *st, cudaStream_t s);
+cudaError_t blas32_update_p(BlasCtx &bc, void *x, void *r, void *p, const void *sv, const void *t,
+                            const void *v, long long Vh, int nrhs, RhsState *st, int max_iter,
+                            cudaStream_t s);
 cudaError_t blas32_p(BlasCtx &bc, const void *r, void *p, const void *v, long long Vh, int nrhs,
                      const RhsState *st, int first, cudaStream_t s);
 cudaError_t blas32_alpha(BlasCtx &bc, const void *rh, const void *v, long long Vh, int nrhs,

@@ -135,6 +135,56 @@ __device__ __forceinline__ void finish_update(RhsState &S, double re, double im,
     }
 }
 
+// The FP32 inner BiCGStab with the p update fused into the x, r update:
+// omega and the next rho come from one reduction, rho' = <rhat, r'> =
+// <rhat, s> - omega <rhat, t> (r' = s - omega t), so beta is known before the
+// update pass.  A breakdown found here (omega or rho' zero) is reported by
+// the update's finisher unless that pass converges.
+__device__ __forceinline__ void finish_omega_rho(RhsState &S, double ts_re, double ts_im, double tt,
+                                                 double rs_re, double rs_im, double rt_re,
+                                                 double rt_im)
+{
+    if (!S.active) return;
+    if (!(isfinite(ts_re) && isfinite(ts_im) && isfinite(tt) && isfinite(rs_re) && isfinite(rs_im) &&
+          isfinite(rt_re) && isfinite(rt_im))) {
+        S.status = 3;
+        S.active = 0;
+        return;
+    }
+    S.omega = tt > 0 ? make_double2(ts_re / tt, ts_im / tt) : make_double2(0.0, 0.0);
+    const double2 wrt = zmul(S.omega, make_double2(rt_re, rt_im));
+    const double2 rho_new = make_double2(rs_re - wrt.x, rs_im - wrt.y);
+    if ((S.omega.x == 0.0 && S.omega.y == 0.0) || (rho_new.x == 0.0 && rho_new.y == 0.0)) {
+        S.brk = 1;
+        S.beta = make_double2(0.0, 0.0);
+    } else {
+        S.beta = zmul(zdiv(rho_new, S.rho), zdiv(S.alpha, S.omega));
+        S.rho = rho_new;
+    }
+}
+
+// iteration count, convergence, cap, and a breakdown flagged by
+// finish_omega_rho
+__device__ __forceinline__ void finish_update_rr(RhsState &S, double rr, int max_iter)
+{
+    if (!S.active) return;
+    S.iters++;
+    S.rr = rr;
+    if (!isfinite(rr)) {
+        S.status = 3;
+        S.active = 0;
+    } else if (S.rr <= S.tol2) {
+        S.status = 1;
+        S.active = 0;
+    } else if (S.iters >= max_iter) {
+        S.status = 4;
+        S.active = 0;
+    } else if (S.brk) {
+        S.status = 2;
+        S.active = 0;
+    }
+}
+
 // start of an inner solve: rho = |r|^2, tol2 (tol^2 on entry) *= |r|^2
 __device__ __forceinline__ void finish_init(RhsState &S, double bb)
 {
@@ -147,6 +197,7 @@ __device__ __forceinline__ void finish_init(RhsState &S, double bb)
     S.omega = make_double2(1.0, 0.0);
     S.beta = make_double2(0.0, 0.0);
     S.iters = 0;
+    S.brk = 0;
     if (!isfinite(bb)) {
         S.status = 3;
         S.active = 0;
@@ -209,30 +260,52 @@ __device__ __forceinline__ void finish_cg_update(RhsState &S, double rr, int max
 
 // Block + grid reduction of NV doubles per RHS for LANES RHS per thread
 // (v[L*NV + k] belongs to RHS LANES*unit + L).  Returns true in exactly one
-// thread per unit (lane 0 of the last block), with the totals in v.
+// thread per unit (lane 0 of the last block), with the totals in v.  The
+// block tree runs kRedChunk values at a time through shared memory; each
+// value's summation order is the same fixed tree whatever NV is.
+constexpr int kRedChunk = 4;
+
+template <int W>
+__device__ __forceinline__ void block_tree(double v[W], double *sh, const Cfg c, int t, int units,
+                                           int lane)
+{
+#pragma unroll
+    for (int k0 = 0; k0 < W; k0 += kRedChunk) {
+#pragma unroll
+        for (int k = 0; k < kRedChunk; k++)
+            if (k0 + k < W) sh[t * kRedChunk + k] = v[k0 + k];
+        __syncthreads();
+        for (int w = c.lanes / 2; w > 0; w >>= 1) {
+            if (lane < w)
+#pragma unroll
+                for (int k = 0; k < kRedChunk; k++)
+                    if (k0 + k < W) sh[t * kRedChunk + k] += sh[(t + w * units) * kRedChunk + k];
+            __syncthreads();
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < kRedChunk; k++)
+                if (k0 + k < W) v[k0 + k] = sh[t * kRedChunk + k];
+        __syncthreads();
+    }
+}
+
 template <int NV, int LANES>
 __device__ bool reduce_last(double v[LANES * NV], const Cfg c, double *partials,
                             unsigned int *counter, int units)
 {
+    static_assert(NV <= kRedWidth, "per-RHS partials hold kRedWidth values");
     constexpr int W = LANES * NV;
-    __shared__ double sh[kMaxBlock * W];
+    __shared__ double sh[kMaxBlock * kRedChunk];
     __shared__ bool last;
     const int t = threadIdx.x, u = t % units, lane = t / units;
-#pragma unroll
-    for (int k = 0; k < W; k++) sh[t * W + k] = v[k];
-    __syncthreads();
-    for (int w = c.lanes / 2; w > 0; w >>= 1) {
-        if (lane < w)
-#pragma unroll
-            for (int k = 0; k < W; k++) sh[t * W + k] += sh[(t + w * units) * W + k];
-        __syncthreads();
-    }
+    block_tree<W>(v, sh, c, t, units, lane);
     if (lane == 0)
 #pragma unroll
         for (int L = 0; L < LANES; L++)
 #pragma unroll
             for (int k = 0; k < NV; k++)
-                partials[((long long)blockIdx.x * kMaxRhs + LANES * u + L) * 4 + k] = sh[t * W + L * NV + k];
+                partials[((long long)blockIdx.x * kMaxRhs + LANES * u + L) * kRedWidth + k] = v[L * NV + k];
     __threadfence();
     __syncthreads();
     if (t == 0) last = (atomicAdd(counter, 1u) == (unsigned)(gridDim.x - 1));
@@ -248,20 +321,12 @@ __device__ bool reduce_last(double v[LANES * NV], const Cfg c, double *partials,
         for (int L = 0; L < LANES; L++)
 #pragma unroll
             for (int k = 0; k < NV; k++)
-                acc[L * NV + k] += __ldcg(partials + ((long long)b * kMaxRhs + LANES * u + L) * 4 + k);
-#pragma unroll
-    for (int k = 0; k < W; k++) sh[t * W + k] = acc[k];
-    __syncthreads();
-    for (int w = c.lanes / 2; w > 0; w >>= 1) {
-        if (lane < w)
-#pragma unroll
-            for (int k = 0; k < W; k++) sh[t * W + k] += sh[(t + w * units) * W + k];
-        __syncthreads();
-    }
+                acc[L * NV + k] += __ldcg(partials + ((long long)b * kMaxRhs + LANES * u + L) * kRedWidth + k);
+    block_tree<W>(acc, sh, c, t, units, lane);
     if (t == 0) *counter = 0u;
     if (lane != 0) return false;
 #pragma unroll
-    for (int k = 0; k < W; k++) v[k] = sh[t * W + k];
+    for (int k = 0; k < W; k++) v[k] = acc[k];
     return true;
 }
 

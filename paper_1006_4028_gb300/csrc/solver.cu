@@ -41,6 +41,16 @@ namespace dp {
 
 namespace {
 
+// stream time of a scope under the context's kernel timing (a no-op when
+// timing is off or while a graph is captured)
+struct Timed {
+    Ctx *c;
+    const char *name;
+    cudaEvent_t ev;
+    Timed(Ctx *c_, const char *n) : c(c_), name(n) { c->time_begin(name, &ev); }
+    ~Timed() { c->time_end(name, ev); }
+};
+
 dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void *out,
                  const void *x, const int *mask, int mask_stride)
 {
@@ -310,6 +320,7 @@ dp_status Batch::upload_mask(const std::vector<int> &m)
 
 dp_status Batch::admit(Job *j)
 {
+    Timed tm(c, "admit");
     const Geom &g = f->g;
     const int Lm = g.Lmax;
     int tab = -1, s0 = -1;
@@ -458,7 +469,16 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
     BlasCtx &bc = c->bc;
     const int pr = opin.pr;
     const long long Vh = f->g.Vh;
-    CK(blas_bicg_init(bc, pr, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, c->stream));
+    // FP32: the p update rides in the x, r update pass (blas32_update_p)
+    const bool fused = pr == 1;
+    if (fused) {
+        CK(cudaMemsetAsync(in.x, 0, vin, c->stream));
+        CK(cudaMemsetAsync(in.v, 0, vin, c->stream));
+        CK(blas32_init(bc, in.rh, in.r, in.rh, Vh, n, inner, c->stream, in.p));
+        CK(blas_count_active(bc, inner, n, c->stream));
+    } else {
+        CK(blas_bicg_init(bc, pr, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, c->stream));
+    }
     c->launches += 2;
     CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -467,16 +487,58 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
         *iters_done = 0;
         return DP_OK;
     }
-    auto body = [&](int first) -> dp_status {
-        CK(blas_bicg_p(bc, pr, in.r, in.p, in.v, Vh, n, inner, first, c->stream));
+    auto body_fused = [&]() -> dp_status {
         dp_status s = apply_mhat(c, opin, sp, in.p, in.v, in.to, inner);
         if (s != DP_OK) return s;
-        CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, c->stream));
-        CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, c->stream));
+        {
+            Timed tm(c, "blas_inner");
+            CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, c->stream));
+        }
+        {
+            Timed tm(c, "blas_inner");
+            CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, c->stream));
+        }
         s = apply_mhat(c, opin, sp, in.s, in.t, in.to, inner);
         if (s != DP_OK) return s;
-        CK(blas_bicg_omega(bc, pr, in.t, in.s, Vh, n, inner, c->stream));
-        CK(blas_bicg_update(bc, pr, in.x, in.r, in.p, in.s, in.t, in.rh, Vh, n, inner, max_iter, c->stream));
+        {
+            Timed tm(c, "blas_inner");
+            CK(blas32_omega_rho(bc, in.t, in.s, in.rh, Vh, n, inner, c->stream));
+        }
+        {
+            Timed tm(c, "blas_inner");
+            CK(blas32_update_p(bc, in.x, in.r, in.p, in.s, in.t, in.v, Vh, n, inner, max_iter,
+                               c->stream));
+        }
+        c->launches += 5;
+        return DP_OK;
+    };
+    auto body = [&](int first) -> dp_status {
+        if (fused) return body_fused();
+        {
+            Timed tm(c, "blas_inner");
+            CK(blas_bicg_p(bc, pr, in.r, in.p, in.v, Vh, n, inner, first, c->stream));
+        }
+        dp_status s = apply_mhat(c, opin, sp, in.p, in.v, in.to, inner);
+        if (s != DP_OK) return s;
+        {
+            Timed tm(c, "blas_inner");
+            CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, c->stream));
+        }
+        {
+            Timed tm(c, "blas_inner");
+            CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, c->stream));
+        }
+        s = apply_mhat(c, opin, sp, in.s, in.t, in.to, inner);
+        if (s != DP_OK) return s;
+        {
+            Timed tm(c, "blas_inner");
+            CK(blas_bicg_omega(bc, pr, in.t, in.s, Vh, n, inner, c->stream));
+        }
+        {
+            Timed tm(c, "blas_inner");
+            CK(blas_bicg_update(bc, pr, in.x, in.r, in.p, in.s, in.t, in.rh, Vh, n, inner, max_iter,
+                                c->stream));
+        }
         c->launches += 6;
         return DP_OK;
     };
@@ -500,7 +562,7 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
                 graph_max_iter = max_iter;
             }
             CK(cudaGraphLaunch(graph, c->stream));
-            c->launches += 10;
+            c->launches += fused ? 9 : 10;
         }
         it++;
         if (it >= max_iter) break;
@@ -713,6 +775,7 @@ dp_status Batch::cgne(int max_iter, int *iters_done)
 
 dp_status Batch::round()
 {
+    Timed tm(c, "round");
     const long long Vh = f->g.Vh;
     const int max_outer = 200;
     // per-RHS stop rules on the host: stagnation of the true residual, round
@@ -738,11 +801,14 @@ dp_status Batch::round()
     if (nact == 0) return DP_OK;
     for (int k = 0; k < n; k++)
         if (slot_job[k] && hs[k].active) slot_outer[k]++;
-    CK(blas_inner_setup(outer, inner, n, opts.inner_tol, 0.0, c->stream));
-    if (mixed)
-        CK(blas_to_f32_scaled(r64, (float4 *)in.rh, Vh, n, outer, c->stream));
-    else
-        CK(blas_scale64(r64, (double2 *)in.rh, Vh, n, outer, c->stream));
+    {
+        Timed tm(c, "outer_blas");
+        CK(blas_inner_setup(outer, inner, n, opts.inner_tol, 0.0, c->stream));
+        if (mixed)
+            CK(blas_to_f32_scaled(r64, (float4 *)in.rh, Vh, n, outer, c->stream));
+        else
+            CK(blas_scale64(r64, (double2 *)in.rh, Vh, n, outer, c->stream));
+    }
     c->launches += 2;
     // inner budget of this round
     int budget = round_iters > 0 ? round_iters : opts.max_iter;
@@ -764,21 +830,28 @@ dp_status Batch::round()
         }
     }
     if (bad) CK(cudaMemcpyAsync(outer, hs.data(), sizeof(RhsState) * n, cudaMemcpyHostToDevice, c->stream));
-    if (mixed)
-        CK(blas_acc_f32(x, (const float4 *)in.x, Vh, n, outer, c->stream));
-    else
-        CK(blas_acc64(x, (const double2 *)in.x, Vh, n, outer, c->stream));
+    {
+        Timed tm(c, "outer_blas");
+        if (mixed)
+            CK(blas_acc_f32(x, (const float4 *)in.x, Vh, n, outer, c->stream));
+        else
+            CK(blas_acc64(x, (const double2 *)in.x, Vh, n, outer, c->stream));
+    }
     // t64 keeps A_qq^-1 D_qp x of this (final, once converged) x: the
     // reconstruction of the other parity reuses it
     s = outer_mhat();
     if (s != DP_OK) return s;
-    CK(blas_residual64(c->bc, bh, y64, r64, Vh, n, outer, nullptr, c->stream));
+    {
+        Timed tm(c, "outer_blas");
+        CK(blas_residual64(c->bc, bh, y64, r64, Vh, n, outer, nullptr, c->stream));
+    }
     c->launches += 3;
     return DP_OK;
 }
 
 dp_status Batch::harvest(std::vector<Job *> &finished)
 {
+    Timed tm(c, "harvest");
     const Geom &g = f->g;
     const long long Vh = g.Vh;
     CK(cudaMemcpyAsync(hs.data(), outer, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
