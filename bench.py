@@ -745,6 +745,22 @@ def main():
                               buf_out.data_ptr(), 12, 0, 0, 20)
     del buf_in, buf_out
     iso_gbs = Vh * b_ainv / (iso_ms / 1e3) / 1e9
+    # the same kernel against the FP32 ALUs: n*(1320 + 96) flop per half-site
+    # for the hops with their profile factors, ~504 per RHS for the fused
+    # A^-1, ~24 per RHS for x - ... in the second Schur launch; peak = SMs x
+    # 128 FP32 lanes x 2 flop x the maximum SM clock (a packed f32x2 FMA
+    # issues two of those lanes' work, it does not add lanes)
+    flop_ainv = n * (1320 + 96 + 504)
+    flop_per_launch = Vh * (flop_ainv + flop_ainv + n * 24) / 2
+    props = torch.cuda.get_device_properties(local)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    alu = {"bound": "alu", "achieved": flop_per_launch / (avg_ms / 1e3) / 1e12,
+           "peak": fp32_peak, "unit": "TFLOP/s",
+           "frac": flop_per_launch / (avg_ms / 1e3) / 1e12 / fp32_peak,
+           "flop_per_launch": flop_per_launch,
+           "peak_source": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (maximum SM clock)"
+                          % (props.multi_processor_count, sm_max)}
 
     # DRAM bytes of one launch of the tuned kernel, from an ncu capture of this
     # workload (dram__bytes_read.sum + dram__bytes_write.sum, A^-1 D launch,
@@ -791,7 +807,8 @@ def main():
                      "launches": d32_n, "peak_source": peak_src,
                      "measured_in": kernel_timing_region,
                      "isolated_all_active": {"avg_launch_ms": iso_ms, "achieved": iso_gbs,
-                                             "frac": iso_gbs / hbm_peak}},
+                                             "frac": iso_gbs / hbm_peak},
+                     "fp32_alu": alu},
         "kernel_time_share": {"dslash_fp32": d32_ms / ms_instr, "dslash_fp64": d64_ms / ms_instr},
         "clocks": clocks,
         "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -28,9 +28,11 @@ where the hop factor is the ratio of the two sites' profile values times the
 sign: this is eq. (redeftbc).
 
 Parity status: every function here is pinned by the CPU tests in
-``tests/test_oracle_*.py`` (closed forms, dense LU, symmetries) except
-``effective_mass`` (a definition the paper does not write out), which is
-exercised only through its use on pinned correlators.
+``tests/test_oracle_*.py`` (closed forms, dense LU, symmetries).  The
+effective masses and the correlator fit (the paper plots effective masses
+without writing a definition out; the log-ratio and cosh readings) are
+pinned to exact one- and two-sided exponentials and to the free-theory pole
+2 ln(1+M) of the pseudoscalar at zero momentum.
 """
 from __future__ import annotations
 
@@ -397,6 +399,65 @@ def effective_mass(cpp):
     without writing it out)."""
     c = np.asarray(cpp)
     return np.log(c[:-1] / c[1:])
+
+
+def _log_cosh(x):
+    x = np.abs(x)
+    return x + np.log1p(np.exp(-2.0 * x)) - np.log(2.0)
+
+
+def effective_mass_cosh(cpp):
+    """Cosh-form effective mass on a lattice with two-sided decay: m(y0) > 0
+    with C(y0)/C(y0+1) = cosh[m (T/2 - y0)] / cosh[m (T/2 - y0 - 1)] (a state
+    propagating both ways round the periodic time direction).  NaN where the
+    ratio has no such solution.  Root by Brent's method."""
+    from scipy.optimize import brentq
+
+    c = np.asarray(cpp, dtype=float)
+    T = len(c)
+    out = np.full(T - 1, np.nan)
+    for t in range(T - 1):
+        r = c[t] / c[t + 1]
+        if not (r > 0 and np.isfinite(r)):
+            continue
+        a, b = T / 2.0 - t, T / 2.0 - t - 1.0
+
+        def f(m):
+            return _log_cosh(m * a) - _log_cosh(m * b) - np.log(r)
+
+        lo, hi = 1e-12, 50.0
+        if f(lo) * f(hi) < 0:
+            out[t] = brentq(f, lo, hi, xtol=1e-15, rtol=1e-15, maxiter=500)
+    return out
+
+
+def fit_correlator(cpp, kind, t0, t1):
+    """Least-squares fit of C(y0) = A exp(-m y0) (kind "exp") or
+    A [exp(-m y0) + exp(-m (T - y0))] (kind "cosh") to y0 = t0..t1, in the
+    relative deviations A model/C - 1 (no statistical weights: one synthetic
+    configuration).  Both parameters by scipy's trust-region least squares
+    from the log-ratio effective mass at the window's start.  Returns
+    (m, A, rms relative deviation)."""
+    from scipy.optimize import least_squares
+
+    c = np.asarray(cpp, dtype=float)
+    T = len(c)
+    t = np.arange(t0, t1 + 1, dtype=float)
+    ct = c[t0:t1 + 1]
+
+    def model(m):
+        f = np.exp(-m * t)
+        if kind == "cosh":
+            f = f + np.exp(-m * (T - t))
+        return f
+
+    m0 = max(np.log(c[t0] / c[t0 + 1]), 1e-3)
+    A0 = ct[0] / model(m0)[0]
+    res = least_squares(lambda p: p[0] * model(p[1]) / ct - 1.0, x0=[A0, m0], xtol=1e-15,
+                        ftol=1e-15, gtol=1e-15, method="lm")
+    A, m = res.x
+    dev = A * model(m) / ct - 1.0
+    return float(m), float(A), float(np.sqrt(np.mean(dev ** 2)))
 
 
 # --------------------------------------------------------------------------
