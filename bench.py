@@ -884,6 +884,11 @@ def main():
         cpp_c, cap_c, _ = dp.dp_solve_point_corr(ctx, field, MASS, prof, (0, 0, 0, 0), RES, opts, T=T)
         mp = dp.pcac_mass(cpp_c, cap_c)
         line["pcac_mass_plateau_y0_8_20"] = float(np.mean(mp[8:21]))
+        # effective mass of the same C_PP: cosh form and a two-sided fit
+        meff = dp.dp_effective_mass(cpp_c, "cosh")
+        m_fit, _, rms_fit = dp.dp_fit_correlator(cpp_c, "cosh", 12, 24)
+        line["effective_mass"] = {"cosh_y0_8_20": [float(v) for v in meff[8:21]],
+                                  "cosh_fit_y0_12_24": m_fit, "fit_rms_rel_dev": rms_fit}
         if "outer_double_float" in line:
             c, _, _ = dp.dp_solve_point(ctx, field, MASS, prof, (0, 0, 0, 0), RES,
                                         dict(opts, outer_df=1), T=T)

@@ -308,6 +308,29 @@ dp_status dp_apply(dp_ctx *ctx, dp_field field, int kind, double M, const dp_pro
 dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profile,
                             const int src[4], double *alpha_out, double *hop_out);
 
+/* ---- correlator analysis (host only, no GPU) ------------------------------
+ * The paper plots effective masses of C_PP (Sec. III, Figs. 1-2) without
+ * writing a definition out.  c holds C(y0), y0 = 0..T-1 relative to the
+ * source (the layout dp_solve_point returns); caller-owned, only read. */
+
+/* Effective mass per y0 = 0..T-2 into m_out[T-1].  kind 0: the log ratio
+ * ln[C(y0)/C(y0+1)].  kind 1: the cosh form for two-sided decay round the
+ * periodic time direction, the m > 0 with C(y0)/C(y0+1) =
+ * cosh[m (T/2 - y0)] / cosh[m (T/2 - y0 - 1)] (bisection on (0, 50]).  NaN
+ * where the ratio is not positive or the form cannot reach it.  Errors:
+ * null pointers, T < 2, another kind (DP_ERR_INVALID_ARG). */
+dp_status dp_effective_mass(const double *c, int T, int kind, double *m_out);
+
+/* Fit of C(y0) = A exp(-m y0) (kind 0) or A [exp(-m y0) + exp(-m (T - y0))]
+ * (kind 1) over y0 = t0..t1 by least squares in the relative deviations
+ * A f(y0)/C(y0) - 1 (one configuration: no statistical weights).  A takes
+ * its closed-form minimum for each m; m is located by a log-spaced scan of
+ * [1e-4, 20] and golden-section search.  Out: m, A (may be NULL) and the rms
+ * relative deviation (may be NULL).  Errors: 0 <= t0 < t1 < T violated, a
+ * zero, non-finite value or sign change in the window (DP_ERR_INVALID_ARG). */
+dp_status dp_fit_correlator(const double *c, int T, int kind, int t0, int t1, double *m_out,
+                            double *A_out, double *rms_out);
+
 /* ---- device-resident operator for benchmarks and the autotuner ---------- */
 
 /* One hopping application D_{p,1-p} with the fused clover-inverse epilogue

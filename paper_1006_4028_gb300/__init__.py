@@ -26,11 +26,11 @@ __all__ = [
     "dp_create", "dp_destroy", "dp_last_error", "dp_device_bytes", "dp_trim",
     "dp_field_load", "dp_field_set_csw", "dp_field_free",
     "dp_solve_point", "dp_solve_point_multi", "dp_solve_point_dev",
-    "dp_solve_point_corr", "dp_solve_point_hl", "pcac_mass", "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
+    "dp_solve_point_corr", "dp_solve_point_hl", "pcac_mass", "dp_effective_mass", "dp_fit_correlator", "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
     "dp_autotune",
     "dp_timing_enable", "dp_timing_reset", "dp_timing_get", "dp_launch_count",
     "dp_serve_start", "dp_submit", "dp_wait", "dp_cancel", "dp_serve_stats_get", "dp_serve_stop",
-    "PROFILE_KINDS", "PREC", "SOLVER", "APPLY", "STATUS",
+    "PROFILE_KINDS", "PREC", "SOLVER", "APPLY", "STATUS", "MEFF_KINDS",
 ]
 
 PROFILE_KINDS = {"none": 0, "exp_t": 1, "cosh_t": 2, "cosh_4d": 3, "table": 4}
@@ -110,6 +110,8 @@ def load(build_if_missing=False):
         "dp_last_error": ([], C.c_char_p),
         "dp_device_bytes": ([vp], sz),
         "dp_trim": ([vp], ip),
+        "dp_effective_mass": ([vp, ip, ip, vp], ip),
+        "dp_fit_correlator": ([vp, ip, ip, ip, ip, P(dp), P(dp), P(dp)], ip),
         "dp_field_load": ([vp, vp, P(C.c_int * 4), ip, P(up)], ip),
         "dp_field_set_csw": ([vp, up, dp], ip),
         "dp_field_free": ([vp, up], ip),
@@ -302,6 +304,31 @@ def pcac_mass(cpp, cap):
     m = np.full(len(cpp), np.nan)
     m[1:-1] = (cap[2:] - cap[:-2]) / (4.0 * cpp[1:-1])
     return m
+
+
+MEFF_KINDS = {"log": 0, "cosh": 1}
+
+
+def dp_effective_mass(cpp, kind="log"):
+    """Effective mass per y0 = 0..T-2 of a correlator (host function of the
+    library): "log" ln[C(y0)/C(y0+1)] or "cosh" (two-sided decay); NaN where
+    undefined."""
+    c = np.ascontiguousarray(cpp, dtype=np.float64)
+    out = np.empty(max(len(c) - 1, 0), dtype=np.float64)
+    _check(load().dp_effective_mass(c.ctypes.data, len(c), MEFF_KINDS[kind], out.ctypes.data))
+    return out
+
+
+def dp_fit_correlator(cpp, kind, t0, t1):
+    """Least-squares fit of A exp(-m y0) ("log"/"exp") or A [exp(-m y0) +
+    exp(-m (T - y0))] ("cosh") over y0 = t0..t1 in relative deviations;
+    returns (m, A, rms relative deviation)."""
+    c = np.ascontiguousarray(cpp, dtype=np.float64)
+    m, A, rms = C.c_double(), C.c_double(), C.c_double()
+    k = {"log": 0, "exp": 0, "cosh": 1}[kind]
+    _check(load().dp_fit_correlator(c.ctypes.data, len(c), k, int(t0), int(t1), C.byref(m),
+                                    C.byref(A), C.byref(rms)))
+    return m.value, A.value, rms.value
 
 
 def dp_solve_point_multi(ctx, field, Ms, profiles, src, r, opts=None, T=None, V=None,

@@ -264,3 +264,20 @@ def test_pool_keeps_memory_and_trim(ctx, inter):
     assert ia["status"] == 0 and ib["status"] == 0
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(b, c)
+
+
+def test_effective_mass_fit_of_solved_free_correlator(ctx):
+    """C_PP from the GPU solve, analysed by the library's host functions,
+    against the oracle's analysis of the exact free correlator."""
+    dims = (16, 8, 8, 8)
+    f = dp.dp_field_load(ctx, li.unit_links(dims), dims, -1)
+    cpp, _, info = dp.dp_solve_point(ctx, f, 0.5, ("cosh_t", 0.4), (0, 0, 0, 0), 1e-11, MIXED, T=16)
+    exact = oracle.free_cpp(dims, 0.5)
+    assert info["status"] == 0
+    got = dp.dp_effective_mass(cpp, "cosh")
+    ref = oracle.effective_mass_cosh(exact)
+    np.testing.assert_allclose(got[:8], ref[:8], rtol=0, atol=1e-5)
+    m, _, _ = dp.dp_fit_correlator(cpp, "cosh", 4, 12)
+    mo, _, _ = oracle.fit_correlator(exact, "cosh", 4, 12)
+    assert abs(m - mo) < 1e-6
+    dp.dp_field_free(ctx, f)

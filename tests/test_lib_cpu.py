@@ -129,3 +129,35 @@ def test_reciprocal_profile_hop_factors(lib, kind, alpha0, bc_t):
         L = dims[mu]
         np.testing.assert_allclose(0.25 / hop[mu, 0, :L], -0.5 * fwd[mu, :L], rtol=1e-14, atol=0)
         np.testing.assert_allclose(0.25 / hop[mu, 1, :L], -0.5 * bwd[mu, :L], rtol=1e-14, atol=0)
+
+
+def test_effective_mass_and_fit_match_oracle(lib):
+    """Host-side correlator analysis of the library (bisection, scan and
+    golden-section search) against the oracle's (Brent, Levenberg-Marquardt)
+    on the free 64x4^3 correlator and on exact exponentials."""
+    c = oracle.free_cpp((64, 4, 4, 4), 0.5)
+    for kind, ref in (("log", oracle.effective_mass(c)), ("cosh", oracle.effective_mass_cosh(c))):
+        got = dp.dp_effective_mass(c, kind)
+        assert np.array_equal(np.isnan(got), np.isnan(ref))
+        ok = np.isfinite(ref)
+        np.testing.assert_allclose(got[ok], ref[ok], rtol=1e-12, atol=1e-13)
+    for kind, t0, t1 in (("cosh", 20, 44), ("cosh", 6, 30), ("exp", 10, 20)):
+        m, A, rms = dp.dp_fit_correlator(c, kind, t0, t1)
+        mo, Ao, rmso = oracle.fit_correlator(c, kind, t0, t1)
+        assert abs(m - mo) < 1e-9 * mo and abs(A - Ao) < 1e-8 * abs(Ao)
+        assert abs(rms - rmso) < 1e-9 + 1e-6 * rmso
+    t = np.arange(24, dtype=float)
+    m, A, rms = dp.dp_fit_correlator(2.0 * np.cosh(0.45 * (t - 12)), "cosh", 3, 21)
+    assert abs(m - 0.45) < 1e-12 and rms < 1e-13
+
+
+def test_analysis_rejects_bad_windows(lib):
+    c = np.array([-1.0, -0.5, 0.2, 0.1, -0.05])
+    with pytest.raises(dp.DpError):
+        dp.dp_fit_correlator(c, "exp", 0, 3)      # sign change
+    with pytest.raises(dp.DpError):
+        dp.dp_fit_correlator(c, "exp", 3, 3)      # one point
+    with pytest.raises(dp.DpError):
+        dp.dp_fit_correlator(c, "cosh", 2, 5)     # past T
+    m = dp.dp_effective_mass(c, "cosh")
+    assert np.isfinite(m[0]) and np.isnan(m[1])
