@@ -271,6 +271,7 @@ def test_effective_mass_fit_of_solved_free_correlator(ctx):
     against the oracle's analysis of the exact free correlator."""
     dims = (16, 8, 8, 8)
     f = dp.dp_field_load(ctx, li.unit_links(dims), dims, -1)
+    dp.dp_field_set_csw(ctx, f, 1.7)
     cpp, _, info = dp.dp_solve_point(ctx, f, 0.5, ("cosh_t", 0.4), (0, 0, 0, 0), 1e-11, MIXED, T=16)
     exact = oracle.free_cpp(dims, 0.5)
     assert info["status"] == 0
