@@ -674,9 +674,10 @@ def main():
                     choices=["heavy48", "free16", "light64", "multimass32", "serve", "sf48"],
                     help="heavy48: the headline solves/s line (default); the others run the "
                          "study's other workloads and print their own JSON line")
-    ap.add_argument("--graphs", type=int, default=0,
-                    help="capture solver iterations as CUDA graphs in the timed region "
-                         "(per-kernel event timing needs them off)")
+    ap.add_argument("--graphs", type=int, default=1,
+                    help="capture solver iterations as CUDA graphs in the timed region (the "
+                         "per-kernel event times then come from a separate pass of up to 3 "
+                         "solves without graphs)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.dims:

@@ -152,23 +152,40 @@ __device__ __forceinline__ void block_sum6(float (&v)[6], float *red)
     }
 }
 
+// Grid: x = RHS pair (fastest, so the pair-CTAs of one block run together
+// and share its links and clover inverses in L1/L2), y = the blocks of this
+// colour (when the x-block count is even; otherwise all blocks, the other
+// colour exiting at once).  Shared memory per CTA: the block residual rho
+// (parity p), the correction delta (parity p) and t, then q (parity q / p).
 template <int LF>
-__global__ void __launch_bounds__(128) k_sap_block(const SapParams p)
+__global__ void __launch_bounds__(128, 3) k_sap_block(const SapParams p)
 {
-    extern __shared__ ulonglong2 sm[];  // R: [12][vbh] (parity p), T: [12][vbh] (parity q)
+    extern __shared__ ulonglong2 sm[];  // R, D: [12][vbh] (parity p); T: [12][vbh]
     __shared__ float red[4 * 6];
     const int vbh = p.bs[0] * p.bs[1] * p.bs[2] * p.bs[3] / 2;
-    ulonglong2 *R = sm, *Tq = sm + 12 * vbh;
+    ulonglong2 *R = sm, *Tq = sm + 12 * vbh, *D = sm + 24 * vbh;
     // block coordinates and colour
-    int b = blockIdx.x;
-    const int bx = b % p.nb[1];
-    b /= p.nb[1];
-    const int by = b % p.nb[2];
-    b /= p.nb[2];
-    const int bz = b % p.nb[3];
-    const int bt = b / p.nb[3];
-    if (((bt + bx + by + bz) & 1) != p.colour) return;
-    const int q0 = blockIdx.y;  // RHS pair
+    int b = blockIdx.y;
+    int bx, by, bz, bt;
+    if (p.nb[1] % 2 == 0) {
+        const int nxh = p.nb[1] / 2;
+        const int j = b % nxh;
+        b /= nxh;
+        by = b % p.nb[2];
+        b /= p.nb[2];
+        bz = b % p.nb[3];
+        bt = b / p.nb[3];
+        bx = 2 * j + ((bt + by + bz + p.colour) & 1);
+    } else {
+        bx = b % p.nb[1];
+        b /= p.nb[1];
+        by = b % p.nb[2];
+        b /= p.nb[2];
+        bz = b % p.nb[3];
+        bt = b / p.nb[3];
+        if (((bt + bx + by + bz) & 1) != p.colour) return;
+    }
+    const int q0 = blockIdx.x;  // RHS pair
     if (p.active && !p.active[2 * q0 * p.active_stride] && !p.active[(2 * q0 + 1) * p.active_stride])
         return;
     const int ot = bt * p.bs[0], ox = bx * p.bs[1], oy = by * p.bs[2], oz = bz * p.bs[3];
@@ -185,11 +202,11 @@ __global__ void __launch_bounds__(128) k_sap_block(const SapParams p)
         sq_ = local_site(p, i, qq, ot, ox, oy, oz);
         const ulonglong2 *src = static_cast<const ulonglong2 *>(p.res) + sp_.s * P + q0;
 #pragma unroll
-        for (int k = 0; k < 12; k++) R[k * vbh + i] = __ldg(src + k * cs);
+        for (int k = 0; k < 12; k++) {
+            R[k * vbh + i] = __ldg(src + k * cs);
+            D[k * vbh + i] = make_ulonglong2(0ull, 0ull);
+        }
     }
-    C2 delta[12];
-#pragma unroll
-    for (int k = 0; k < 12; k++) delta[k] = {0ull, 0ull};
     for (int it = 0; it < p.n_mr; it++) {
         __syncthreads();
         C2 acc[12];
@@ -201,24 +218,28 @@ __global__ void __launch_bounds__(128) k_sap_block(const SapParams p)
             for (int k = 0; k < 12; k++) Tq[k * vbh + i] = make_ulonglong2(acc[k].re, acc[k].im);
         }
         __syncthreads();
-        float d[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // <q, rho> re, im per lane; |q|^2 per lane
-        C2 qv[12];
         if (live) {
-            // q (p-site i) = rho - A_pp^-1 D_pq|_B t
+            // A_pp^-1 D_pq|_B t (p-site i)
             block_hops<LF>(p, sp_, pp, Tq, vbh, ht, acc);
             clover_inv_apply(static_cast<const float4 *>(p.clov[pp][grp]), Vh, sp_.s, acc);
+        }
+        __syncthreads();  // every t read: T now holds q
+        float d[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // <q, rho> re, im per lane; |q|^2 per lane
+        if (live) {
+            // q = rho - A_pp^-1 D_pq|_B t
             f2 dre = 0ull, dim = 0ull, nn = 0ull;
 #pragma unroll
             for (int k = 0; k < 12; k++) {
                 const ulonglong2 rv = R[k * vbh + i];
                 const C2 rho = {rv.x, rv.y};
-                qv[k] = c2_sub(rho, acc[k]);
-                dre = ffma2(qv[k].re, rho.re, dre);
-                dre = ffma2(qv[k].im, rho.im, dre);
-                dim = ffma2(qv[k].re, rho.im, dim);
-                dim = ffma2(fneg2(qv[k].im), rho.re, dim);
-                nn = ffma2(qv[k].re, qv[k].re, nn);
-                nn = ffma2(qv[k].im, qv[k].im, nn);
+                const C2 q = c2_sub(rho, acc[k]);
+                Tq[k * vbh + i] = make_ulonglong2(q.re, q.im);
+                dre = ffma2(q.re, rho.re, dre);
+                dre = ffma2(q.im, rho.im, dre);
+                dim = ffma2(q.re, rho.im, dim);
+                dim = ffma2(fneg2(q.im), rho.re, dim);
+                nn = ffma2(q.re, q.re, nn);
+                nn = ffma2(q.im, q.im, nn);
             }
             upk(dre, d[0], d[1]);
             upk(dim, d[2], d[3]);
@@ -235,11 +256,12 @@ __global__ void __launch_bounds__(128) k_sap_block(const SapParams p)
             const C2 mom = {fneg2(om.re), fneg2(om.im)};
 #pragma unroll
             for (int k = 0; k < 12; k++) {
-                const ulonglong2 rv = R[k * vbh + i];
+                const ulonglong2 rv = R[k * vbh + i], qv = Tq[k * vbh + i], dv = D[k * vbh + i];
                 C2 rho = {rv.x, rv.y};
-                delta[k] = c2_lanefma(om, rho, delta[k]);
-                rho = c2_lanefma(mom, qv[k], rho);
+                const C2 dl = c2_lanefma(om, rho, C2{dv.x, dv.y});
+                rho = c2_lanefma(mom, C2{qv.x, qv.y}, rho);
                 R[k * vbh + i] = make_ulonglong2(rho.re, rho.im);
+                D[k * vbh + i] = make_ulonglong2(dl.re, dl.im);
             }
         }
     }
@@ -247,20 +269,20 @@ __global__ void __launch_bounds__(128) k_sap_block(const SapParams p)
         ulonglong2 *z = static_cast<ulonglong2 *>(p.z) + sp_.s * P + q0;
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-            const ulonglong2 zv = z[k * cs];
-            const C2 s = c2_add({zv.x, zv.y}, delta[k]);
+            const ulonglong2 zv = z[k * cs], dv = D[k * vbh + i];
+            const C2 s = c2_add({zv.x, zv.y}, C2{dv.x, dv.y});
             z[k * cs] = make_ulonglong2(s.re, s.im);
         }
     }
 }
 
-// 4^4 blocks need 48 KB of dynamic shared memory plus the reduction scratch:
+// 4^4 blocks need 72 KB of dynamic shared memory plus the reduction scratch:
 // opt in once per kernel
 template <int LF>
 cudaError_t launch_sap_k(const SapParams &p, dim3 grid, int threads, size_t smem, cudaStream_t st)
 {
     static const cudaError_t attr =
-        cudaFuncSetAttribute(k_sap_block<LF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        cudaFuncSetAttribute(k_sap_block<LF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024);
     if (attr != cudaSuccess) return attr;
     k_sap_block<LF><<<grid, threads, smem, st>>>(p);
     return cudaGetLastError();
@@ -284,8 +306,9 @@ cudaError_t launch_sap_block(const SapParams &p, int link_fmt, cudaStream_t st)
     const int vbh = p.bs[0] * p.bs[1] * p.bs[2] * p.bs[3] / 2;
     if (vbh < 1 || vbh > 128 || p.nrhs % 2) return cudaErrorInvalidValue;
     const int threads = (vbh + 31) / 32 * 32;
-    const size_t smem = (size_t)2 * 12 * vbh * sizeof(ulonglong2);
-    dim3 grid(p.nb[0] * p.nb[1] * p.nb[2] * p.nb[3], p.nrhs / 2);
+    const size_t smem = (size_t)3 * 12 * vbh * sizeof(ulonglong2);
+    const int nbt = p.nb[0] * p.nb[1] * p.nb[2] * p.nb[3];
+    dim3 grid(p.nrhs / 2, p.nb[1] % 2 == 0 ? nbt / 2 : nbt);
     switch (link_fmt) {
     case LINK_F32_12: return launch_sap_k<LINK_F32_12>(p, grid, threads, smem, st);
     case LINK_F32_18: return launch_sap_k<LINK_F32_18>(p, grid, threads, smem, st);
