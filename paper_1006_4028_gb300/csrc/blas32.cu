@@ -1,9 +1,12 @@
 // FP32 inner-solver BLAS-1 kernels on the paired layout of pair.cuh: one
 // thread per (site, RHS pair), every update one packed f32x2 instruction for
 // the two RHS, per-RHS scalars (alpha, omega, beta) held per lane.  Dot
-// products are formed per site in FP32 (24 terms) and accumulated across
-// sites in FP64 per RHS; the reductions and scalar recurrences are those of
-// the FP64 kernels (reduce.cuh), so every decision stays per RHS.
+// products are summed in FP32 over the sites one thread visits (24 terms a
+// site, a few tens of sites: one packed f32x2 add per site and value, where
+// an FP64 add per site would run on GB300's 1/64-rate FP64 pipe) and across
+// threads and blocks in FP64 per RHS; the reductions and scalar recurrences
+// are those of the FP64 kernels (reduce.cuh), so every decision stays per
+// RHS.
 //
 // A pair is processed while either of its RHS is active; an inactive lane's
 // solution x is never changed (lane blend), and its terms are excluded from
@@ -116,13 +119,16 @@ __global__ void __launch_bounds__(kMaxBlock) k32_alpha(Cfg c, const void *rh, co
 {
     double acc[4] = {0, 0, 0, 0};  // lane 0: re, im; lane 1: re, im
     {
+        f2 sum0 = 0ull, sum1 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
             const C2 d = pdot(ldp(rh, cs, me), ldp(vv, cs, me));
-            add_lanes(acc[0], acc[2], d.re, a0, a1);
-            add_lanes(acc[1], acc[3], d.im, a0, a1);
+            sum0 = fadd2(sum0, d.re);
+            sum1 = fadd2(sum1, d.im);
         }
+        add_lanes(acc[0], acc[2], sum0, a0, a1);
+        add_lanes(acc[1], acc[3], sum1, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<2, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -150,15 +156,19 @@ __global__ void __launch_bounds__(kMaxBlock) k32_omega(Cfg c, const void *tv, co
 {
     double acc[6] = {0, 0, 0, 0, 0, 0};
     {
+        f2 sum0 = 0ull, sum1 = 0ull, sum2 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
             const P12 t = ldp(tv, cs, me), sx = ldp(sv, cs, me);
             const C2 d = pdot(t, sx);
-            add_lanes(acc[0], acc[3], d.re, a0, a1);
-            add_lanes(acc[1], acc[4], d.im, a0, a1);
-            add_lanes(acc[2], acc[5], pnorm(t), a0, a1);
+            sum0 = fadd2(sum0, d.re);
+            sum1 = fadd2(sum1, d.im);
+            sum2 = fadd2(sum2, pnorm(t));
         }
+        add_lanes(acc[0], acc[3], sum0, a0, a1);
+        add_lanes(acc[1], acc[4], sum1, a0, a1);
+        add_lanes(acc[2], acc[5], sum2, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<3, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -181,6 +191,7 @@ k32_update(Cfg c, void *xv, void *rv, const void *pv, const void *sv, const void
         const C2 al = lanes(st[2 * qq].alpha, st[2 * qq + 1].alpha);
         const C2 om = lanes(st[2 * qq].omega, st[2 * qq + 1].omega);
         const C2 mom = neg(om);
+        f2 sum0 = 0ull, sum1 = 0ull, sum2 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
@@ -203,10 +214,13 @@ k32_update(Cfg c, void *xv, void *rv, const void *pv, const void *sv, const void
                 nn = ffma2(r.re, r.re, nn);
                 nn = ffma2(r.im, r.im, nn);
             }
-            add_lanes(acc[0], acc[3], dre, a0, a1);
-            add_lanes(acc[1], acc[4], dim, a0, a1);
-            add_lanes(acc[2], acc[5], nn, a0, a1);
+            sum0 = fadd2(sum0, dre);
+            sum1 = fadd2(sum1, dim);
+            sum2 = fadd2(sum2, nn);
         }
+        add_lanes(acc[0], acc[3], sum0, a0, a1);
+        add_lanes(acc[1], acc[4], sum1, a0, a1);
+        add_lanes(acc[2], acc[5], sum2, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<3, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -220,6 +234,7 @@ __global__ void __launch_bounds__(kMaxBlock) k32_init(Cfg c, const void *bv, voi
 {
     double acc[2] = {0, 0};
     {
+        f2 sum0 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
@@ -227,8 +242,9 @@ __global__ void __launch_bounds__(kMaxBlock) k32_init(Cfg c, const void *bv, voi
             stp(rv, cs, me, b);
             stp(rh, cs, me, b);
             if (pv) stp(pv, cs, me, b);
-            add_lanes(acc[0], acc[1], pnorm(b), a0, a1);
+            sum0 = fadd2(sum0, pnorm(b));
         }
+        add_lanes(acc[0], acc[1], sum0, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -252,6 +268,7 @@ __global__ void __launch_bounds__(kMaxBlock) k32_omega_rho(Cfg c, const void *tv
 #pragma unroll
     for (int k = 0; k < 14; k++) acc[k] = 0;
     {
+        f2 sum0 = 0ull, sum1 = 0ull, sum2 = 0ull, sum3 = 0ull, sum4 = 0ull, sum5 = 0ull, sum6 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
@@ -274,14 +291,21 @@ __global__ void __launch_bounds__(kMaxBlock) k32_omega_rho(Cfg c, const void *tv
                 rti = ffma2(h.re, t.im, rti);
                 rti = ffma2(fneg2(h.im), t.re, rti);
             }
-            add_lanes(acc[0], acc[7], tsr, a0, a1);
-            add_lanes(acc[1], acc[8], tsi, a0, a1);
-            add_lanes(acc[2], acc[9], tt, a0, a1);
-            add_lanes(acc[3], acc[10], rsr, a0, a1);
-            add_lanes(acc[4], acc[11], rsi, a0, a1);
-            add_lanes(acc[5], acc[12], rtr, a0, a1);
-            add_lanes(acc[6], acc[13], rti, a0, a1);
+            sum0 = fadd2(sum0, tsr);
+            sum1 = fadd2(sum1, tsi);
+            sum2 = fadd2(sum2, tt);
+            sum3 = fadd2(sum3, rsr);
+            sum4 = fadd2(sum4, rsi);
+            sum5 = fadd2(sum5, rtr);
+            sum6 = fadd2(sum6, rti);
         }
+        add_lanes(acc[0], acc[7], sum0, a0, a1);
+        add_lanes(acc[1], acc[8], sum1, a0, a1);
+        add_lanes(acc[2], acc[9], sum2, a0, a1);
+        add_lanes(acc[3], acc[10], sum3, a0, a1);
+        add_lanes(acc[4], acc[11], sum4, a0, a1);
+        add_lanes(acc[5], acc[12], sum5, a0, a1);
+        add_lanes(acc[6], acc[13], sum6, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<7, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -301,6 +325,7 @@ k32_update_p(Cfg c, void *xv, void *rv, void *pv, const void *sv, const void *tv
         const C2 om = lanes(st[2 * qq].omega, st[2 * qq + 1].omega);
         const C2 be = lanes(st[2 * qq].beta, st[2 * qq + 1].beta);
         const C2 mom = neg(om);
+        f2 sum0 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
@@ -320,8 +345,9 @@ k32_update_p(Cfg c, void *xv, void *rv, void *pv, const void *sv, const void *tv
                 nn = ffma2(r.re, r.re, nn);
                 nn = ffma2(r.im, r.im, nn);
             }
-            add_lanes(acc[0], acc[1], nn, a0, a1);
+            sum0 = fadd2(sum0, nn);
         }
+        add_lanes(acc[0], acc[1], sum0, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -339,6 +365,7 @@ k32_cg_gamma(Cfg c, const void *zv, long long Vh, int nrhs, RhsState *st, int fi
 {
     double acc[2] = {0, 0};
     {
+        f2 sum0 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
@@ -349,8 +376,9 @@ k32_cg_gamma(Cfg c, const void *zv, long long Vh, int nrhs, RhsState *st, int fi
                 nn = ffma2(z.re, z.re, nn);
                 nn = ffma2(z.im, z.im, nn);
             }
-            add_lanes(acc[0], acc[1], nn, a0, a1);
+            sum0 = fadd2(sum0, nn);
         }
+        add_lanes(acc[0], acc[1], sum0, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -385,6 +413,7 @@ k32_cg_alpha(Cfg c, const void *wv, long long Vh, int nrhs, RhsState *st, double
 {
     double acc[2] = {0, 0};
     {
+        f2 sum0 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
@@ -395,8 +424,9 @@ k32_cg_alpha(Cfg c, const void *wv, long long Vh, int nrhs, RhsState *st, double
                 nn = ffma2(w.re, w.re, nn);
                 nn = ffma2(w.im, w.im, nn);
             }
-            add_lanes(acc[0], acc[1], nn, a0, a1);
+            sum0 = fadd2(sum0, nn);
         }
+        add_lanes(acc[0], acc[1], sum0, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -414,6 +444,7 @@ k32_cg_update(Cfg c, void *xv, void *rv, const void *pv, const void *wv, long lo
         const int qq = threadIdx.x % (nrhs / 2);
         const f2 al = lanes_re(st[2 * qq].alpha.x, st[2 * qq + 1].alpha.x);
         const f2 mal = fneg2(al);
+        f2 sum0 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
@@ -434,8 +465,9 @@ k32_cg_update(Cfg c, void *xv, void *rv, const void *pv, const void *wv, long lo
                 nn = ffma2(r.re, r.re, nn);
                 nn = ffma2(r.im, r.im, nn);
             }
-            add_lanes(acc[0], acc[1], nn, a0, a1);
+            sum0 = fadd2(sum0, nn);
         }
+        add_lanes(acc[0], acc[1], sum0, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -453,6 +485,7 @@ k32_dotv(Cfg c, const void *av, const void *bv, long long Vh, int nrhs, const Rh
 {
     double acc[4] = {0, 0, 0, 0};
     {
+        f2 sum0 = 0ull, sum1 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
@@ -465,9 +498,11 @@ k32_dotv(Cfg c, const void *av, const void *bv, long long Vh, int nrhs, const Rh
                 im = ffma2(x.re, y.im, im);
                 im = ffma2(fneg2(x.im), y.re, im);
             }
-            add_lanes(acc[0], acc[2], re, a0, a1);
-            add_lanes(acc[1], acc[3], im, a0, a1);
+            sum0 = fadd2(sum0, re);
+            sum1 = fadd2(sum1, im);
         }
+        add_lanes(acc[0], acc[2], sum0, a0, a1);
+        add_lanes(acc[1], acc[3], sum1, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<2, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -482,6 +517,7 @@ k32_norm2v(Cfg c, const void *av, long long Vh, int nrhs, const RhsState *st, do
 {
     double acc[2] = {0, 0};
     {
+        f2 sum0 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
@@ -492,8 +528,9 @@ k32_norm2v(Cfg c, const void *av, long long Vh, int nrhs, const RhsState *st, do
                 nn = ffma2(x.re, x.re, nn);
                 nn = ffma2(x.im, x.im, nn);
             }
-            add_lanes(acc[0], acc[1], nn, a0, a1);
+            sum0 = fadd2(sum0, nn);
         }
+        add_lanes(acc[0], acc[1], sum0, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
@@ -557,6 +594,7 @@ k32_gcr_update(Cfg c, void *xv, void *rv, const void *zv, const void *wv, long l
     {
         const int qq = threadIdx.x % (nrhs / 2);
         const C2 a = coef_lanes(cf, qq, 1.0), ma = coef_lanes(cf, qq, -1.0);
+        f2 sum0 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
@@ -574,8 +612,9 @@ k32_gcr_update(Cfg c, void *xv, void *rv, const void *zv, const void *wv, long l
                 nn = ffma2(r.re, r.re, nn);
                 nn = ffma2(r.im, r.im, nn);
             }
-            add_lanes(acc[0], acc[1], nn, a0, a1);
+            sum0 = fadd2(sum0, nn);
         }
+        add_lanes(acc[0], acc[1], sum0, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
     if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
