@@ -66,6 +66,25 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_max(pg, x):
+    """The maximum of a float over the ranks of the job (x itself without a
+    process group); NCCL reduces on the GPU, gloo on the host."""
+    if pg is None:
+        return float(x)
+    import torch
+
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(steps, ws, ms_max):
+    """Whole-job throughput of N independent replicas: the solves of every
+    rank over the slowest rank's time (weak scaling)."""
+    return steps * ws / (ms_max / 1e3)
+
+
 class Clocks:
     """nvidia-smi sampling of SM clock and throttle reasons during a region."""
 
@@ -780,12 +799,8 @@ def main():
     d32_n, d32_ms = dp.dp_timing_get(ctx, "dslash_fp32")
     d64_n, d64_ms = dp.dp_timing_get(ctx, "dslash_fp64")
     dp.dp_timing_enable(ctx, False)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    total = args.steps * ws
-    value = total / (ms / 1e3)
+    ms = rank_max(pg, ms)
+    value = replica_value(args.steps, ws, ms)
 
     # ---- roofline of the dominant kernel (multi-RHS FP32 dslash) ----
     Vh = V // 2
