@@ -347,9 +347,10 @@ dp_status dp_fit_correlator(const double *c, int T, int kind, int t0, int t1, do
  * 2-3 staged through shared memory with that many of the 8 directions in
  * flight, 4 staged (2 in flight) by one persistent wave of blocks whose
  * threads walk several sites (staging needs 64, 96 or 128 threads per
- * block), 5 direct loads with an L1 prefetch 2 directions ahead (all of
- * 2-5 need FP32 or 16-bit 12-real links and 2 RHS per thread), -1 the tuned
- * or default choice.
+ * block), 5 direct loads with an L1 prefetch 2 directions ahead, 6 the
+ * spinor alone staged (2 in flight) with the link read from L1, 16 warps
+ * per SM (64, 96 or 128 threads per block); all of 2-6 need FP32 or 16-bit
+ * 12-real links and 2 RHS per thread.  -1: the tuned or default choice.
  * FP32 needs nrhs even.  iters launches back to back; if ms_out is non-NULL
  * it receives the average launch time measured with CUDA events on the
  * context stream. */

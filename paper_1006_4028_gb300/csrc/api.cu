@@ -812,7 +812,7 @@ dp_status dp_dslash_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile 
     Field &f = *fp;
     if (!in || !out || nrhs < 1 || nrhs > kMaxRhs || iters < 1 || (out_parity & ~1) ||
         prec < DP_PREC_FP64 || prec > DP_PREC_MIXED_BF16 ||
-        rhs_per_thread < 0 || stages < -1 || stages > 5 ||
+        rhs_per_thread < 0 || stages < -1 || stages > 6 ||
         (block_threads != 0 && (block_threads < 32 || block_threads > 256 || block_threads % 32))) {
         set_error("dp_dslash_dev: invalid argument");
         return DP_ERR_INVALID_ARG;
@@ -917,11 +917,12 @@ dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int
     cudaMemsetAsync(in, 0, vb, c.stream);
     // candidates: four block sizes x RHS per thread (FP64: 1; FP32: one or
     // two RHS pairs) x how neighbour data arrives (FP32 one pair per thread:
-    // direct, shared-memory staging 2-3 directions ahead or in a persistent
-    // wave, or direct with an L1 prefetch 2 directions ahead)
+    // direct, shared-memory staging of spinor and link 2-3 directions ahead
+    // or in a persistent wave, direct with an L1 prefetch 2 directions ahead,
+    // or the spinor alone staged 2 directions ahead with the link from L1)
     const int blocks[] = {64, 96, 128, 192, 256};
     const int rpts[] = {1, 2, 4};
-    const int stage_opts[] = {0, 2, 3, 4, 5};
+    const int stage_opts[] = {0, 2, 3, 4, 5, 6};
     Shape best;
     float bms = 1e30f;
     dp_status st = DP_OK;

@@ -90,7 +90,9 @@ struct DslashParams {
 // that stages neighbour spinors and links through shared memory: 2-3 =
 // that many directions in flight; 4 = 2 in flight, one persistent wave of
 // blocks whose threads walk several sites; 5 = direct loads with an L1
-// prefetch 2 directions ahead (any block size); 0 = direct loads
+// prefetch 2 directions ahead (any block size); 6 = the spinor alone staged
+// (2 in flight), the link prefetched into L1, 16 warps per SM; 0 = direct
+// loads
 cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi, int block,
                           int rpt, cudaStream_t st, int stages = 0);
 bool dslash_rpt_ok(int nrhs, int rpt, int prec, int epi);

@@ -639,6 +639,123 @@ __global__ void __launch_bounds__(256) k_dslash32f(const DslashParams p)
     finish32<EPI, 1>(p, acc, act, s, q0, grp, cs);
 }
 
+// ---- spinor-only staging: as k_dslash32s with 2 stages, but only the
+// neighbour spinor goes through shared memory (12 slots a stage); the link
+// is requested into L1 when the spinor copy is issued and read from there
+// (the lanes of one site read the same link: one request).  A thread needs
+// 384 B of shared memory instead of 480, and the launch bound of 512/BD
+// blocks caps it at 128 registers: 16 resident warps per SM against 14 for
+// the link-staging kernel (0.275 vs 0.317 ms at 48x24^3, 12 RHS).
+constexpr int kSlotT = 12;
+
+template <int LF>
+__device__ __forceinline__ void prefetch_link(const void *lk, long long Vh, long long lsite, int mu)
+{
+    if constexpr (LF == LINK_F32_12) {
+        prefetch3(static_cast<const float4 *>(lk) + (long long)mu * 3 * Vh + lsite, Vh * 16);
+    } else {
+        prefetch3(static_cast<const uint2 *>(lk) + (long long)mu * 3 * Vh + lsite, Vh * 8);
+        prefetch_l1(reinterpret_cast<const float *>(static_cast<const uint2 *>(lk) + 12 * Vh) +
+                    (long long)mu * Vh + lsite);
+    }
+}
+
+template <int LF, int MU, int SG>
+__device__ __forceinline__ void hop_smem_l1(C2 (&acc)[12], const float4 *sb, int bd, const void *lk,
+                                            long long Vh, long long lsite, float c)
+{
+    Cx<float> u[9];
+    load_link<LF, float>(lk, Vh, lsite, MU, u);
+    const f2 C = bc(c), MC = bc(-c);
+    C2 h[6];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        C2 q[4];
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++) {
+            const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(sb)[(sp * 3 + a) * bd];
+            q[sp] = {v.x, v.y};
+        }
+        project_pair<MU, SG>(q[0], q[1], q[2], q[3], h[a], h[3 + a]);
+    }
+    hop_apply<MU, SG>(acc, h, u, C, MC);
+}
+
+template <int LF, int BD, int D>
+__device__ __forceinline__ void tstep(C2 (&acc)[12], const float4 *mine, unsigned smine,
+                                      const int (&nbi)[8], const float4 *in, int P, long long cs,
+                                      const Nbr &nb, long long s, const void *lown, const void *loth,
+                                      long long Vh, const float (&hc)[8])
+{
+    constexpr int MU = D / 2;
+    constexpr int SLOT = (D % 2) * kSlotT * BD;
+    cp_async_wait<1>();
+    hop_smem_l1<LF, MU, (D & 1) ? +1 : -1>(acc, mine + SLOT, BD, (D & 1) ? loth : lown, Vh,
+                                           (D & 1) ? (long long)nb.b[MU] : s, hc[D]);
+    if constexpr (D + 2 < 8) {
+        constexpr int E = D + 2, ME = E / 2;
+        stage_spinor<BD>(smine + SLOT * 16, in + (long long)nbi[E] * P, cs * 16);
+        prefetch_link<LF>((E & 1) ? loth : lown, Vh, (E & 1) ? (long long)nb.b[ME] : s, ME);
+    }
+    cp_async_commit();
+}
+
+template <int LF, int EPI, int BD>
+__global__ void __launch_bounds__(BD, 512 / BD) k_dslash32t(const DslashParams p)
+{
+    extern __shared__ float4 sbuf[];
+    const Geom &g = p.g;
+    const int P = p.nrhs / 2;
+    const long long gid = (long long)blockIdx.x * BD + threadIdx.x;
+    const long long s = gid / P;
+    const int q0 = (int)(gid - s * P);
+    if (s >= g.Vh) return;
+    bool act[1];
+    act[0] = !p.active || p.active[2 * q0 * p.active_stride] || p.active[(2 * q0 + 1) * p.active_stride];
+    if (!act[0]) return;
+    const Nbr nb = neighbours(g, s, p.parity);
+    const long long cs = g.Vh * P;
+    const float4 *in = static_cast<const float4 *>(p.in) + q0;
+    const int grp = p.grp_of[2 * q0];
+    const void *lown = p.links[p.parity], *loth = p.links[1 - p.parity];
+    const long long Vh = g.Vh;
+    const float4 *mine = sbuf + threadIdx.x;
+    const unsigned smine = (unsigned)__cvta_generic_to_shared(mine);
+    const int nbi[8] = {nb.f[0], nb.b[0], nb.f[1], nb.b[1], nb.f[2], nb.b[2], nb.f[3], nb.b[3]};
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+        stage_spinor<BD>(smine + d * kSlotT * BD * 16, in + (long long)nbi[d] * P, cs * 16);
+        prefetch_link<LF>((d & 1) ? loth : lown, Vh, (d & 1) ? (long long)nb.b[0] : s, 0);
+        cp_async_commit();
+    }
+    {
+        const float4 *cl = static_cast<const float4 *>(p.clov[grp]) + s;
+#pragma unroll 1
+        for (int k = 0; k < 18; k++) prefetch_l1(cl + k * Vh);
+        if (EPI == EPI_XMY_AINV) {
+            const float4 *xin = static_cast<const float4 *>(p.x) + s * P + q0;
+#pragma unroll 1
+            for (int k = 0; k < 12; k++) prefetch_l1(xin + k * cs);
+        }
+    }
+    const float *ht = static_cast<const float *>(p.hop) + (long long)grp * 8 * g.Lmax;
+    const float hc[8] = {ht[0 * g.Lmax + nb.t], ht[1 * g.Lmax + nb.t], ht[2 * g.Lmax + nb.x],
+                         ht[3 * g.Lmax + nb.x], ht[4 * g.Lmax + nb.y], ht[5 * g.Lmax + nb.y],
+                         ht[6 * g.Lmax + nb.z], ht[7 * g.Lmax + nb.z]};
+    C2 acc[1][12];
+#pragma unroll
+    for (int j = 0; j < 12; j++) acc[0][j] = {0ull, 0ull};
+    tstep<LF, BD, 0>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    tstep<LF, BD, 1>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    tstep<LF, BD, 2>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    tstep<LF, BD, 3>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    tstep<LF, BD, 4>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    tstep<LF, BD, 5>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    tstep<LF, BD, 6>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    tstep<LF, BD, 7>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    finish32<EPI, 1>(p, acc, act, s, q0, grp, cs);
+}
+
 // ---- persistent staged variant: one wave of blocks, each thread walks the
 // (site, pair) items w, w + G, w + 2G, ... (G = threads in the grid) with two
 // stages; the next item's first two directions are copied while the current
@@ -855,12 +972,39 @@ cudaError_t launch32f(const DslashParams &p, int epi, int block, cudaStream_t st
     return cudaGetLastError();
 }
 
+template <int LF, int EPI, int BD>
+cudaError_t launch32t_k(const DslashParams &p, cudaStream_t st)
+{
+    constexpr int smem = 2 * kSlotT * BD * 16;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_dslash32t<LF, EPI, BD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
+    const long long threads = p.g.Vh * (p.nrhs / 2);
+    const unsigned grid = (unsigned)((threads + BD - 1) / BD);
+    k_dslash32t<LF, EPI, BD><<<grid, BD, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int LF, int EPI>
+cudaError_t launch32t(const DslashParams &p, int block, cudaStream_t st)
+{
+    switch (block) {
+    case 64: return launch32t_k<LF, EPI, 64>(p, st);
+    case 96: return launch32t_k<LF, EPI, 96>(p, st);
+    case 128: return launch32t_k<LF, EPI, 128>(p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int LF>
 cudaError_t launch32s_epi(const DslashParams &p, int epi, int block, int stages, int rpt,
                           cudaStream_t st)
 {
     (void)rpt;
     if (stages == 5) return launch32f<LF, 2>(p, epi, block, st);
+    if (stages == 6)
+        return epi == EPI_AINV ? launch32t<LF, EPI_AINV>(p, block, st)
+                               : launch32t<LF, EPI_XMY_AINV>(p, block, st);
     if (epi == EPI_AINV) return launch32s<LF, EPI_AINV>(p, block, stages, st);
     return launch32s<LF, EPI_XMY_AINV>(p, block, stages, st);
 }
@@ -883,7 +1027,7 @@ bool dslash_staged_ok(int prec, int link_fmt, int epi, int rpt, int stages, int 
         block % 32 == 0 && (epi == EPI_AINV || epi == EPI_XMY_AINV) &&
         (link_fmt == LINK_F32_12 || link_fmt == LINK_H16_12 || link_fmt == LINK_B16_12))
         return true;
-    return prec == 1 && rpt == 2 && stages >= 2 && stages <= 4 &&
+    return prec == 1 && rpt == 2 && ((stages >= 2 && stages <= 4) || stages == 6) &&
            (block == 64 || block == 96 || block == 128) &&
            (epi == EPI_AINV || epi == EPI_XMY_AINV) &&
            (link_fmt == LINK_F32_12 || link_fmt == LINK_H16_12 || link_fmt == LINK_B16_12);

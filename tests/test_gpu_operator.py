@@ -150,7 +150,7 @@ def test_invalid_arguments_are_errors(ctx):
 # threads leave a ragged last block on the 8x4x6x4 lattice (2304 pairs)
 SHAPES32 = [(2, 0, 64), (4, 0, 64), (2, 2, 64), (2, 3, 128), (2, 3, 96), (2, 2, 96),
             (4, 0, 256), (2, 0, 160), (2, 4, 64), (2, 4, 96), (2, 4, 128), (2, 5, 64),
-            (2, 5, 160), (2, 5, 128), (2, 5, 256)]
+            (2, 5, 160), (2, 5, 128), (2, 5, 256), (2, 6, 64), (2, 6, 96), (2, 6, 128)]
 
 
 @pytest.mark.parametrize("prec,tol,rpts", [("mixed_fp32", 1e-6, SHAPES32),
