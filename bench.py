@@ -846,7 +846,8 @@ def main():
     # autotuner launches of the A^-1 D kernel with all 12 RHS active, 12-real
     # FP32 links), per launch shape (threads per block, RHS per thread,
     # stages); valid only while the tuner picks a captured shape
-    captured = {(64, 2, 2): 1000676992, (96, 2, 2): 999261184, (64, 2, 5): 999319936}
+    captured = {(64, 2, 2): 1000676992, (96, 2, 2): 999261184, (64, 2, 5): 999319936,
+                (64, 2, 6): 1041893120, (128, 2, 6): 1039764992}
     traffic, traffic_note = None, "tuned shape has no ncu capture"
     shape = tuple(tuned.get("%s_n12" % args.prec, [0, 0, 0])[:3])
     if args.prec == "mixed_fp32" and shape in captured:

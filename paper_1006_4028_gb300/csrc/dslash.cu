@@ -596,7 +596,7 @@ __device__ __forceinline__ void pf_step(C2 (&acc)[1][12], const bool (&act)[1], 
 }
 
 template <int LF, int EPI, int DIST>
-__global__ void __launch_bounds__(256) k_dslash32f(const DslashParams p)
+__global__ void __launch_bounds__(256, 2) k_dslash32f(const DslashParams p)
 {
     const Geom &g = p.g;
     const int P = p.nrhs / 2;
@@ -685,13 +685,15 @@ template <int LF, int BD, int D>
 __device__ __forceinline__ void tstep(C2 (&acc)[12], const float4 *mine, unsigned smine,
                                       const int (&nbi)[8], const float4 *in, int P, long long cs,
                                       const Nbr &nb, long long s, const void *lown, const void *loth,
-                                      long long Vh, const float (&hc)[8])
+                                      long long Vh, const float *ht, int Lmax)
 {
     constexpr int MU = D / 2;
     constexpr int SLOT = (D % 2) * kSlotT * BD;
+    const int crd = MU == 0 ? nb.t : MU == 1 ? nb.x : MU == 2 ? nb.y : nb.z;
+    const float c = __ldg(ht + D * Lmax + crd);
     cp_async_wait<1>();
     hop_smem_l1<LF, MU, (D & 1) ? +1 : -1>(acc, mine + SLOT, BD, (D & 1) ? loth : lown, Vh,
-                                           (D & 1) ? (long long)nb.b[MU] : s, hc[D]);
+                                           (D & 1) ? (long long)nb.b[MU] : s, c);
     if constexpr (D + 2 < 8) {
         constexpr int E = D + 2, ME = E / 2;
         stage_spinor<BD>(smine + SLOT * 16, in + (long long)nbi[E] * P, cs * 16);
@@ -739,20 +741,17 @@ __global__ void __launch_bounds__(BD, 512 / BD) k_dslash32t(const DslashParams p
         }
     }
     const float *ht = static_cast<const float *>(p.hop) + (long long)grp * 8 * g.Lmax;
-    const float hc[8] = {ht[0 * g.Lmax + nb.t], ht[1 * g.Lmax + nb.t], ht[2 * g.Lmax + nb.x],
-                         ht[3 * g.Lmax + nb.x], ht[4 * g.Lmax + nb.y], ht[5 * g.Lmax + nb.y],
-                         ht[6 * g.Lmax + nb.z], ht[7 * g.Lmax + nb.z]};
     C2 acc[1][12];
 #pragma unroll
     for (int j = 0; j < 12; j++) acc[0][j] = {0ull, 0ull};
-    tstep<LF, BD, 0>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
-    tstep<LF, BD, 1>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
-    tstep<LF, BD, 2>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
-    tstep<LF, BD, 3>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
-    tstep<LF, BD, 4>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
-    tstep<LF, BD, 5>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
-    tstep<LF, BD, 6>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
-    tstep<LF, BD, 7>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, hc);
+    tstep<LF, BD, 0>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    tstep<LF, BD, 1>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    tstep<LF, BD, 2>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    tstep<LF, BD, 3>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    tstep<LF, BD, 4>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    tstep<LF, BD, 5>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    tstep<LF, BD, 6>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
+    tstep<LF, BD, 7>(acc[0], mine, smine, nbi, in, P, cs, nb, s, lown, loth, Vh, ht, g.Lmax);
     finish32<EPI, 1>(p, acc, act, s, q0, grp, cs);
 }
 
