@@ -349,8 +349,9 @@ dp_status dp_fit_correlator(const double *c, int T, int kind, int t0, int t1, do
  * threads walk several sites (staging needs 64, 96 or 128 threads per
  * block), 5 direct loads with an L1 prefetch 2 directions ahead, 6 the
  * spinor alone staged (2 in flight) with the link read from L1, 16 warps
- * per SM (64, 96 or 128 threads per block); all of 2-6 need FP32 or 16-bit
- * 12-real links and 2 RHS per thread.  -1: the tuned or default choice.
+ * per SM (64, 96 or 128 threads per block); all of 2-6 need 2 RHS per
+ * thread and FP32 or 16-bit 12-real links (6 also takes FP32 18-real
+ * links).  -1: the tuned or default choice.
  * FP32 needs nrhs even.  iters launches back to back; if ms_out is non-NULL
  * it receives the average launch time measured with CUDA events on the
  * context stream. */
@@ -385,6 +386,16 @@ dp_status dp_schur_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *
 dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int nrhs,
                       int *best_block_threads, int *best_rhs_per_thread, int *best_stages,
                       float *best_ms);
+
+/* Set the launch shape of the Schur dslash for (this field's volume, prec,
+ * link format from compress12, nrhs) without timing, e.g. a shape an earlier
+ * dp_autotune reported and the caller kept (a tune cache), so that a rerun
+ * (under a profiler, say) launches the same kernels.  The shape is checked
+ * as dp_dslash_dev checks an explicit one (stages 0 with rhs_per_thread 1, 2
+ * or 4 by precision, 2-6 for FP32 pairs); DP_ERR_INVALID_ARG if it cannot
+ * serve nrhs. */
+dp_status dp_tune_set(dp_ctx *ctx, dp_field field, int prec, int compress12, int nrhs,
+                      int block_threads, int rhs_per_thread, int stages);
 
 /* ---- per-kernel timing (CUDA events on the context stream) ---------------- */
 

@@ -27,7 +27,7 @@ __all__ = [
     "dp_field_load", "dp_field_set_csw", "dp_field_free",
     "dp_solve_point", "dp_solve_point_multi", "dp_solve_point_dev",
     "dp_solve_point_corr", "dp_solve_point_hl", "pcac_mass", "dp_effective_mass", "dp_fit_correlator", "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
-    "dp_autotune",
+    "dp_autotune", "dp_tune_set",
     "dp_timing_enable", "dp_timing_reset", "dp_timing_get", "dp_launch_count",
     "dp_serve_start", "dp_submit", "dp_wait", "dp_cancel", "dp_serve_stats_get", "dp_serve_stop",
     "PROFILE_KINDS", "PREC", "SOLVER", "APPLY", "STATUS", "MEFF_KINDS",
@@ -132,6 +132,7 @@ def load(build_if_missing=False):
         "dp_schur_dev": ([vp, up, dp, P(Profile), P(C.c_int * 4), ip, ip, ip, ip, vp, vp, ip], ip),
         "dp_dslash_dev": ([vp, up, dp, P(Profile), ip, ip, ip, vp, vp, ip, ip, ip, ip, ip,
                            P(C.c_float)], ip),
+        "dp_tune_set": ([vp, up, ip, ip, ip, ip, ip, ip], ip),
         "dp_autotune": ([vp, up, ip, ip, ip, P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_float)],
                         ip),
         "dp_timing_enable": ([vp, ip], ip),
@@ -502,6 +503,14 @@ def dp_autotune(ctx, field, prec, compress12, nrhs):
     _check(load().dp_autotune(ctx, int(field), p, int(compress12), int(nrhs), C.byref(b),
                               C.byref(rpt), C.byref(sg), C.byref(ms)))
     return b.value, rpt.value, sg.value, ms.value
+
+
+def dp_tune_set(ctx, field, prec, compress12, nrhs, block_threads, rhs_per_thread, stages):
+    """Set the Schur dslash launch shape for this volume, precision and RHS
+    count (e.g. from a tune cache) without timing."""
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check(load().dp_tune_set(ctx, int(field), p, int(compress12), int(nrhs), int(block_threads),
+                              int(rhs_per_thread), int(stages)))
 
 
 # ---- timing ----------------------------------------------------------------------

@@ -968,6 +968,42 @@ dp_status dp_autotune(dp_ctx *ctx, dp_field field, int prec, int compress12, int
     return DP_OK;
 }
 
+dp_status dp_tune_set(dp_ctx *ctx, dp_field field, int prec, int compress12, int nrhs,
+                      int block_threads, int rhs_per_thread, int stages)
+{
+    CTX_CHECK(ctx);
+    Ctx &c = ctx->c;
+    auto fp = find_field(&c, field);
+    if (!fp) {
+        set_error("unknown field");
+        return DP_ERR_NOT_FOUND;
+    }
+    if (nrhs < 1 || nrhs > kMaxRhs || prec < DP_PREC_FP64 || prec > DP_PREC_MIXED_BF16) {
+        set_error("dp_tune_set: invalid argument");
+        return DP_ERR_INVALID_ARG;
+    }
+    const int pr = prec == DP_PREC_FP64 ? 0 : 1;
+    const int lf = inner_link_format(prec, compress12);
+    const bool ok = block_threads > 0 && block_threads <= 256 && block_threads % 32 == 0 &&
+                    dslash_rpt_ok(nrhs, rhs_per_thread, pr, EPI_AINV) &&
+                    dslash_rpt_ok(nrhs, rhs_per_thread, pr, EPI_XMY_AINV) &&
+                    (stages == 0 || (dslash_staged_ok(pr, lf, EPI_AINV, rhs_per_thread, stages, block_threads) &&
+                                     dslash_staged_ok(pr, lf, EPI_XMY_AINV, rhs_per_thread, stages,
+                                                      block_threads)));
+    if (!ok) {
+        set_error("dp_tune_set: shape (%d threads, %d RHS per thread, stages %d) cannot serve %d RHS here",
+                  block_threads, rhs_per_thread, stages, nrhs);
+        return DP_ERR_INVALID_ARG;
+    }
+    Shape sh;
+    sh.block = block_threads;
+    sh.rpt = rhs_per_thread;
+    sh.stages = stages;
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.tuned[TuneKey{fp->g.Vh, pr, lf, nrhs}] = sh;
+    return DP_OK;
+}
+
 dp_status dp_timing_enable(dp_ctx *ctx, int on)
 {
     CTX_CHECK(ctx);

@@ -653,6 +653,11 @@ __device__ __forceinline__ void prefetch_link(const void *lk, long long Vh, long
 {
     if constexpr (LF == LINK_F32_12) {
         prefetch3(static_cast<const float4 *>(lk) + (long long)mu * 3 * Vh + lsite, Vh * 16);
+    } else if constexpr (LF == LINK_F32_18) {
+        const float2 *l = static_cast<const float2 *>(lk) + (long long)mu * 9 * Vh + lsite;
+        prefetch3(l, Vh * 8);
+        prefetch3(l + 3 * Vh, Vh * 8);
+        prefetch3(l + 6 * Vh, Vh * 8);
     } else {
         prefetch3(static_cast<const uint2 *>(lk) + (long long)mu * 3 * Vh + lsite, Vh * 8);
         prefetch_l1(reinterpret_cast<const float *>(static_cast<const uint2 *>(lk) + 12 * Vh) +
@@ -1026,6 +1031,9 @@ bool dslash_staged_ok(int prec, int link_fmt, int epi, int rpt, int stages, int 
         block % 32 == 0 && (epi == EPI_AINV || epi == EPI_XMY_AINV) &&
         (link_fmt == LINK_F32_12 || link_fmt == LINK_H16_12 || link_fmt == LINK_B16_12))
         return true;
+    if (prec == 1 && rpt == 2 && stages == 6 && (block == 64 || block == 96 || block == 128) &&
+        (epi == EPI_AINV || epi == EPI_XMY_AINV) && link_fmt == LINK_F32_18)
+        return true;
     return prec == 1 && rpt == 2 && ((stages >= 2 && stages <= 4) || stages == 6) &&
            (block == 64 || block == 96 || block == 128) &&
            (epi == EPI_AINV || epi == EPI_XMY_AINV) &&
@@ -1052,6 +1060,9 @@ cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi
     }
     if (stages > 0) {
         if (!dslash_staged_ok(prec, link_fmt, epi, rpt, stages, block)) return cudaErrorInvalidValue;
+        if (link_fmt == LINK_F32_18)  // spinor staging only (stages == 6)
+            return epi == EPI_AINV ? launch32t<LINK_F32_18, EPI_AINV>(p, block, st)
+                                   : launch32t<LINK_F32_18, EPI_XMY_AINV>(p, block, st);
         if (link_fmt == LINK_F32_12) return launch32s_epi<LINK_F32_12>(p, epi, block, stages, rpt, st);
         if (link_fmt == LINK_H16_12) return launch32s_epi<LINK_H16_12>(p, epi, block, stages, rpt, st);
         return launch32s_epi<LINK_B16_12>(p, epi, block, stages, rpt, st);

@@ -153,9 +153,14 @@ SHAPES32 = [(2, 0, 64), (4, 0, 64), (2, 2, 64), (2, 3, 128), (2, 3, 96), (2, 2, 
             (2, 5, 160), (2, 5, 128), (2, 5, 256), (2, 6, 64), (2, 6, 96), (2, 6, 128)]
 
 
-@pytest.mark.parametrize("prec,tol,rpts", [("mixed_fp32", 1e-6, SHAPES32),
-                                           ("fp64", 1e-13, [(1, 0, 64), (1, 0, 160)])])
-def test_schur_launch_all_rhs_per_thread(ctx, setup, prec, tol, rpts):
+# 18-real FP32 links: the direct kernels and the spinor-staged one
+SHAPES32_18 = [(2, 0, 64), (2, 6, 64), (2, 6, 96), (2, 6, 128), (4, 0, 64)]
+
+
+@pytest.mark.parametrize("prec,tol,rpts,c12", [("mixed_fp32", 1e-6, SHAPES32, 1),
+                                               ("mixed_fp32", 1e-6, SHAPES32_18, 0),
+                                               ("fp64", 1e-13, [(1, 0, 64), (1, 0, 160)], 1)])
+def test_schur_launch_all_rhs_per_thread(ctx, setup, prec, tol, rpts, c12):
     """out_e = A_ee^-1 D_eo psi_o on packed device spinors (the solver's launch),
     for every launch shape (RHS per thread, staging, block): bit-identical to
     each other and, through A_ee out_e = D_eo psi_o, equal to the oracle."""
@@ -187,7 +192,7 @@ def test_schur_launch_all_rhs_per_thread(ctx, setup, prec, tol, rpts):
     outs = []
     for r, stages, block in rpts:
         out = torch.zeros_like(xin)
-        dp.dp_dslash_dev(ctx, f, M, prof, prec, 1, 0, xin.data_ptr(), out.data_ptr(), 12,
+        dp.dp_dslash_dev(ctx, f, M, prof, prec, c12, 0, xin.data_ptr(), out.data_ptr(), 12,
                          block, r, 1, stages=stages)
         torch.cuda.synchronize()
         outs.append(host(out))
@@ -235,3 +240,26 @@ def test_dirichlet_time_boundary_operator(ctx, prec, tol):
     got = dp.dp_apply(ctx, f, "full", 0.2, prof[:2], prof[2], prec, psi)
     assert per_site_rel(got, op.apply(psi, 0.2, prof)) < tol
     dp.dp_field_free(ctx, f)
+
+
+def test_tune_set_fixes_the_launch_shape(ctx, setup):
+    """A shape set with dp_tune_set is the one the tuned-or-default launch
+    uses (bit-identical to the explicit launch); shapes that cannot serve the
+    RHS count are refused."""
+    torch = pytest.importorskip("torch")
+    dims, f, op, _ = setup
+    nb = dp.dp_spinor_bytes(ctx, f, "mixed_fp32", 12)
+    a = torch.randn(nb // 4, device="cuda")
+    explicit, tuned = torch.zeros_like(a), torch.zeros_like(a)
+    for shape in [(128, 2, 6), (64, 2, 2), (64, 4, 0)]:
+        dp.dp_tune_set(ctx, f, "mixed_fp32", 1, 12, *shape)
+        dp.dp_dslash_dev(ctx, f, 0.3, ("cosh_t", 0.4), "mixed_fp32", 1, 0, a.data_ptr(),
+                         explicit.data_ptr(), 12, shape[0], shape[1], 1, stages=shape[2])
+        dp.dp_dslash_dev(ctx, f, 0.3, ("cosh_t", 0.4), "mixed_fp32", 1, 0, a.data_ptr(),
+                         tuned.data_ptr(), 12, 0, 0, 1, stages=-1)
+        torch.cuda.synchronize()
+        assert torch.equal(explicit, tuned)
+    for bad in [(100, 2, 6), (64, 1, 0), (64, 2, 7), (256, 2, 6)]:
+        with pytest.raises(dp.DpError):
+            dp.dp_tune_set(ctx, f, "mixed_fp32", 1, 12, *bad)
+    dp.dp_autotune(ctx, f, "mixed_fp32", 1, 12)
