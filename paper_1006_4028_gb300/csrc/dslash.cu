@@ -713,9 +713,10 @@ __global__ void __launch_bounds__(BD, 512 / BD) k_dslash32t(const DslashParams p
     extern __shared__ float4 sbuf[];
     const Geom &g = p.g;
     const int P = p.nrhs / 2;
-    const long long gid = (long long)blockIdx.x * BD + threadIdx.x;
-    const long long s = gid / P;
-    const int q0 = (int)(gid - s * P);
+    // 32-bit division: the launcher keeps Vh * P below 2^32
+    const unsigned gid = blockIdx.x * BD + threadIdx.x;
+    const long long s = gid / (unsigned)P;
+    const int q0 = (int)(gid - (unsigned)s * (unsigned)P);
     if (s >= g.Vh) return;
     bool act[1];
     act[0] = !p.active || p.active[2 * q0 * p.active_stride] || p.active[(2 * q0 + 1) * p.active_stride];
@@ -984,6 +985,7 @@ cudaError_t launch32t_k(const DslashParams &p, cudaStream_t st)
         k_dslash32t<LF, EPI, BD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (attr != cudaSuccess) return attr;
     const long long threads = p.g.Vh * (p.nrhs / 2);
+    if (threads + BD >= (1ll << 32)) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)((threads + BD - 1) / BD);
     k_dslash32t<LF, EPI, BD><<<grid, BD, smem, st>>>(p);
     return cudaGetLastError();
