@@ -263,3 +263,46 @@ def test_tune_set_fixes_the_launch_shape(ctx, setup):
         with pytest.raises(dp.DpError):
             dp.dp_tune_set(ctx, f, "mixed_fp32", 1, 12, *bad)
     dp.dp_autotune(ctx, f, "mixed_fp32", 1, 12)
+
+
+def test_full_size_48x24_schur_launch_in_the_benchmark_shape(ctx):
+    """The benchmark's launch at its full size: 48x24^3 heavy-quark lattice
+    (eps = 0.3, seed 1, c_sw = 1.7, M = 0.5, cosh alpha0 = 0.4), 12 RHS in
+    the spinor-staged kernel with 128 threads (the tuned shape),
+    out_e = A_ee^-1 D_eo psi_o, checked through A_ee out_e = D_eo psi_o at
+    every even site against the oracle (hop and clover terms), and
+    bit-identical to the direct kernel."""
+    torch = pytest.importorskip("torch")
+    dims = (48, 24, 24, 24)
+    U = li.su3_links(dims, 0.3, 1)
+    f = dp.dp_field_load(ctx, U, dims, -1)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    M, prof = 0.5, ("cosh_t", 0.4)
+    psi = li.random_spinor(dims, 12, 33)
+    ev, od = dp.pack_half_spinors(psi, dims)
+    del psi
+    Vh = ev.shape[1]
+    pr = od.reshape(12, Vh, 6, 2)
+    b = np.stack([pr.real[..., 0], pr.real[..., 1], pr.imag[..., 0], pr.imag[..., 1]], -1)
+    xin = torch.from_numpy(np.ascontiguousarray(b.astype(np.float32))).cuda()
+    del b, pr
+    outs = []
+    for block, rpt, stages in [(128, 2, 6), (64, 2, 0)]:
+        out = torch.zeros_like(xin)
+        dp.dp_dslash_dev(ctx, f, M, prof, "mixed_fp32", 1, 0, xin.data_ptr(), out.data_ptr(), 12,
+                         block, rpt, 1, stages=stages)
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+    o = outs[0].reshape(12, Vh, 6, 4).astype(np.float64)
+    got = np.stack([o[..., 0] + 1j * o[..., 2], o[..., 1] + 1j * o[..., 3]], -1).reshape(12, Vh, 12)
+    del outs, o
+    full_out = dp.unpack_half_spinors(got, np.zeros_like(got), dims)
+    psi_odd = dp.unpack_half_spinors(np.zeros_like(od), od, dims)
+    op = oracle.WilsonClover(U, dims, 1.7, -1)
+    lhs = (4 + M) * full_out + op.clover(full_out)
+    rhs = op.hop(psi_odd, (prof[0], prof[1], (0, 0, 0, 0)))
+    t, z, y, x = np.indices(oracle.array_shape(dims))
+    even = ((t + x + y + z) % 2) == 0
+    assert per_site_rel(lhs[:, even], rhs[:, even]) < 1e-5
+    dp.dp_field_free(ctx, f)
