@@ -737,10 +737,12 @@ __global__ void __launch_bounds__(BD, 512 / BD) k_dslash32t(const DslashParams p
         cp_async_commit();
     }
     {
-        const float4 *cl = static_cast<const float4 *>(p.clov[grp]) + s;
+        if (EPI != EPI_XMY_G5) {
+            const float4 *cl = static_cast<const float4 *>(p.clov[grp]) + s;
 #pragma unroll 1
-        for (int k = 0; k < 18; k++) prefetch_l1(cl + k * Vh);
-        if (EPI == EPI_XMY_AINV) {
+            for (int k = 0; k < 18; k++) prefetch_l1(cl + k * Vh);
+        }
+        if (EPI == EPI_XMY_AINV || EPI == EPI_XMY_G5) {
             const float4 *xin = static_cast<const float4 *>(p.x) + s * P + q0;
 #pragma unroll 1
             for (int k = 0; k < 12; k++) prefetch_l1(xin + k * cs);
@@ -1009,8 +1011,9 @@ cudaError_t launch32s_epi(const DslashParams &p, int epi, int block, int stages,
     (void)rpt;
     if (stages == 5) return launch32f<LF, 2>(p, epi, block, st);
     if (stages == 6)
-        return epi == EPI_AINV ? launch32t<LF, EPI_AINV>(p, block, st)
-                               : launch32t<LF, EPI_XMY_AINV>(p, block, st);
+        return epi == EPI_AINV       ? launch32t<LF, EPI_AINV>(p, block, st)
+               : epi == EPI_XMY_G5 ? launch32t<LF, EPI_XMY_G5>(p, block, st)
+                                   : launch32t<LF, EPI_XMY_AINV>(p, block, st);
     if (epi == EPI_AINV) return launch32s<LF, EPI_AINV>(p, block, stages, st);
     return launch32s<LF, EPI_XMY_AINV>(p, block, stages, st);
 }
@@ -1034,7 +1037,7 @@ bool dslash_staged_ok(int prec, int link_fmt, int epi, int rpt, int stages, int 
         (link_fmt == LINK_F32_12 || link_fmt == LINK_H16_12 || link_fmt == LINK_B16_12))
         return true;
     if (prec == 1 && rpt == 2 && stages == 6 && (block == 64 || block == 96 || block == 128) &&
-        (epi == EPI_AINV || epi == EPI_XMY_AINV) && link_fmt == LINK_F32_18)
+        (epi == EPI_AINV || epi == EPI_XMY_AINV || epi == EPI_XMY_G5) && link_fmt == LINK_F32_18)
         return true;
     return prec == 1 && rpt == 2 && ((stages >= 2 && stages <= 4) || stages == 6) &&
            (block == 64 || block == 96 || block == 128) &&
@@ -1063,8 +1066,9 @@ cudaError_t launch_dslash(const DslashParams &p, int prec, int link_fmt, int epi
     if (stages > 0) {
         if (!dslash_staged_ok(prec, link_fmt, epi, rpt, stages, block)) return cudaErrorInvalidValue;
         if (link_fmt == LINK_F32_18)  // spinor staging only (stages == 6)
-            return epi == EPI_AINV ? launch32t<LINK_F32_18, EPI_AINV>(p, block, st)
-                                   : launch32t<LINK_F32_18, EPI_XMY_AINV>(p, block, st);
+            return epi == EPI_AINV       ? launch32t<LINK_F32_18, EPI_AINV>(p, block, st)
+                   : epi == EPI_XMY_G5 ? launch32t<LINK_F32_18, EPI_XMY_G5>(p, block, st)
+                                       : launch32t<LINK_F32_18, EPI_XMY_AINV>(p, block, st);
         if (link_fmt == LINK_F32_12) return launch32s_epi<LINK_F32_12>(p, epi, block, stages, rpt, st);
         if (link_fmt == LINK_H16_12) return launch32s_epi<LINK_H16_12>(p, epi, block, stages, rpt, st);
         return launch32s_epi<LINK_B16_12>(p, epi, block, stages, rpt, st);

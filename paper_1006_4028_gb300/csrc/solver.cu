@@ -74,8 +74,11 @@ dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void
     c->time_begin(name, &ev);
     const bool schur = epi == EPI_AINV || epi == EPI_XMY_AINV;
     const int rpt = schur ? op.rpt : (op.pr == 0 ? 1 : 2);
+    // the Schur launches take the tuned shape; the adjoint's x - g5 D launch
+    // (CGNE) too when that shape is the spinor-staged kernel
+    const bool shaped = schur || (epi == EPI_XMY_G5 && op.stages == 6);
     const int stages =
-        schur && dslash_staged_ok(op.pr, op.lf, epi, rpt, op.stages, op.block) ? op.stages : 0;
+        shaped && dslash_staged_ok(op.pr, op.lf, epi, rpt, op.stages, op.block) ? op.stages : 0;
     CK(launch_dslash(P, op.pr, op.lf, epi, op.block, rpt, c->stream, stages));
     c->time_end(name, ev);
     c->launches++;

@@ -282,3 +282,24 @@ def test_effective_mass_fit_of_solved_free_correlator(ctx):
     mo, _, _ = oracle.fit_correlator(exact, "cosh", 4, 12)
     assert abs(m - mo) < 1e-6
     dp.dp_field_free(ctx, f)
+
+
+@pytest.mark.parametrize("opts", [MIXED, CGNE_MIXED, SAP_GCR])
+@pytest.mark.parametrize("shape", [(128, 2, 6), (96, 2, 6)])
+def test_solvers_on_the_spinor_staged_kernel(ctx, opts, shape):
+    """BiCGStab, CGNE (whose adjoint's x - g5 D launch also runs on it) and
+    SAP+GCR with the tuned shape forced to the spinor-staged kernel, on a
+    6x4x6x6 lattice whose 2592 pair-threads leave a ragged last block:
+    C_PP against the oracle."""
+    dims = (6, 4, 6, 6)
+    U = field(dims, 0.3, 5)
+    f = dp.dp_field_load(ctx, U, dims, -1)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    op = oracle.WilsonClover(U, dims, 1.7, -1)
+    src = (1, 0, 2, 3)
+    ref, _, _ = oracle.solve_point(op, 0.5, "cosh_t", 0.4, src, tol=1e-13)
+    dp.dp_tune_set(ctx, f, "mixed_fp32", 1, 12, *shape)
+    cpp, _, info = dp.dp_solve_point(ctx, f, 0.5, ("cosh_t", 0.4), src, 1e-10, opts, T=6)
+    assert info["status"] == 0 and info["true_rel_residue"] < 1e-10
+    assert slice_rel(cpp, ref, 3) < 1e-6
+    dp.dp_field_free(ctx, f)
