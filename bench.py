@@ -45,6 +45,8 @@ WORKLOAD = {
     "residue": 1e-11,
     "rhs_per_solve": 12,
 }
+# per-run state of the benchmark (clock samples, the tune cache); git-ignored
+STATE = os.environ.get("DP_BENCH_STATE", os.path.join(ROOT, ".bench_state"))
 DIMS = (48, 24, 24, 24)
 EPS, SEED, CSW, MASS, ALPHA0, RES = 0.3, 1, 1.7, 0.5, 0.4, 1e-11
 METRIC = "Precond. Wilson-clover solves/s & dslash HBM GB/s vs FP64 plain; p99 latency"
@@ -117,7 +119,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        self.path = os.path.join(STATE, "bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
@@ -715,7 +717,7 @@ def main():
                     choices=["heavy48", "free16", "light64", "multimass32", "serve", "sf48"],
                     help="heavy48: the headline solves/s line (default); the others run the "
                          "study's other workloads and print their own JSON line")
-    ap.add_argument("--tune-cache", default=os.path.join(ROOT, "gpurun_out", "tunecache.json"),
+    ap.add_argument("--tune-cache", default=os.path.join(STATE, "tunecache.json"),
                     help="launch shapes kept between runs of a workload ('none': always tune)")
     ap.add_argument("--graphs", type=int, default=1,
                     help="capture solver iterations as CUDA graphs in the timed region (the "
