@@ -303,3 +303,25 @@ def test_solvers_on_the_spinor_staged_kernel(ctx, opts, shape):
     assert info["status"] == 0 and info["true_rel_residue"] < 1e-10
     assert slice_rel(cpp, ref, 3) < 1e-6
     dp.dp_field_free(ctx, f)
+
+
+def test_full_size_48x24_solve_matches_stored_oracle(ctx):
+    """The benchmark's solve at its full size: 48x24^3 heavy-quark workload,
+    point source at the origin, r = 1e-11, FP32 inner BiCGStab on the
+    spinor-staged kernel (the tuned shape) in the FP64 outer loop; C_PP per
+    time slice out to T/2 against the oracle's stored r = 1e-13 result
+    (tests/golden/cpp_48x24_M0.5_cosh0.4.json, written by make_golden.py)."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "cpp_48x24_M0.5_cosh0.4.json")))
+    dims = tuple(g["dims"])
+    f = dp.dp_field_load(ctx, li.su3_links(dims, g["eps"], g["seed"]), dims, g["bc_t"])
+    dp.dp_field_set_csw(ctx, f, g["csw"])
+    dp.dp_tune_set(ctx, f, "mixed_fp32", 1, 12, 128, 2, 6)
+    cpp, _, info = dp.dp_solve_point(ctx, f, g["M"], (g["profile"], g["alpha0"]), tuple(g["src"]),
+                                     1e-11, MIXED, T=dims[0])
+    assert info["status"] == 0 and info["true_rel_residue"] < 1e-11
+    assert slice_rel(cpp, g["cpp"], dims[0] // 2) < 1e-6
+    dp.dp_field_free(ctx, f)
