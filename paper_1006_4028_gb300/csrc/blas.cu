@@ -472,7 +472,7 @@ cudaError_t blas_bicg_init(BlasCtx &bc, int prec, const void *b, void *r, void *
 cudaError_t blas_bicg_p(BlasCtx &bc, int prec, const void *r, void *p, const void *v,
                         long long Vh, int nrhs, const RhsState *st, int first, cudaStream_t s)
 {
-    if (prec != 0) return blas32_p(bc, r, p, v, Vh, nrhs, st, first, s);
+    if (prec != 0) return cudaErrorInvalidValue;  // FP32: the p update rides in blas32_update_p
     const Cfg c = cfg_wave(bc, k_bicg_p, Vh, nrhs);
     k_bicg_p<<<c.grid, c.block, 0, s>>>(c, r, p, v, Vh, nrhs, st, first);
     return cudaGetLastError();
@@ -499,7 +499,7 @@ cudaError_t blas_bicg_s(BlasCtx &bc, int prec, const void *r, const void *v, voi
 cudaError_t blas_bicg_omega(BlasCtx &bc, int prec, const void *t, const void *sv,
                             long long Vh, int nrhs, RhsState *st, cudaStream_t s)
 {
-    if (prec != 0) return blas32_omega(bc, t, sv, Vh, nrhs, st, s);
+    if (prec != 0) return cudaErrorInvalidValue;  // FP32: blas32_omega_rho
     const Cfg c = cfg_wave(bc, k_bicg_omega, Vh, nrhs);
     k_bicg_omega<<<c.grid, c.block, 0, s>>>(c, t, sv, Vh, nrhs, st, bc.partials, bc.counter);
     return cudaGetLastError();
@@ -511,7 +511,7 @@ cudaError_t blas_bicg_update(BlasCtx &bc, int prec, void *x, void *r, const void
 {
     cudaError_t e;
     if (prec != 0) {
-        e = blas32_update(bc, x, r, p, sv, t, rhat, Vh, nrhs, st, max_iter, s);
+        return cudaErrorInvalidValue;  // FP32: blas32_update_p
     } else {
         const Cfg c = cfg_wave(bc, k_bicg_update, Vh, nrhs);
         k_bicg_update<<<c.grid, c.block, 0, s>>>(c, x, r, p, sv, t, rhat, Vh, nrhs, st, max_iter,

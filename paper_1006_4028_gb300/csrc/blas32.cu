@@ -93,27 +93,6 @@ __device__ __forceinline__ void add_lanes(double &d0, double &d1, f2 v, bool a0,
     for (long long s = (long long)blockIdx.x * c.lanes + lane; (a0 || a1) && s < Vh; \
          s += (long long)gridDim.x * c.lanes)
 
-__global__ void __launch_bounds__(kMaxBlock) k32_p(Cfg c, const void *rv, void *pv, const void *vv, long long Vh, int nrhs,
-                      const RhsState *st, int first)
-{
-    const int qq = threadIdx.x % (nrhs / 2);
-    const C2 be = lanes(st[2 * qq].beta, st[2 * qq + 1].beta);
-    const C2 mom = neg(lanes(st[2 * qq].omega, st[2 * qq + 1].omega));
-    PAIR_LOOP
-    {
-        const long long me = s * P + q;
-        P12 r = ldp(rv, cs, me);
-        if (first) {
-            stp(pv, cs, me, r);
-            continue;
-        }
-        P12 p = ldp(pv, cs, me), v = ldp(vv, cs, me);
-#pragma unroll
-        for (int k = 0; k < 12; k++) p.c[k] = c2_lanefma(be, c2_lanefma(mom, v.c[k], p.c[k]), r.c[k]);
-        stp(pv, cs, me, p);
-    }
-}
-
 __global__ void __launch_bounds__(kMaxBlock) k32_alpha(Cfg c, const void *rh, const void *vv, long long Vh, int nrhs,
                           RhsState *st, double *partials, unsigned int *counter)
 {
@@ -151,82 +130,8 @@ __global__ void __launch_bounds__(kMaxBlock) k32_s(Cfg c, const void *rv, const 
     }
 }
 
-__global__ void __launch_bounds__(kMaxBlock) k32_omega(Cfg c, const void *tv, const void *sv, long long Vh, int nrhs,
-                          RhsState *st, double *partials, unsigned int *counter)
-{
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    {
-        f2 sum0 = 0ull, sum1 = 0ull, sum2 = 0ull;
-        PAIR_LOOP
-        {
-            const long long me = s * P + q;
-            const P12 t = ldp(tv, cs, me), sx = ldp(sv, cs, me);
-            const C2 d = pdot(t, sx);
-            sum0 = fadd2(sum0, d.re);
-            sum1 = fadd2(sum1, d.im);
-            sum2 = fadd2(sum2, pnorm(t));
-        }
-        add_lanes(acc[0], acc[3], sum0, a0, a1);
-        add_lanes(acc[1], acc[4], sum1, a0, a1);
-        add_lanes(acc[2], acc[5], sum2, a0, a1);
-    }
-    const int q = threadIdx.x % (nrhs / 2);
-    if (!reduce_last<3, 2>(acc, c, partials, counter, nrhs / 2)) return;
-    finish_omega(st[2 * q], acc[0], acc[1], acc[2]);
-    finish_omega(st[2 * q + 1], acc[3], acc[4], acc[5]);
-}
-
 // keep the lanes of `old` whose RHS is inactive
 __device__ __forceinline__ f2 blend(f2 nw, f2 old, f2 m) { return (nw & m) | (old & ~m); }
-
-// one component at a time: five streams in, two out, few live registers
-__global__ void __launch_bounds__(kMaxBlock)
-k32_update(Cfg c, void *xv, void *rv, const void *pv, const void *sv, const void *tv,
-           const void *rh, long long Vh, int nrhs, RhsState *st, int max_iter, double *partials,
-           unsigned int *counter)
-{
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    {
-        const int qq = threadIdx.x % (nrhs / 2);
-        const C2 al = lanes(st[2 * qq].alpha, st[2 * qq + 1].alpha);
-        const C2 om = lanes(st[2 * qq].omega, st[2 * qq + 1].omega);
-        const C2 mom = neg(om);
-        f2 sum0 = 0ull, sum1 = 0ull, sum2 = 0ull;
-        PAIR_LOOP
-        {
-            const long long me = s * P + q;
-            const f2 m = (a0 ? 0x00000000ffffffffull : 0ull) | (a1 ? 0xffffffff00000000ull : 0ull);
-            f2 dre = 0ull, dim = 0ull, nn = 0ull;
-#pragma unroll
-            for (int k = 0; k < 12; k++) {
-                const C2 x = ld1(xv, cs, me, k), p = ld1(pv, cs, me, k), sx = ld1(sv, cs, me, k);
-                const C2 t = ld1(tv, cs, me, k), h = ld1(rh, cs, me, k);
-                C2 xn = c2_lanefma(om, sx, c2_lanefma(al, p, x));
-                xn.re = blend(xn.re, x.re, m);
-                xn.im = blend(xn.im, x.im, m);
-                st1(xv, cs, me, k, xn);
-                const C2 r = c2_lanefma(mom, t, sx);
-                st1(rv, cs, me, k, r);
-                dre = ffma2(h.re, r.re, dre);
-                dre = ffma2(h.im, r.im, dre);
-                dim = ffma2(h.re, r.im, dim);
-                dim = ffma2(fneg2(h.im), r.re, dim);
-                nn = ffma2(r.re, r.re, nn);
-                nn = ffma2(r.im, r.im, nn);
-            }
-            sum0 = fadd2(sum0, dre);
-            sum1 = fadd2(sum1, dim);
-            sum2 = fadd2(sum2, nn);
-        }
-        add_lanes(acc[0], acc[3], sum0, a0, a1);
-        add_lanes(acc[1], acc[4], sum1, a0, a1);
-        add_lanes(acc[2], acc[5], sum2, a0, a1);
-    }
-    const int q = threadIdx.x % (nrhs / 2);
-    if (!reduce_last<3, 2>(acc, c, partials, counter, nrhs / 2)) return;
-    finish_update(st[2 * q], acc[0], acc[1], acc[2], max_iter);
-    finish_update(st[2 * q + 1], acc[3], acc[4], acc[5], max_iter);
-}
 
 __global__ void __launch_bounds__(kMaxBlock) k32_init(Cfg c, const void *bv, void *rv, void *rh, void *pv,
                                                       long long Vh, int nrhs, RhsState *st,
@@ -716,15 +621,6 @@ cudaError_t blas32_update_p(BlasCtx &bc, void *x, void *r, void *p, const void *
     return blas_count_active(bc, st, nrhs, s);
 }
 
-cudaError_t blas32_p(BlasCtx &bc, const void *r, void *p, const void *v, long long Vh, int nrhs,
-                     const RhsState *st, int first, cudaStream_t s)
-{
-    if (nrhs % 2) return cudaErrorInvalidValue;
-    const Cfg c = cfg_wave(bc, k32_p, Vh, nrhs / 2);
-    k32_p<<<c.grid, c.block, 0, s>>>(c, r, p, v, Vh, nrhs, st, first);
-    return cudaGetLastError();
-}
-
 cudaError_t blas32_alpha(BlasCtx &bc, const void *rh, const void *v, long long Vh, int nrhs,
                          RhsState *st, cudaStream_t s)
 {
@@ -740,26 +636,6 @@ cudaError_t blas32_s(BlasCtx &bc, const void *r, const void *v, void *sv, long l
     if (nrhs % 2) return cudaErrorInvalidValue;
     const Cfg c = cfg_wave(bc, k32_s, Vh, nrhs / 2);
     k32_s<<<c.grid, c.block, 0, s>>>(c, r, v, sv, Vh, nrhs, st);
-    return cudaGetLastError();
-}
-
-cudaError_t blas32_omega(BlasCtx &bc, const void *t, const void *sv, long long Vh, int nrhs,
-                         RhsState *st, cudaStream_t s)
-{
-    if (nrhs % 2) return cudaErrorInvalidValue;
-    const Cfg c = cfg_wave(bc, k32_omega, Vh, nrhs / 2);
-    k32_omega<<<c.grid, c.block, 0, s>>>(c, t, sv, Vh, nrhs, st, bc.partials, bc.counter);
-    return cudaGetLastError();
-}
-
-cudaError_t blas32_update(BlasCtx &bc, void *x, void *r, const void *p, const void *sv,
-                          const void *t, const void *rh, long long Vh, int nrhs, RhsState *st,
-                          int max_iter, cudaStream_t s)
-{
-    if (nrhs % 2) return cudaErrorInvalidValue;
-    const Cfg c = cfg_wave(bc, k32_update, Vh, nrhs / 2);
-    k32_update<<<c.grid, c.block, 0, s>>>(c, x, r, p, sv, t, rh, Vh, nrhs, st, max_iter,
-                                          bc.partials, bc.counter);
     return cudaGetLastError();
 }
 

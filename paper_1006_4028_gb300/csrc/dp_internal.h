@@ -211,6 +211,8 @@ struct BlasCtx {
 cudaError_t blas_bicg_init(BlasCtx &bc, int prec, const void *b, void *r, void *rhat, void *p,
                            void *v, void *x, long long Vh, int nrhs, RhsState *st, double tol,
                            cudaStream_t s);
+// p, omega and update: FP64 only (the FP32 solver uses blas32_omega_rho and
+// blas32_update_p, which carry the p update); alpha and s: both precisions
 cudaError_t blas_bicg_p(BlasCtx &bc, int prec, const void *r, void *p, const void *v,
                         long long Vh, int nrhs, const RhsState *st, int first, cudaStream_t s);
 cudaError_t blas_bicg_alpha(BlasCtx &bc, int prec, const void *rhat, const void *v,
@@ -235,17 +237,10 @@ cudaError_t blas32_omega_rho(BlasCtx &bc, const void *t, const void *sv, const v
 cudaError_t blas32_update_p(BlasCtx &bc, void *x, void *r, void *p, const void *sv, const void *t,
                             const void *v, long long Vh, int nrhs, RhsState *st, int max_iter,
                             cudaStream_t s);
-cudaError_t blas32_p(BlasCtx &bc, const void *r, void *p, const void *v, long long Vh, int nrhs,
-                     const RhsState *st, int first, cudaStream_t s);
 cudaError_t blas32_alpha(BlasCtx &bc, const void *rh, const void *v, long long Vh, int nrhs,
                          RhsState *st, cudaStream_t s);
 cudaError_t blas32_s(BlasCtx &bc, const void *r, const void *v, void *sv, long long Vh, int nrhs,
                      const RhsState *st, cudaStream_t s);
-cudaError_t blas32_omega(BlasCtx &bc, const void *t, const void *sv, long long Vh, int nrhs,
-                         RhsState *st, cudaStream_t s);
-cudaError_t blas32_update(BlasCtx &bc, void *x, void *r, const void *p, const void *sv,
-                          const void *t, const void *rh, long long Vh, int nrhs, RhsState *st,
-                          int max_iter, cudaStream_t s);
 // CGNE (CG on the normal equations Mhat^dag Mhat x = Mhat^dag b), per RHS,
 // real scalars in the .x parts of rho / alpha / beta.  Init: blas_bicg_init
 // (r = b, x = p = 0, |b|^2).  Per iteration, with z = Mhat^dag r and
