@@ -15,13 +15,19 @@
 // h = psi_up -/+ e_mu psi_down, so only the 2-spin half spinor h is multiplied
 // by the link and the lower spins are rebuilt from U h.
 //
-// Two kernels:
+// Kernels:
 //  * FP64, one thread per (output site, RHS), scalar double arithmetic (the
 //    FP64 pipe is the bound on GB300);
 //  * FP32, one thread per (output site, 1 or 2 RHS pairs) on the paired layout
 //    of pair.cuh: every arithmetic step is one packed f32x2 instruction for two
 //    RHS, with links, hop factors and the clover inverse loaded once per
-//    thread and broadcast to both lanes.
+//    thread and broadcast to both lanes.  Variants for one pair per thread
+//    differ in how the neighbour data arrives: direct loads; spinor and link
+//    staged through shared memory (k_dslash32s, or k_dslash32p in one
+//    persistent wave); direct loads with an L1 prefetch (k_dslash32f); the
+//    spinor alone staged with the link read from L1 at 16 warps per SM
+//    (k_dslash32t, the tuner's choice on the benchmark lattice).  All give
+//    bit-identical results; the tuner picks per volume and RHS count.
 // RHS (pairs) are the fastest index: the RHS of a site sit in adjacent threads
 // of one warp, every component load of the [component][site][rhs] layout is
 // one contiguous 128-bit run per warp, and the RHS threads of a site share
