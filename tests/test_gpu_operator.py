@@ -306,3 +306,26 @@ def test_full_size_48x24_schur_launch_in_the_benchmark_shape(ctx):
     even = ((t + x + y + z) % 2) == 0
     assert per_site_rel(lhs[:, even], rhs[:, even]) < 1e-5
     dp.dp_field_free(ctx, f)
+
+
+def test_full_size_64x32_light_quark_hop(ctx):
+    """The largest workload: the light-quark 64x32^3 lattice (eps = 0.5,
+    seed 7) with its cosh-4d profile (alpha0 = 0.2) and an off-origin
+    source, 2 RHS: FP32 12-real links against the oracle, and FP16 links
+    (the configuration's inner solver) against the oracle on the links as
+    the 16-bit storage reproduces them; every site."""
+    dims = (64, 32, 32, 32)
+    U = li.su3_links(dims, 0.5, 7)
+    f = dp.dp_field_load(ctx, U, dims, -1)
+    psi = li.random_spinor(dims, 2, 44)
+    prof, src = ("cosh_4d", 0.2), (5, 7, 11, 30)
+    op = oracle.WilsonClover(U, dims, 0.0, -1)
+    ref = op.hop(psi, (prof[0], prof[1], src))
+    got = dp.dp_apply(ctx, f, "hop", 0.0, prof, src, "mixed_fp32", psi, compress12=1)
+    assert per_site_rel(got, ref) < 1e-6
+    del op, ref, got
+    op16 = oracle.WilsonClover(oracle.stored_links16(U.reshape(oracle.array_shape(dims) + (4, 3, 3)),
+                                                     "fp16"), dims, 0.0, -1)
+    got16 = dp.dp_apply(ctx, f, "hop", 0.0, prof, src, "mixed_fp16", psi)
+    assert per_site_rel(got16, op16.hop(psi, (prof[0], prof[1], src))) < 1e-6
+    dp.dp_field_free(ctx, f)
