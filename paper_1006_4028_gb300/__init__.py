@@ -11,6 +11,17 @@ links ``(T, Lz, Ly, Lx, 4, 3, 3)``, spinors ``(nrhs, T, Lz, Ly, Lx, 4, 3)``.
 Profiles are given as ``(kind, alpha0)`` or ``(kind, alpha0, tables)`` with
 kind one of ``"none", "exp_t", "cosh_t", "cosh_4d", "table"`` (alpha_B
 orientation: S' = alpha_B S, see the header).
+
+A point-source solve, restored and contracted::
+
+    import paper_1006_4028_gb300 as dp
+    ctx = dp.dp_create(0)
+    f = dp.dp_field_load(ctx, links, (48, 24, 24, 24), -1)   # antiperiodic time
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    dp.dp_autotune(ctx, f, "mixed_fp32", 1, 12)               # optional
+    cpp, _, info = dp.dp_solve_point(ctx, f, 0.5, ("cosh_t", 0.4), (0, 0, 0, 0), 1e-11,
+                                     {"prec": "mixed_fp32"}, T=48)
+    m_eff = dp.dp_effective_mass(cpp, "cosh")
 """
 from __future__ import annotations
 
