@@ -705,7 +705,7 @@ def main():
                     help="skip the leg with the outer Schur operator in double-float")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-load", type=float, default=0.9,
-                    help="offered load as a fraction of the measured batch-solve rate")
+                    help="offered load of the serving leg as a fraction of the capacity a closed burst of the same request mix measures")
     ap.add_argument("--dims", default=None,
                     help="T,Lx,Ly,Lz of a smaller lattice for profiling runs (not the headline)")
     ap.add_argument("--prec", default="mixed_fp32",
