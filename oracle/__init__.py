@@ -394,6 +394,27 @@ def solve_point(op, M, profile_kind="none", alpha0=0.0, src=(0, 0, 0, 0), tol=1e
                     "cap": contract_cap(S, dims, src[0])}
 
 
+def slice_residuals(op, M, S, eta, t_src=0):
+    """Per-time-slice relative residual of a restored solution.
+
+    rho(y0) = |[eta - (D+M) S]_t| / |S_t| with |.|_t the L2 norm over the
+    spatial sites of time slice t = (y0 + t_src) mod T and over all right-hand
+    sides (the 12 components of a point source), on the unpreconditioned
+    system of Sec. I eq. (linsysunprec).  The paper's global criterion (eq.
+    stopping) bounds only the sum over slices; this is the quantity whose
+    smallness on the far slices decides whether C_PP(y0) is accurate there
+    (Sec. II, the error argument behind the preconditioning).
+    S, eta: (n, T, Lz, Ly, Lx, 4, 3).  Returns an array of length T.
+    """
+    S = _c128(S)
+    r = _c128(eta) - op.apply(S, M)
+    T = dims_tuple(op.dims)[0]
+    n = S.size // (op.V * 12)
+    rt = np.sum(np.abs(r.reshape(n, T, -1)) ** 2, axis=(0, 2))
+    st = np.sum(np.abs(S.reshape(n, T, -1)) ** 2, axis=(0, 2))
+    return np.roll(np.sqrt(rt / st), -int(t_src))
+
+
 def effective_mass(cpp):
     """m_eff(y0) = ln[C(y0)/C(y0+1)] (log-ratio reading; the paper plots it
     without writing it out)."""
