@@ -127,7 +127,25 @@ typedef struct {
                          double-float arithmetic (two FP32 per real, ~48-bit
                          significands, ~1e-14 relative; for r >= 1e-12) on the
                          FP32 units instead of FP64; 0 = FP64                       */
+    double slice_tol; /* per-time-slice accuracy target: 0 = 10 r (default), > 0 as
+                         given, < 0 off (the paper's global test alone).  See below. */
 } dp_solve_opts;
+
+/* Per-time-slice accuracy.  The residue r of the paper's stopping rule (Sec.
+ * I, eq. stopping) bounds the residual summed over the lattice, which leaves
+ * the far time slices, where the propagator is exponentially small, wrong
+ * unless the profile makes the preconditioned solution roughly flat (Sec. II;
+ * the light-quark profile of Sec. III steepens it instead).  So after the
+ * global test passes, the FP64 outer loop measures per time slice t
+ *   rho_t = |r_t / alpha_B| / |x_t / alpha_B|
+ * (r the FP64 true residual of the even-odd Schur system, x the solution, both
+ * on the Schur parity, restored by the profile per site, summed over the 12
+ * components of the point source).  While max_t rho_t > slice_tol it runs more
+ * defect-correction rounds whose inner solve uses a time profile built from
+ * the measured slice norms (an exact change of the correction equation's
+ * preconditioning, Sec. II).  If that stops improving, the solve returns
+ * DP_ERR_NOT_CONVERGED (results still written) instead of DP_OK.
+ * dp_solve_info.slice_residue reports the final max_t rho_t. */
 
 typedef struct {
     int iters_inner;         /* inner Krylov iterations (max over RHS)          */
@@ -136,6 +154,9 @@ typedef struct {
     double seconds;          /* wall time of the call                           */
     int n_rhs;               /* right-hand sides solved                         */
     int status;              /* dp_status of this solve                         */
+    double slice_residue;    /* max over time slices of rho_t (see above); 0 when
+                                the per-slice check is off                       */
+    int refine_rounds;       /* outer rounds spent on per-slice refinement       */
 } dp_solve_info;
 
 /* Optional device allocator.  alloc returns device memory of >= bytes, 256-byte
@@ -265,12 +286,19 @@ dp_status dp_restore_contract_dev(dp_ctx *ctx, dp_field field, int n_groups,
  * every GPU that loads the library, held until the process exits): profile
  * tables, slot descriptors and the per-slice partial sums, sized for T <= 256,
  * up to 64 partial sums per time slice (always the case for extents <= 256)
- * and n_groups <= 5.  Larger requests return DP_ERR_INVALID_ARG.  No
+ * and n_groups <= 5 (the 64 RHS slots of a batch hold five 12-component
+ * groups).  Larger requests return DP_ERR_INVALID_ARG.  No
  * cudaMalloc, cudaFree or other allocating call is made.
  *
  * The first call on a device looks up the array's device address (with that
  * device current) and keeps it; make that first call before any stream
- * capture.  Every call shares the one array and it keeps the last call's
+ * capture.  A device reset (cudaDeviceReset) unloads the array with everything
+ * else, and every dp_ctx on that device must then be destroyed and created
+ * again: creating a context on a device forgets the kept address, so the next
+ * call looks it up anew (make that call, too, before any stream capture).
+ * The host-side tables of a call live in per-thread storage (about 82 KiB per
+ * calling thread, set up by the loader), not on the caller's stack.  Every
+ * call shares the one array and it keeps the last call's
  * contents (nothing needs clearing: each value read is written earlier in the
  * same call).  Calls that overlap on the GPU (other threads, other contexts on
  * the same device) race on the array: serialise them.  Arguments, layouts and
@@ -320,6 +348,15 @@ dp_status dp_profile_tables(const int dims[4], int bc_t, const dp_profile *profi
  * where the ratio is not positive or the form cannot reach it.  Errors:
  * null pointers, T < 2, another kind (DP_ERR_INVALID_ARG). */
 dp_status dp_effective_mass(const double *c, int T, int kind, double *m_out);
+
+/* PCAC mass from the two correlators dp_solve_point_corr returns (the paper
+ * labels its quark masses by am_PCAC, Sec. II):
+ *   m_out[y0] = [C_AP(y0+1) - C_AP(y0-1)] / (4 C_PP(y0)),  y0 = 1..T-2,
+ * the symmetric lattice derivative of the local axial current over twice the
+ * pseudoscalar density correlator, no O(a) improvement term (the paper names
+ * none); m_out[0] = m_out[T-1] = NaN.  cpp, cap, m_out: [T], caller-owned.
+ * Errors: null pointers, T < 3 (DP_ERR_INVALID_ARG). */
+dp_status dp_pcac_mass(const double *cpp, const double *cap, int T, double *m_out);
 
 /* Fit of C(y0) = A exp(-m y0) (kind 0) or A [exp(-m y0) + exp(-m (T - y0))]
  * (kind 1) over y0 = t0..t1 by least squares in the relative deviations
@@ -418,6 +455,7 @@ typedef struct {
     int src[4];
     double r;
     int prec;             /* dp_prec */
+    double slice_tol;     /* as dp_solve_opts.slice_tol (0: 10 r, < 0: off)   */
 } dp_request;
 
 typedef struct {

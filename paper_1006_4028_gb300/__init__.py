@@ -37,7 +37,7 @@ __all__ = [
     "dp_create", "dp_destroy", "dp_last_error", "dp_device_bytes", "dp_trim",
     "dp_field_load", "dp_field_set_csw", "dp_field_free",
     "dp_solve_point", "dp_solve_point_multi", "dp_solve_point_dev",
-    "dp_solve_point_corr", "dp_solve_point_hl", "pcac_mass", "dp_effective_mass", "dp_fit_correlator", "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
+    "dp_solve_point_corr", "dp_solve_point_hl", "dp_pcac_mass", "dp_effective_mass", "dp_fit_correlator", "dp_apply", "dp_profile_tables", "dp_spinor_bytes", "dp_dslash_dev", "dp_schur_dev",
     "dp_autotune", "dp_tune_set",
     "dp_timing_enable", "dp_timing_reset", "dp_timing_get", "dp_launch_count",
     "dp_serve_start", "dp_submit", "dp_wait", "dp_cancel", "dp_serve_stats_get", "dp_serve_stop",
@@ -68,13 +68,15 @@ class SolveOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("solver", C.c_int), ("prec", C.c_int),
                 ("compress12", C.c_int), ("inner_tol", C.c_double), ("batched", C.c_int),
                 ("use_graph", C.c_int), ("check_every", C.c_int), ("sap_ncy", C.c_int),
-                ("sap_nmr", C.c_int), ("gcr_nkv", C.c_int), ("outer_df", C.c_int)]
+                ("sap_nmr", C.c_int), ("gcr_nkv", C.c_int), ("outer_df", C.c_int),
+                ("slice_tol", C.c_double)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters_inner", C.c_int), ("iters_outer", C.c_int),
                 ("true_rel_residue", C.c_double), ("seconds", C.c_double),
-                ("n_rhs", C.c_int), ("status", C.c_int)]
+                ("n_rhs", C.c_int), ("status", C.c_int), ("slice_residue", C.c_double),
+                ("refine_rounds", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,7 +84,8 @@ class SolveInfo(C.Structure):
 
 class Request(C.Structure):
     _fields_ = [("field", C.c_uint64), ("M", C.c_double), ("profile", Profile),
-                ("src", C.c_int * 4), ("r", C.c_double), ("prec", C.c_int)]
+                ("src", C.c_int * 4), ("r", C.c_double), ("prec", C.c_int),
+                ("slice_tol", C.c_double)]
 
 
 class ServeStats(C.Structure):
@@ -122,6 +125,7 @@ def load(build_if_missing=False):
         "dp_device_bytes": ([vp], sz),
         "dp_trim": ([vp], ip),
         "dp_effective_mass": ([vp, ip, ip, vp], ip),
+        "dp_pcac_mass": ([vp, vp, ip, vp], ip),
         "dp_fit_correlator": ([vp, ip, ip, ip, ip, P(dp), P(dp), P(dp)], ip),
         "dp_field_load": ([vp, vp, P(C.c_int * 4), ip, P(up)], ip),
         "dp_field_set_csw": ([vp, up, dp], ip),
@@ -213,6 +217,7 @@ def _opts(o):
     s.sap_ncy = int(o.get("sap_ncy", 0))
     s.sap_nmr = int(o.get("sap_nmr", 0))
     s.gcr_nkv = int(o.get("gcr_nkv", 0))
+    s.slice_tol = float(o.get("slice_tol", 0.0))
     return s
 
 
@@ -308,14 +313,16 @@ def dp_solve_point_hl(ctx, field, Mh, prof_h, Ml, prof_l, src, r, opts=None, T=N
     return cpp, hl[:, 0] + 1j * hl[:, 1], [infos[0].as_dict(), infos[1].as_dict()]
 
 
-def pcac_mass(cpp, cap):
+def dp_pcac_mass(cpp, cap):
     """m_PCAC(y0) = [C_AP(y0+1) - C_AP(y0-1)] / (4 C_PP(y0)) for y0 = 1..T-2 (host
-    arithmetic on the two returned correlators; NaN at the ends)."""
-    cpp = np.asarray(cpp, float)
-    cap = np.asarray(cap, float)
-    m = np.full(len(cpp), np.nan)
-    m[1:-1] = (cap[2:] - cap[:-2]) / (4.0 * cpp[1:-1])
-    return m
+    function of the library); NaN at the ends."""
+    c = np.ascontiguousarray(cpp, dtype=np.float64)
+    a = np.ascontiguousarray(cap, dtype=np.float64)
+    if a.shape != c.shape:
+        raise ValueError("cpp and cap must have the same length")
+    out = np.empty(len(c), dtype=np.float64)
+    _check(load().dp_pcac_mass(c.ctypes.data, a.ctypes.data, len(c), out.ctypes.data))
+    return out
 
 
 MEFF_KINDS = {"log": 0, "cosh": 1}
@@ -548,7 +555,7 @@ def dp_serve_start(ctx, hbm_budget=0, max_slots=0):
     _check(load().dp_serve_start(ctx, int(hbm_budget), int(max_slots)))
 
 
-def dp_submit(ctx, field, M, profile, src, r, prec="mixed_fp32"):
+def dp_submit(ctx, field, M, profile, src, r, prec="mixed_fp32", slice_tol=0.0):
     rq = Request()
     rq.field = int(field)
     rq.M = float(M)
@@ -557,6 +564,7 @@ def dp_submit(ctx, field, M, profile, src, r, prec="mixed_fp32"):
     rq.src = _i4(src)
     rq.r = float(r)
     rq.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    rq.slice_tol = float(slice_tol)
     t = C.c_uint64()
     _check(load().dp_submit(ctx, C.byref(rq), C.byref(t)))
     return t.value

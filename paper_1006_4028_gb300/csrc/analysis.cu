@@ -90,6 +90,18 @@ dp_status dp_effective_mass(const double *c, int T, int kind, double *m_out)
     return DP_OK;
 }
 
+dp_status dp_pcac_mass(const double *cpp, const double *cap, int T, double *m_out)
+{
+    if (!cpp || !cap || !m_out || T < 3) {
+        dp::set_error("PCAC mass needs cpp[T], cap[T], m_out[T] and T >= 3");
+        return DP_ERR_INVALID_ARG;
+    }
+    m_out[0] = m_out[T - 1] = NAN;
+    for (int t = 1; t + 1 < T; t++)
+        m_out[t] = (cap[t + 1] - cap[t - 1]) / (4.0 * cpp[t]);
+    return DP_OK;
+}
+
 dp_status dp_fit_correlator(const double *c, int T, int kind, int t0, int t1, double *m_out,
                             double *A_out, double *rms_out)
 {

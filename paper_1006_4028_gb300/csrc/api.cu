@@ -383,6 +383,10 @@ dp_status check_opts(const dp_solve_opts *in, dp_solve_opts *out)
         return DP_ERR_INVALID_ARG;
     }
     if (o.prec == DP_PREC_FP64) o.outer_df = 0;  // the FP64 solver has no separate outer operator
+    if (!std::isfinite(o.slice_tol)) {
+        set_error("slice_tol must be finite");
+        return DP_ERR_INVALID_ARG;
+    }
     *out = o;
     return DP_OK;
 }
@@ -436,6 +440,9 @@ dp_status dp_create(dp_ctx **out, int device, const dp_alloc_hooks *hooks, void 
         return DP_ERR_CUDA;
     }
     CUDA_OK(cudaSetDevice(device));
+    // a new context may follow a device reset, which invalidates the scratch
+    // array's looked-up address of dp_restore_contract_noalloc
+    noalloc_forget_address(device);
     dp_ctx *ctx = new dp_ctx();
     Ctx &c = ctx->c;
     c.device = device;

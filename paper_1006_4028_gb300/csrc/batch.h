@@ -19,8 +19,15 @@ struct Job {
     double *cpp_host = nullptr;  // host [T], written on completion
     double *cap_dst = nullptr;   // device [T] C_AP, written (or added to) on completion, or NULL
     double *prop_host = nullptr; // host [ncomp][V][12] complex128 or NULL
+    // per-slice accuracy target (0: not checked): the restored Schur residual
+    // of every time slice relative to that slice's solution, see slices.cu
+    double slice_tol = 0;
     SolveResult res;
     bool done = false;
+    // per-slice check state (set by the batch)
+    bool slice_ok = false, refining = false;
+    int refine_rounds = 0, slice_stall = 0;
+    double slice_best = 0, slice_res = 0;
     // set by the batch
     int tab = -1, slot0 = -1;
     double src_scale = 1.0;
@@ -78,6 +85,12 @@ class Batch {
   private:
     void *get(size_t bytes);
     dp_status upload_mask(const std::vector<int> &m);
+    // per-slice residuals of the jobs that finished globally or are refining;
+    // starts, continues or ends their refinement (updates hs; sets *changed)
+    dp_status slice_check(bool *changed);
+    // inner solver's profile of a job: a time table that flattens the
+    // restored per-slice norms xx[t] (absolute t) of its current solution
+    dp_status set_inner_profile(const Job &j, const double *xx);
     dp_status bicgstab(int max_iter, int *iters_done);
     dp_status cgne(int max_iter, int *iters_done);
     dp_status sap_gcr(int max_iter, int *iters_done);
@@ -110,6 +123,12 @@ class Batch {
     InnerVecs in;
     RhsState *outer = nullptr, *inner = nullptr;
     double *alpha_d = nullptr, *hop64_d = nullptr, *hopadj64_d = nullptr;
+    // the inner solver's profile per group (equal to alpha_d until a job is
+    // refined) and, for the FP64 inner solver, its own hop tables
+    double *alpha_in_d = nullptr, *hopin64_d = nullptr;
+    double *slice_d = nullptr;  // [kMaxGroups][T][2] per-slice norms
+    std::vector<double> slice_h;
+    bool any_refining() const;
     float *hop32_d = nullptr, *hopadj32_d = nullptr;  // adj: the reciprocal profile (CGNE)
     SlotInfo *slots_d = nullptr;
     int *tsrc_d = nullptr, *mask_d = nullptr;

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_residual64(Cfg c, const double2 *
     if (!isfinite(acc[0])) {
         S.status = 3;
         S.active = 0;
-    } else if (acc[0] <= S.tol2) {
+    } else if (!S.refine && acc[0] <= S.tol2) {  // a refined RHS stops on its slices
         S.status = 1;
         S.active = 0;
     }
@@ -370,7 +370,12 @@ __global__ void k_inner_setup(const RhsState *outer, RhsState *inner, int n, dou
     RhsState S = {};
     S.active = outer[r].active;
     double tol = inner_tol;
-    if (outer[r].rr > 0) {
+    if (outer[r].refine) {
+        // per-slice refinement: the round's reduction, set per job in tol2
+        // (the global threshold does not apply to a refined RHS)
+        const double want = sqrt(outer[r].tol2);
+        if (want > tol) tol = want;
+    } else if (outer[r].rr > 0) {
         const double want = 0.5 * sqrt(outer[r].tol2 / outer[r].rr);
         if (want > tol) tol = want;
     }
@@ -398,7 +403,7 @@ __global__ void k_acc64(double2 *x64, const double2 *e64, long long Vh, int n, c
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= Vh * n) return;
     const int r = (int)(gid % n);
-    if (!st[r].active) return;
+    if (!st[r].active || st[r].refine) return;  // refined RHS: blas_acc64_ratio
     const long long cs = Vh * n;
     const double sc = st[r].scale;
     V12 x = ld(x64, cs, gid), e = ld(e64, cs, gid);

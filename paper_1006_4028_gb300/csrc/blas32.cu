@@ -564,7 +564,9 @@ __global__ void k32_acc64(double2 *x64, const float4 *e32, long long Vh, int n, 
     if (gid >= Vh * P) return;
     const long long s = gid / P;
     const int q = (int)(gid - s * P);
-    const bool a0 = st[2 * q].active != 0, a1 = st[2 * q + 1].active != 0;
+    // refined RHS take blas_acc_f32_ratio instead
+    const bool a0 = st[2 * q].active != 0 && !st[2 * q].refine;
+    const bool a1 = st[2 * q + 1].active != 0 && !st[2 * q + 1].refine;
     if (!a0 && !a1) return;
     const double s0 = st[2 * q].scale, s1 = st[2 * q + 1].scale;
 #pragma unroll

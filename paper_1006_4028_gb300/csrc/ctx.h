@@ -141,7 +141,17 @@ struct SolveResult {
     int iters_inner = 0, iters_outer = 0;
     double true_rel_residue = 0;
     int status = 0;
+    double slice_residue = 0;  // max over time slices of the restored per-slice residual
+    int refine_rounds = 0;     // outer rounds spent on per-slice refinement
 };
+
+// per-slice target of a solve at residue r: opts_tol > 0 as given, < 0 off,
+// 0 the default kSliceFactor * r
+constexpr double kSliceFactor = 10.0;
+inline double slice_target(double opts_tol, double r)
+{
+    return opts_tol > 0 ? opts_tol : (opts_tol < 0 ? 0.0 : kSliceFactor * r);
+}
 
 // the method for a set of point-source groups on one field (solver.cu)
 // cap_dev (optional, device [n_groups][T]): also C_AP(y0)
@@ -151,6 +161,10 @@ dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group
                        double *hl_dev = nullptr);
 
 dp_status check_opts(const dp_solve_opts *in, dp_solve_opts *out);
+
+// forget the looked-up device address of the allocation-free entry point's
+// scratch array on `device` (field.cu)
+void noalloc_forget_address(int device);
 
 }  // namespace dp
 

@@ -196,6 +196,8 @@ struct RhsState {        // per RHS, device resident
     int status;           // 0 running, 1 converged, 2 breakdown, 3 non-finite, 4 max-iter
     int fresh;            // 1: x = 0, next residual call sets |b|^2 and tol2
     int brk;              // fused FP32 BiCGStab: breakdown found by the omega reduction
+    int refine;           // FP64 outer loop: per-slice refinement (the inner solve runs in
+                          // another profile's metric; the global test does not stop it)
 };
 
 constexpr int kRedWidth = 8;  // values per RHS in a block's reduction partials
@@ -299,6 +301,37 @@ struct SapParams {
 // block extents: 4 where the extent allows, else 2; false if an extent is odd
 bool sap_blocks(const Geom &g, int bs[4], int nb[4]);
 cudaError_t launch_sap_block(const SapParams &p, int link_fmt, cudaStream_t st);
+
+// ---- per-time-slice accuracy of the outer loop (slices.cu) ----
+// Per group m and absolute time slice t, over the RHS with mask[r] != 0 on
+// the Schur parity `parity`: out[(m*T + t)*2 + 0] = sum |x/alpha_B|^2,
+// out[... + 1] = sum |r/alpha_B|^2 (alpha_B of the group, per site: the
+// restored metric); summed in a fixed order.  partials: 2 * T * P * ngroups
+// doubles, P = contract_blocks_per_slice(g).
+cudaError_t launch_slice_norms(const double2 *x, const double2 *r, const Geom &g, int parity,
+                               int nrhs, const double *alpha, const SlotInfo *slots_dev,
+                               int ngroups, const int *mask, double *partials, double *out,
+                               cudaStream_t st);
+// Transfer of the outer residual into the inner solver's metric for RHS with
+// st.active && st.refine: R(site) = alpha_in/alpha_out of the RHS's group
+// (alpha tables [group][mu][Lmax]).  ratio_norm: st.scale = |R r| (FP64,
+// deterministic); to_f32 / scale64: inner source R r / scale (paired FP32 or
+// FP64 layout, only the refined RHS are written); acc: x += scale e / R.
+cudaError_t blas_ratio_norm(BlasCtx &bc, const double2 *r64, const Geom &g, int parity, int nrhs,
+                            const double *alpha_out, const double *alpha_in,
+                            const SlotInfo *slots_dev, RhsState *st, cudaStream_t s);
+cudaError_t blas_to_f32_ratio(const double2 *r64, float4 *r32, const Geom &g, int parity,
+                              int nrhs, const double *alpha_out, const double *alpha_in,
+                              const SlotInfo *slots_dev, const RhsState *st, cudaStream_t s);
+cudaError_t blas_scale64_ratio(const double2 *r64, double2 *out, const Geom &g, int parity,
+                               int nrhs, const double *alpha_out, const double *alpha_in,
+                               const SlotInfo *slots_dev, const RhsState *st, cudaStream_t s);
+cudaError_t blas_acc_f32_ratio(double2 *x64, const float4 *e32, const Geom &g, int parity,
+                               int nrhs, const double *alpha_out, const double *alpha_in,
+                               const SlotInfo *slots_dev, const RhsState *st, cudaStream_t s);
+cudaError_t blas_acc64_ratio(double2 *x64, const double2 *e64, const Geom &g, int parity,
+                             int nrhs, const double *alpha_out, const double *alpha_in,
+                             const SlotInfo *slots_dev, const RhsState *st, cudaStream_t s);
 
 // FP64 outer loop helpers
 // r = b - y (r = b for `fresh` RHS); |r|^2 -> st.rr; st.scale = |r|;

@@ -500,10 +500,19 @@ size_t noalloc_scratch_bytes() { return kNaBytes; }
 namespace {
 // Device address of g_noalloc_scratch per device.  In host code the array's
 // name only stands in for the symbol; the address a kernel may use is looked
-// up once per device with that device current.
+// up once per device with that device current.  A device reset destroys the
+// module that holds the array, so the address is forgotten whenever a context
+// is created on that device (every context there is invalid after a reset and
+// has to be created again) and looked up anew on the next call.
 constexpr int kNaMaxDevices = 64;
 std::mutex g_na_mu;
 void *g_na_addr[kNaMaxDevices] = {};
+
+// host-side tables of one call: per thread, outside the caller's stack
+// (about 82 KiB), allocated once per thread by the loader, not per call
+thread_local double t_na_alpha[dp::kMaxGroups * 4 * dp::kMaxL];
+thread_local double t_na_hop[8 * dp::kMaxL];
+thread_local dp::SlotInfo t_na_slots[dp::kMaxRhs];
 
 dp_status noalloc_scratch_address(int device, unsigned char **out)
 {
@@ -526,6 +535,15 @@ dp_status noalloc_scratch_address(int device, unsigned char **out)
 }
 }  // namespace
 
+namespace dp {
+void noalloc_forget_address(int device)
+{
+    if (device < 0 || device >= kNaMaxDevices) return;
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    g_na_addr[device] = nullptr;
+}
+}  // namespace dp
+
 extern "C" dp_status dp_restore_contract_noalloc(dp_ctx *ctx, dp_field field, int n_groups,
                                                  const dp_profile *profiles, const int *src,
                                                  const double *xe, const double *xo,
@@ -546,9 +564,11 @@ extern "C" dp_status dp_restore_contract_noalloc(dp_ctx *ctx, dp_field field, in
         set_error("unknown field");
         return DP_ERR_NOT_FOUND;
     }
-    if (n_groups < 1 || 12 * n_groups > kMaxRhs || n_groups > kNaMaxGroups || !profiles || !src ||
-        !xe || !xo || !cpp_dev) {
-        set_error("dp_restore_contract_noalloc: invalid argument (n_groups in [1, %d])", kMaxRhs / 12);
+    constexpr int kNaGroupsMax = kMaxRhs / 12 < kNaMaxGroups ? kMaxRhs / 12 : kNaMaxGroups;
+    if (n_groups < 1 || n_groups > kNaGroupsMax || !profiles || !src || !xe || !xo || !cpp_dev) {
+        set_error("dp_restore_contract_noalloc: invalid argument (n_groups in [1, %d]: %d RHS "
+                  "slots of 12, scratch for %d groups; non-null pointers)",
+                  kNaGroupsMax, kMaxRhs, kNaMaxGroups);
         return DP_ERR_INVALID_ARG;
     }
     const Geom &g = fp->g;
@@ -561,10 +581,8 @@ extern "C" dp_status dp_restore_contract_noalloc(dp_ctx *ctx, dp_field field, in
     unsigned char *base = nullptr;
     dp_status s = noalloc_scratch_address(c.device, &base);
     if (s != DP_OK) return s;
-    // host-side tables in fixed-size stack arrays (about 82 KiB): no heap use
-    double alpha[kNaMaxGroups * 4 * kMaxL];
-    double hop[8 * kMaxL];
-    SlotInfo slots[kMaxRhs];
+    double *alpha = t_na_alpha, *hop = t_na_hop;
+    SlotInfo *slots = t_na_slots;
     int tsrc[kNaMaxGroups] = {};
     const int Lm = g.Lmax, n = 12 * n_groups;
     const int L[4] = {g.T, g.Lx, g.Ly, g.Lz};
@@ -613,8 +631,8 @@ extern "C" dp_status dp_restore_contract_noalloc(dp_ctx *ctx, dp_field field, in
                                                                    nullptr);
         e = cudaGetLastError();
     }
-    // the host tables live on this stack frame: wait for the copies (and the
-    // kernels) before returning
+    // the host tables are reused by this thread's next call: wait for the
+    // copies (and the kernels) before returning
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) {
         set_error("restore/contract (no-alloc): %s", cudaGetErrorString(e));

@@ -129,7 +129,8 @@ void Scheduler::run()
                 Request *rq = static_cast<Request *>(j->user);
                 rq->status = (dp_status)j->res.status;
                 if (rq->status != DP_OK)
-                    rq->err = rq->status == DP_ERR_NOT_CONVERGED ? "solve did not reach the requested residue"
+                    rq->err = rq->status == DP_ERR_NOT_CONVERGED ? "solve did not reach the requested residue "
+                                                                   "or per-slice accuracy"
                                                                  : "solve failed";
                 rq->done = true;
                 rq->t_done = Clock::now();
@@ -284,8 +285,8 @@ dp_status dp_submit(dp_ctx *ctx, const dp_request *req, dp_ticket *ticket)
         set_error("the scheduler serves mixed-precision FP32 requests");
         return DP_ERR_INVALID_ARG;
     }
-    if (!std::isfinite(req->M) || !(req->r > 0 && req->r < 1)) {
-        set_error("invalid mass or residue");
+    if (!std::isfinite(req->M) || !(req->r > 0 && req->r < 1) || !std::isfinite(req->slice_tol)) {
+        set_error("invalid mass, residue or slice_tol");
         return DP_ERR_INVALID_ARG;
     }
     const int L[4] = {f->g.T, f->g.Lx, f->g.Ly, f->g.Lz};
@@ -313,6 +314,7 @@ dp_status dp_submit(dp_ctx *ctx, const dp_request *req, dp_ticket *ticket)
     rq->cpp.assign(f->g.T, 0.0);
     rq->job.grp = rq->grp;
     rq->job.r = req->r;
+    rq->job.slice_tol = slice_target(req->slice_tol, req->r);
     rq->job.cpp_host = rq->cpp.data();
     rq->job.user = rq.get();
     rq->t_submit = Clock::now();
@@ -366,6 +368,8 @@ dp_status dp_wait(dp_ctx *ctx, dp_ticket ticket, double timeout_s, double *cpp_o
         info->iters_inner = rq->job.res.iters_inner;
         info->iters_outer = rq->job.res.iters_outer;
         info->true_rel_residue = rq->job.res.true_rel_residue;
+        info->slice_residue = rq->job.res.slice_residue;
+        info->refine_rounds = rq->job.res.refine_rounds;
         info->seconds = std::chrono::duration<double>(rq->t_done - rq->t_submit).count();
         info->n_rhs = 12;
         info->status = rq->status;

@@ -198,6 +198,9 @@ dp_status Batch::init()
     hop32_d = (float *)get(sizeof(float) * kMaxGroups * 8 * Lm);
     hopadj64_d = (double *)get(sizeof(double) * kMaxGroups * 8 * Lm);
     hopadj32_d = (float *)get(sizeof(float) * kMaxGroups * 8 * Lm);
+    alpha_in_d = (double *)get(sizeof(double) * kMaxGroups * 4 * Lm);
+    if (ipr == 0) hopin64_d = (double *)get(sizeof(double) * kMaxGroups * 8 * Lm);
+    slice_d = (double *)get(sizeof(double) * kMaxGroups * 2 * g.T);
     slots_d = (SlotInfo *)get(sizeof(SlotInfo) * kMaxRhs);
     tsrc_d = (int *)get(sizeof(int) * kMaxGroups);
     mask_d = (int *)get(sizeof(int) * kMaxRhs);
@@ -206,7 +209,7 @@ dp_status Batch::init()
     cpart = (double *)get(sizeof(double) * 2 * (size_t)g.T * contract_blocks_per_slice(g) * kMaxGroups);
     nrm_d = (double *)get(sizeof(double) * kMaxRhs);
     ok = ok && outer && inner && alpha_d && hop64_d && hop32_d && hopadj64_d && hopadj32_d &&
-         slots_d && tsrc_d && mask_d &&
+         alpha_in_d && (ipr != 0 || hopin64_d) && slice_d && slots_d && tsrc_d && mask_d &&
          cpp_d && cap_d && cpart && nrm_d;
     if (!ok) {
         set_error("out of device memory for a %d-slot solver batch (%zu bytes per FP64 vector)", n, v64);
@@ -223,6 +226,9 @@ dp_status Batch::init()
     CK(cudaMemsetAsync(outer, 0, sizeof(RhsState) * kMaxRhs, c->stream));
     CK(cudaMemsetAsync(inner, 0, sizeof(RhsState) * kMaxRhs, c->stream));
     CK(cudaMemsetAsync(alpha_d, 0, sizeof(double) * kMaxGroups * 4 * Lm, c->stream));
+    CK(cudaMemsetAsync(alpha_in_d, 0, sizeof(double) * kMaxGroups * 4 * Lm, c->stream));
+    if (hopin64_d) CK(cudaMemsetAsync(hopin64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, c->stream));
+    slice_h.assign((size_t)kMaxGroups * 2 * g.T, 0.0);
     CK(cudaMemsetAsync(hop64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, c->stream));
     CK(cudaMemsetAsync(hop32_d, 0, sizeof(float) * kMaxGroups * 8 * Lm, c->stream));
     CK(cudaMemsetAsync(hopadj64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, c->stream));
@@ -244,7 +250,9 @@ dp_status Batch::init()
         dp_status e = field_links(c, *f, ilf, p, &opin.links[p]);
         if (e != DP_OK) return e;
     }
-    opin.hop = ipr == 0 ? (const void *)hop64_d : (const void *)hop32_d;
+    // the inner solver's own hop tables: a job under per-slice refinement
+    // solves its corrections in another profile's metric (slices.cu)
+    opin.hop = ipr == 0 ? (const void *)hopin64_d : (const void *)hop32_d;
     set_shape(opin, c->launch_shape(Vh, ipr, ilf, n));
     opin_adj = opin;
     opin_adj.hop = ipr == 0 ? (const void *)hopadj64_d : (const void *)hopadj32_d;
@@ -382,6 +390,9 @@ dp_status Batch::admit(Job *j)
         for (int p = 0; p < 2; p++) opdf.inv[p][tab] = ci->invdf[p];
     }
     CK(cudaMemcpyAsync(alpha_d + (size_t)tab * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(alpha_in_d + (size_t)tab * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm, cudaMemcpyHostToDevice, c->stream));
+    if (hopin64_d)
+        CK(cudaMemcpyAsync(hopin64_d + (size_t)tab * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(hop64_d + (size_t)tab * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(hop32_d + (size_t)tab * 8 * Lm, hopf.data(), sizeof(float) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
     const int ts = j->grp.src[0];
@@ -413,6 +424,9 @@ dp_status Batch::admit(Job *j)
     j->tab = tab;
     j->slot0 = s0;
     j->src_scale = scale;
+    j->slice_ok = j->refining = false;
+    j->refine_rounds = j->slice_stall = 0;
+    j->slice_best = j->slice_res = 0;
     jobs[tab] = j;
     if (graph) {  // kernel parameters (clover pointers, groups) changed
         cudaGraphExecDestroy(graph);
@@ -792,7 +806,8 @@ dp_status Batch::round()
     bool changed = false;
     for (int k = 0; k < n; k++) {
         if (!slot_job[k] || !hs[k].active) continue;
-        if (slot_outer[k] > 0 && hs[k].rr >= slot_rr_prev[k]) slot_stall[k]++;
+        // (a refined RHS is judged per slice in harvest, not by its global |r|)
+        if (!hs[k].refine && slot_outer[k] > 0 && hs[k].rr >= slot_rr_prev[k]) slot_stall[k]++;
         else slot_stall[k] = 0;
         slot_rr_prev[k] = hs[k].rr;
         if (slot_stall[k] >= 3 || slot_outer[k] >= max_outer || slot_inner[k] >= opts.max_iter) {
@@ -807,13 +822,30 @@ dp_status Batch::round()
     if (nact == 0) return DP_OK;
     for (int k = 0; k < n; k++)
         if (slot_job[k] && hs[k].active) slot_outer[k]++;
+    const bool refine = any_refining();
+    const Geom &g = f->g;
     {
         Timed tm(c, "outer_blas");
+        // refined RHS: |R r| in the inner solver's metric first (it may flag
+        // a non-finite RHS before the inner state is set up)
+        if (refine) {
+            CK(blas_ratio_norm(c->bc, r64, g, sp, n, alpha_d, alpha_in_d, slots_d, outer, c->stream));
+            c->launches++;
+        }
         CK(blas_inner_setup(outer, inner, n, opts.inner_tol, 0.0, c->stream));
         if (mixed)
             CK(blas_to_f32_scaled(r64, (float4 *)in.rh, Vh, n, outer, c->stream));
         else
             CK(blas_scale64(r64, (double2 *)in.rh, Vh, n, outer, c->stream));
+        if (refine) {
+            if (mixed)
+                CK(blas_to_f32_ratio(r64, (float4 *)in.rh, g, sp, n, alpha_d, alpha_in_d, slots_d, outer,
+                                     c->stream));
+            else
+                CK(blas_scale64_ratio(r64, (double2 *)in.rh, g, sp, n, alpha_d, alpha_in_d, slots_d,
+                                      outer, c->stream));
+            c->launches++;
+        }
     }
     c->launches += 2;
     // inner budget of this round
@@ -842,6 +874,15 @@ dp_status Batch::round()
             CK(blas_acc_f32(x, (const float4 *)in.x, Vh, n, outer, c->stream));
         else
             CK(blas_acc64(x, (const double2 *)in.x, Vh, n, outer, c->stream));
+        if (refine) {
+            if (mixed)
+                CK(blas_acc_f32_ratio(x, (const float4 *)in.x, g, sp, n, alpha_d, alpha_in_d, slots_d,
+                                      outer, c->stream));
+            else
+                CK(blas_acc64_ratio(x, (const double2 *)in.x, g, sp, n, alpha_d, alpha_in_d, slots_d,
+                                    outer, c->stream));
+            c->launches++;
+        }
     }
     // t64 keeps A_qq^-1 D_qp x of this (final, once converged) x: the
     // reconstruction of the other parity reuses it
@@ -855,6 +896,164 @@ dp_status Batch::round()
     return DP_OK;
 }
 
+bool Batch::any_refining() const
+{
+    for (const Job *j : jobs)
+        if (j && j->refining) return true;
+    return false;
+}
+
+dp_status Batch::set_inner_profile(const Job &j, const double *xx)
+{
+    const Geom &g = f->g;
+    const int Lm = g.Lmax, T = g.T, m = j.tab;
+    // alpha_B,t(t) = |x_src|/|x_t| in the restored metric (a slice without a
+    // usable norm keeps its neighbour's factor), times 1 in space
+    std::vector<double> tt(T), one(Lm, 1.0);
+    const int ts = j.grp.src[0];
+    const double ref = xx[ts];
+    double prev = 1.0;
+    for (int k = 0; k < T; k++) {
+        const int t = (ts + k) % T;
+        const double v = xx[t];
+        double a = (v > 0 && ref > 0 && std::isfinite(v)) ? std::sqrt(ref / v) : prev;
+        if (!(a > 0) || !std::isfinite(a)) a = prev;
+        tt[t] = prev = a;
+    }
+    dp_profile pf{};
+    pf.kind = DP_PROF_TABLE;
+    pf.table[0] = tt.data();
+    pf.table[1] = pf.table[2] = pf.table[3] = one.data();
+    std::vector<double> alpha(4 * Lm), hop(8 * Lm), hopa(8 * Lm);
+    dp_status s = profile_tables(pf, g, f->bc_t, j.grp.src, alpha.data(), hop.data());
+    if (s != DP_OK) return s;
+    for (size_t k = 0; k < hop.size(); k++) hopa[k] = hop[k] != 0.0 ? 0.25 / hop[k] : 0.0;
+    CK(cudaMemcpyAsync(alpha_in_d + (size_t)m * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm,
+                       cudaMemcpyHostToDevice, c->stream));
+    if (ipr == 0) {
+        CK(cudaMemcpyAsync(hopin64_d + (size_t)m * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm,
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(hopadj64_d + (size_t)m * 8 * Lm, hopa.data(), sizeof(double) * 8 * Lm,
+                           cudaMemcpyHostToDevice, c->stream));
+    } else {
+        std::vector<float> hf(hop.begin(), hop.end()), haf(hopa.begin(), hopa.end());
+        CK(cudaMemcpyAsync(hop32_d + (size_t)m * 8 * Lm, hf.data(), sizeof(float) * 8 * Lm,
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(hopadj32_d + (size_t)m * 8 * Lm, haf.data(), sizeof(float) * 8 * Lm,
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));  // the float vectors go away
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return DP_OK;
+}
+
+// Per-slice accuracy (slices.cu).  A job is checked when all its RHS passed
+// the global test, and after every refinement round.  Refinement gives up
+// (status 4: not converged) when two rounds in a row fail to halve the worst
+// slice residual, or after kMaxRefine rounds.
+dp_status Batch::slice_check(bool *changed)
+{
+    constexpr int kMaxRefine = 16;
+    const Geom &g = f->g;
+    const int T = g.T;
+    std::vector<Job *> cand;
+    int ng = 0;
+    for (int tab = 0; tab < kMaxGroups; tab++) {
+        Job *j = jobs[tab];
+        if (!j || !(j->slice_tol > 0)) continue;
+        bool any_active = false, all_ok = true;
+        for (int k = 0; k < j->ncomp; k++) {
+            const RhsState &st = hs[j->slot0 + k];
+            if (st.active) any_active = true;
+            else if (st.status != 1) all_ok = false;
+        }
+        const bool want = j->refining ? any_active : (!any_active && all_ok && !j->slice_ok);
+        if (want) {
+            cand.push_back(j);
+            ng = std::max(ng, tab + 1);
+        }
+    }
+    if (cand.empty()) return DP_OK;
+    std::vector<int> m(n, 0);
+    for (Job *j : cand)
+        for (int k = 0; k < j->ncomp; k++) m[j->slot0 + k] = 1;
+    dp_status s = upload_mask(m);
+    if (s != DP_OK) return s;
+    {
+        Timed tm(c, "slice_norms");
+        CK(launch_slice_norms(x, r64, g, sp, n, alpha_d, slots_d, ng, mask_d, cpart, slice_d,
+                              c->stream));
+    }
+    c->launches += 2;
+    CK(cudaMemcpyAsync(slice_h.data(), slice_d, sizeof(double) * ng * T * 2, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<double> xx(T);
+    for (Job *j : cand) {
+        const double *h = slice_h.data() + (size_t)j->tab * T * 2;
+        double worst = 0;
+        for (int t = 0; t < T; t++) {
+            const double a = h[2 * t], b = h[2 * t + 1];
+            xx[t] = a;
+            const double rho = a > 0 ? std::sqrt(b / a) : (b > 0 ? INFINITY : 0.0);
+            if (!(rho <= worst)) worst = rho;  // NaN propagates
+        }
+        j->slice_res = worst;
+        // inner reduction of the next refinement round: a tenth of the factor
+        // the worst slice still misses by (in the flattened metric the global
+        // reduction is about the per-slice one), at least the inner solver's
+        // own floor (the round's tolerance rides in the outer tol2, which the
+        // global test ignores for a refined RHS)
+        const double floor_tol = std::max(opts.inner_tol, 1e-12);
+        const double want = std::min(0.5, std::max(floor_tol, 0.1 * j->slice_tol / worst));
+        auto set_all = [&](int active, int status, int refine) {
+            for (int k = 0; k < j->ncomp; k++) {
+                RhsState &st = hs[j->slot0 + k];
+                st.active = active;
+                st.status = status;
+                st.refine = refine;
+                if (refine) st.tol2 = want * want;
+                slot_stall[j->slot0 + k] = 0;
+            }
+            *changed = true;
+        };
+        if (j->refining) j->refine_rounds++;  // a refinement round has just finished
+        if (worst <= j->slice_tol) {
+            j->slice_ok = true;
+            if (j->refining) set_all(0, 1, 0);
+            j->refining = false;
+        } else if (!j->refining) {
+            if (!std::isfinite(worst)) {
+                set_all(0, 3, 0);
+                continue;
+            }
+            j->refining = true;
+            j->refine_rounds = 0;
+            j->slice_best = worst;
+            j->slice_stall = 0;
+            s = set_inner_profile(*j, xx.data());
+            if (s != DP_OK) return s;
+            set_all(1, 0, 1);
+        } else {
+            if (worst < 0.5 * j->slice_best) {
+                j->slice_best = worst;
+                j->slice_stall = 0;
+            } else {
+                j->slice_stall++;
+            }
+            if (j->slice_stall >= 2 || j->refine_rounds >= kMaxRefine || !std::isfinite(worst)) {
+                set_all(0, std::isfinite(worst) ? 4 : 3, 0);
+                j->refining = false;
+            } else {
+                s = set_inner_profile(*j, xx.data());
+                if (s != DP_OK) return s;
+                set_all(1, 0, 1);  // the next round's tolerance
+            }
+        }
+    }
+    return DP_OK;
+}
+
 dp_status Batch::harvest(std::vector<Job *> &finished)
 {
     Timed tm(c, "harvest");
@@ -862,6 +1061,15 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
     const long long Vh = g.Vh;
     CK(cudaMemcpyAsync(hs.data(), outer, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    {
+        bool changed = false;
+        dp_status s = slice_check(&changed);
+        if (s != DP_OK) return s;
+        if (changed) {
+            CK(cudaMemcpyAsync(outer, hs.data(), sizeof(RhsState) * n, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+    }
     for (int tab = 0; tab < kMaxGroups; tab++) {
         Job *j = jobs[tab];
         if (!j) continue;
@@ -929,6 +1137,8 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
         SolveResult &R = j->res;
         R = SolveResult{};
         R.status = DP_OK;
+        R.slice_residue = j->slice_res;
+        R.refine_rounds = j->refine_rounds;
         for (int k = 0; k < j->ncomp; k++) {
             const int sl = j->slot0 + k;
             R.iters_inner = std::max(R.iters_inner, slot_inner[sl]);
@@ -993,6 +1203,7 @@ dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group
         j.comp0 = batched ? 0 : (int)k % 12;
         j.ncomp = batched ? 12 : 1;
         j.r = r_target;
+        j.slice_tol = slice_target(o.slice_tol, r_target);
         j.cpp_dst = cpp_dev + (size_t)gi * g.T;
         if (cap_dev) j.cap_dst = cap_dev + (size_t)gi * g.T;
         j.accumulate = batched ? 0 : (j.comp0 > 0);
@@ -1035,6 +1246,8 @@ dp_status solve_groups(Ctx *c, std::shared_ptr<Field> f, const std::vector<Group
                 R.iters_inner = std::max(R.iters_inner, J.iters_inner);
                 R.iters_outer = std::max(R.iters_outer, J.iters_outer);
                 R.true_rel_residue = std::max(R.true_rel_residue, J.true_rel_residue);
+                R.slice_residue = std::max(R.slice_residue, J.slice_residue);
+                R.refine_rounds = std::max(R.refine_rounds, J.refine_rounds);
                 if (J.status != DP_OK && R.status == DP_OK) R.status = J.status;
             }
         }
@@ -1134,6 +1347,8 @@ static dp_status solve_common(dp_ctx *ctx, dp_field field, int n_mass, const dou
                 info[k].iters_outer = res[k].iters_outer;
                 info[k].true_rel_residue = res[k].true_rel_residue;
                 info[k].status = res[k].status;
+                info[k].slice_residue = res[k].slice_residue;
+                info[k].refine_rounds = res[k].refine_rounds;
             } else {
                 info[k].status = s;
             }

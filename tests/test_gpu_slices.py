@@ -1,0 +1,103 @@
+"""Per-time-slice accuracy control of the outer loop, through the C ABI.
+
+A heavy quark (M = 0.8) solved with the steepening light-quark profile
+(cosh_4d, alpha0 = 0.4; Sec. III eq. betaa) on a 48x4^3 lattice: the global
+residue r = 1e-10 of the paper's stopping rule (Sec. I eq. stopping) is met
+while the far slices of the restored C_PP are still wrong (the effect of
+Sec. II).  The library measures the restored per-slice residual and refines
+until every slice meets its target; the result must then match the oracle to
+1e-6 per slice out to T/2, and an unreachable target must come back as
+DP_ERR_NOT_CONVERGED, not DP_OK.  A heavy profile matched to the decay rate
+needs at most one refinement round.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1006_4028_gb300 as dp
+from gpu_common import field, require_gpu, slice_rel
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (48, 4, 4, 4)  # C_PP falls with effective mass 1.40 (quark energy 0.70)
+M = 0.8
+STEEP = ("cosh_4d", 0.4)
+
+MIXED = {"prec": "mixed_fp32", "batched": 1, "use_graph": 1}
+PLAIN = {"prec": "fp64", "batched": 0, "use_graph": 0}
+FP64_BATCHED = {"prec": "fp64", "batched": 1, "use_graph": 0}
+MIXED_FP16 = {"prec": "mixed_fp16", "batched": 1, "use_graph": 1}
+CGNE_MIXED = {"prec": "mixed_fp32", "solver": "cgne", "batched": 1, "use_graph": 1}
+SAP_GCR = {"prec": "mixed_fp32", "solver": "sap_gcr", "batched": 1, "use_graph": 0}
+
+
+@pytest.fixture(scope="module")
+def setup():
+    require_gpu()
+    ctx = dp.dp_create(0)
+    U = field(DIMS, 0.3, 5)
+    f = dp.dp_field_load(ctx, U, DIMS, -1)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    op = oracle.WilsonClover(U, DIMS, 1.7, -1)
+    # reference: a flattening time profile keeps the oracle's far slices
+    # within its 1e-13 residue; certified by its own per-slice residuals
+    ref, S, info = oracle.solve_point(op, M, "cosh_t", 0.6, (0, 0, 0, 0), tol=1e-13)
+    assert info["converged"]
+    rho = oracle.slice_residuals(op, M, S, oracle.point_sources(DIMS, (0, 0, 0, 0)))
+    assert rho.max() < 1e-11
+    yield ctx, f, ref
+    dp.dp_destroy(ctx)
+
+
+def test_global_residue_alone_leaves_far_slices_wrong(setup):
+    """The failure the per-slice check exists for (check switched off)."""
+    ctx, f, ref = setup
+    o = dict(MIXED, slice_tol=-1.0)
+    cpp, _, info = dp.dp_solve_point(ctx, f, M, STEEP, (0, 0, 0, 0), 1e-10, o, T=DIMS[0])
+    assert info["status"] == 0
+    assert info["refine_rounds"] == 0 and info["slice_residue"] == 0.0
+    assert slice_rel(cpp, ref, DIMS[0] // 2) > 1e-4
+
+
+@pytest.mark.parametrize("opts", [MIXED, PLAIN, FP64_BATCHED, MIXED_FP16, CGNE_MIXED, SAP_GCR])
+def test_refinement_meets_per_slice_accuracy(setup, opts):
+    ctx, f, ref = setup
+    r = 1e-10
+    cpp, _, info = dp.dp_solve_point(ctx, f, M, STEEP, (0, 0, 0, 0), r, opts, T=DIMS[0])
+    assert info["status"] == 0, info
+    if opts is MIXED:  # the case shown to fail without the check
+        assert info["refine_rounds"] >= 1
+    assert 0 < info["slice_residue"] <= 10 * r
+    assert slice_rel(cpp, ref, DIMS[0] // 2) < 1e-6
+
+
+def test_unreachable_slice_target_is_not_ok(setup):
+    ctx, f, ref = setup
+    o = dict(MIXED, slice_tol=1e-19)
+    cpp, _, info = dp.dp_solve_point(ctx, f, M, STEEP, (0, 0, 0, 0), 1e-10, o, T=DIMS[0])
+    assert info["status"] == 3  # DP_ERR_NOT_CONVERGED, results still written
+    assert info["slice_residue"] > 1e-19
+    assert np.all(np.isfinite(cpp)) and np.all(cpp < 0)
+
+
+def test_matched_profile_needs_no_refinement(setup):
+    ctx, f, ref = setup
+    cpp, _, info = dp.dp_solve_point(ctx, f, M, ("cosh_t", 0.7), (0, 0, 0, 0), 1e-10, MIXED,
+                                     T=DIMS[0])
+    assert info["status"] == 0
+    assert info["refine_rounds"] <= 1
+    assert 0 < info["slice_residue"] <= 1e-9
+    assert slice_rel(cpp, ref, DIMS[0] // 2) < 1e-6
+
+
+def test_served_request_is_refined_too(setup):
+    """The scheduler applies the same per-slice target to a request."""
+    ctx, f, ref = setup
+    dp.dp_serve_start(ctx, 0, 12)
+    try:
+        t = dp.dp_submit(ctx, f, M, STEEP, (0, 0, 0, 0), 1e-10)
+        cpp, info = dp.dp_wait(ctx, t, DIMS[0], 120.0, allow=())
+    finally:
+        dp.dp_serve_stop(ctx, 1)
+    assert info["status"] == 0 and info["refine_rounds"] >= 1
+    assert slice_rel(cpp, ref, DIMS[0] // 2) < 1e-6
