@@ -6,6 +6,7 @@ import re
 import numpy as np
 import pytest
 
+import lattice_inputs as li
 import oracle
 import paper_1006_4028_gb300 as dp
 from paper_1006_4028_gb300 import build as dpbuild
@@ -161,3 +162,18 @@ def test_analysis_rejects_bad_windows(lib):
         dp.dp_fit_correlator(c, "cosh", 2, 5)     # past T
     m = dp.dp_effective_mass(c, "cosh")
     assert np.isfinite(m[0]) and np.isnan(m[1])
+
+
+def test_pcac_mass_matches_oracle(lib):
+    """The library's PCAC ratio (host function) against the oracle's on the
+    free correlators (whose plateau the oracle pins to the bare mass), and its
+    NaN ends and argument checks."""
+    dims, M = (16, 4, 4, 4), 0.05
+    op = oracle.WilsonClover(li.unit_links(dims), dims, csw=1.7, bc_t=-1)
+    cpp, _, info = oracle.solve_point(op, M, "none", 0.0, (0, 0, 0, 0), tol=1e-13)
+    got = dp.dp_pcac_mass(cpp, info["cap"])
+    ref = oracle.pcac_mass(cpp, info["cap"])
+    assert np.isnan(got[0]) and np.isnan(got[-1])
+    np.testing.assert_allclose(got[1:-1], ref[1:-1], rtol=1e-13, atol=0)
+    with pytest.raises(dp.DpError):
+        dp.dp_pcac_mass(cpp[:2], info["cap"][:2])

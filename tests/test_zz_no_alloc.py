@@ -7,13 +7,16 @@ serves them with a fixed scratch array inside the library.  Here it is called
 through the C ABI twice in a row, with different inputs, and must reproduce
 dp_restore_contract_dev (the allocating entry point) within the 1e-13
 tolerance of the contraction tests, including after the shared array has
-held another call's data.  This file runs last so that a failure here leaves
-every other result in place.
+held another call's data, and the oracle's restore and contraction of the
+same propagators (Sec. II eq. backcorrection; Sec. III, restore before
+contracting) within the same tolerance.  This file runs last so that a
+failure here leaves every other result in place.
 """
 import numpy as np
 import pytest
 
 import lattice_inputs as li
+import oracle
 import paper_1006_4028_gb300 as dp
 from gpu_common import require_gpu, torch
 
@@ -53,6 +56,12 @@ def test_noalloc_matches_allocating_entry_point_twice():
             r, g = ref.cpu().numpy(), got.cpu().numpy()
             assert np.all(np.isfinite(g))
             assert np.max(np.abs(g / r - 1)) < 1e-13
+            T = dims[0]
+            for k, (prof, src) in enumerate(groups):
+                al = oracle.profile_alpha(prof[0], prof[1], dims, src)
+                Sk = S[12 * k: 12 * (k + 1)].reshape((12,) + oracle.array_shape(dims) + (4, 3))
+                want = oracle.contract_cpp(oracle.restore(Sk, al, dims), dims, src[0])
+                assert np.max(np.abs(g[k * T:(k + 1) * T] / want - 1)) < 1e-13
             dp.dp_field_free(ctx, f)
     finally:
         dp.dp_destroy(ctx)
