@@ -92,7 +92,8 @@ class ServeStats(C.Structure):
     _fields_ = [("submitted", C.c_long), ("completed", C.c_long), ("rejected", C.c_long),
                 ("in_flight", C.c_long), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
                 ("mean_ms", C.c_double), ("solves_per_s", C.c_double),
-                ("hbm_budget", C.c_size_t), ("hbm_in_use", C.c_size_t)]
+                ("hbm_budget", C.c_size_t), ("hbm_in_use", C.c_size_t),
+                ("max_concurrent_batches", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

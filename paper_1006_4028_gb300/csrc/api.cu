@@ -79,18 +79,18 @@ cudaEvent_t Ctx::get_event()
     return e;
 }
 
-void Ctx::time_begin(const char *name, cudaEvent_t *a)
+void Ctx::time_begin(const char *name, cudaEvent_t *a, cudaStream_t st)
 {
     (void)name;
     *a = nullptr;
-    if (!timing) return;
+    if (!timing || (st && st != stream)) return;
     *a = get_event();
     cudaEventRecord(*a, stream);
 }
 
-void Ctx::time_end(const char *name, cudaEvent_t a)
+void Ctx::time_end(const char *name, cudaEvent_t a, cudaStream_t st)
 {
-    if (!timing || !a) return;
+    if (!timing || !a || (st && st != stream)) return;
     cudaEvent_t b = get_event();
     cudaEventRecord(b, stream);
     pending.push_back({name, a, b});

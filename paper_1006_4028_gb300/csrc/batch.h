@@ -36,6 +36,7 @@ struct Job {
 
 struct Op {
     const Field *f = nullptr;
+    cudaStream_t st = nullptr;  // the stream its launches go to
     int pr = 0;  // 0 FP64, 1 FP32
     int lf = 0;  // link format
     const void *links[2] = {nullptr, nullptr};  // per parity, in format lf
@@ -57,8 +58,11 @@ class Batch {
   public:
     // schur_parity: the parity p whose Schur system is solved; a job whose
     // source sits on parity p needs no dslash to set up its right-hand side
+    // own_stream: the batch runs on a stream of its own with its own reduction
+    // scratch (the scheduler runs one batch per field concurrently); else on
+    // the context stream with the context's scratch
     Batch(Ctx *c, std::shared_ptr<Field> f, int nslots, const dp_solve_opts &o, int round_cap,
-          int schur_parity = 0);
+          int schur_parity = 0, bool own_stream = false);
     ~Batch();
     Batch(const Batch &) = delete;
     Batch &operator=(const Batch &) = delete;
@@ -102,6 +106,10 @@ class Batch {
 
     Ctx *c;
     std::shared_ptr<Field> f;
+    bool own_stream_ = false;
+    cudaStream_t st_ = nullptr;
+    BlasCtx bc_{};
+    int *hnact_ = nullptr;  // pinned
     int n;
     dp_solve_opts opts;
     int round_iters;

@@ -1,14 +1,18 @@
 // Request scheduler: continuous batching of point-source solves over the
 // gauge fields resident in a context.
 //
-// A scheduler thread keeps one solver batch (see solver.cu) per field with
-// queued or running work.  Between defect-correction rounds it completes the
-// jobs whose RHS have all converged, frees their slots, and admits queued
+// One solver batch (see solver.cu) per field with queued or running work,
+// each on a CUDA stream of its own and driven by a worker thread of its own,
+// so the rounds of different fields (different lattice volumes) run
+// concurrently on the device.  Between defect-correction rounds a worker
+// completes the jobs whose RHS have all converged (and met their per-slice
+// accuracy target), frees their slots, and admits its field's queued
 // requests into free slots, so requests that arrive while others are on the
-// GPU join the running batch.  A batch's device memory is counted against
-// the HBM budget; a request whose field has no batch waits until a new batch
-// fits the budget, and one that can never fit is rejected at submit time.
-// Latency is measured from submit to completion on the host clock.
+// GPU join the running batch.  A coordinator thread creates a field's batch
+// when its device memory fits the HBM budget and retires idle batches when
+// other fields wait for memory; a request that can never fit is rejected at
+// submit time.  Latency is measured from submit to completion on the host
+// clock.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -33,6 +37,20 @@ struct Request {
     std::shared_ptr<Field> field;
 };
 
+struct Scheduler;
+
+// one field's batch and the thread that runs its rounds
+struct Worker {
+    uint64_t fid = 0;
+    std::shared_ptr<Field> field;
+    std::unique_ptr<Batch> B;
+    std::thread th;
+    size_t bytes = 0;
+    bool stop = false;     // set by the coordinator (under Scheduler::mu)
+    bool finished = false; // the thread has left its loop
+    int running = 0;       // jobs in the batch (under Scheduler::mu)
+};
+
 struct Scheduler {
     Ctx *c;
     std::thread th;
@@ -40,8 +58,7 @@ struct Scheduler {
     std::condition_variable cv, done_cv;
     std::deque<std::shared_ptr<Request>> queue;
     std::map<dp_ticket, std::shared_ptr<Request>> all;
-    std::map<uint64_t, std::unique_ptr<Batch>> batches;  // by field id
-    std::map<uint64_t, uint64_t> field_of_batch;
+    std::map<uint64_t, std::unique_ptr<Worker>> workers;  // by field id
     bool stop = false, drain = true;
     size_t budget = 0, in_use = 0;
     int max_slots = 48;
@@ -49,156 +66,190 @@ struct Scheduler {
     long submitted = 0, completed = 0, rejected = 0;
     std::vector<double> lat_ms;
     Clock::time_point first_done, last_done;
+    int in_round = 0, max_in_round = 0;  // batches inside a round at once
     dp_solve_opts opts{};
 
-    void run();
+    void run();            // coordinator
+    void work(Worker *w);  // a field's batch
+    // (under mu) a request ends with a status
+    void finish(Request *rq, dp_status s, const char *why);
 };
 
 void SchedDeleter::operator()(Scheduler *s) const { delete s; }
 
-void Scheduler::run()
+void Scheduler::finish(Request *rq, dp_status s, const char *why)
+{
+    rq->status = s;
+    if (s != DP_OK) rq->err = why;
+    rq->done = true;
+    rq->t_done = Clock::now();
+    rq->field->users--;
+}
+
+void Scheduler::work(Worker *w)
 {
     cudaSetDevice(c->device);
     std::unique_lock<std::mutex> lk(mu);
     while (true) {
-        // admit queued requests into batches (FIFO per field)
+        Batch &B = *w->B;  // (replaced after a failing round)
+        // admit this field's queued requests into free slots (FIFO)
         for (auto it = queue.begin(); it != queue.end();) {
             auto rq = *it;
             if (rq->cancelled) {
                 it = queue.erase(it);
                 continue;
             }
-            const uint64_t fid = rq->req.field;
-            auto bit = batches.find(fid);
-            if (bit == batches.end()) {
-                const size_t need = Batch::bytes_needed(rq->field->g, max_slots, rq->req.prec);
-                if (in_use + need > budget) {
-                    ++it;
-                    continue;
-                }
-                auto b = std::make_unique<Batch>(c, rq->field, max_slots, opts, 200);
-                lk.unlock();
-                dp_status s = b->init();
-                lk.lock();
-                if (s != DP_OK) {
-                    rq->status = s;
-                    rq->err = dp_last_error();
-                    rq->done = true;
-                    rq->t_done = Clock::now();
-                    rq->field->users--;
-                    it = queue.erase(it);
-                    done_cv.notify_all();
-                    continue;
-                }
-                in_use += b->bytes();
-                bit = batches.emplace(fid, std::move(b)).first;
+            if (rq->req.field != w->fid) {
+                ++it;
+                continue;
             }
-            Batch &B = *bit->second;
-            if (!B.can_admit(12)) {
+            if (!B.can_admit(12)) break;
+            queue.erase(it);
+            rq->admitted = true;
+            lk.unlock();
+            dp_status s = B.admit(&rq->job);
+            std::string msg = s != DP_OK ? dp_last_error() : "";
+            lk.lock();
+            // the queue may have changed while unlocked (submits, other
+            // fields' workers): its iterators are stale, scan it afresh
+            it = queue.begin();
+            if (s != DP_OK) {
+                finish(rq.get(), s, msg.c_str());
+                done_cv.notify_all();
+                continue;
+            }
+            w->running++;
+        }
+        if (B.active_jobs() == 0) {
+            if (w->stop) break;
+            cv.wait_for(lk, std::chrono::milliseconds(20));
+            continue;
+        }
+        in_round++;
+        max_in_round = std::max(max_in_round, in_round);
+        lk.unlock();
+        std::vector<Job *> fin;
+        dp_status s = B.round();
+        if (s == DP_OK) s = B.harvest(fin);
+        std::string msg = s != DP_OK ? dp_last_error() : "";
+        lk.lock();
+        in_round--;
+        for (Job *j : fin) {
+            Request *rq = static_cast<Request *>(j->user);
+            const dp_status st = (dp_status)j->res.status;
+            finish(rq, st, st == DP_ERR_NOT_CONVERGED
+                               ? "solve did not reach the requested residue or per-slice accuracy"
+                               : "solve failed");
+            w->running--;
+            completed++;
+            lat_ms.push_back(std::chrono::duration<double, std::milli>(rq->t_done - rq->t_submit).count());
+            if (completed == 1) first_done = rq->t_done;
+            last_done = rq->t_done;
+        }
+        if (s != DP_OK) {
+            // a failing batch fails its running jobs and starts afresh
+            for (auto &ar : all)
+                if (ar.second->admitted && !ar.second->done && ar.second->req.field == w->fid)
+                    finish(ar.second.get(), s, msg.c_str());
+            w->running = 0;
+            lk.unlock();
+            w->B.reset(new Batch(c, w->field, max_slots, opts, 200, 0, true));
+            dp_status e = w->B->init();
+            lk.lock();
+            done_cv.notify_all();
+            if (e != DP_OK) break;
+            continue;
+        }
+        if (!fin.empty()) done_cv.notify_all();
+    }
+    w->finished = true;
+    cv.notify_all();
+}
+
+void Scheduler::run()
+{
+    cudaSetDevice(c->device);
+    std::unique_lock<std::mutex> lk(mu);
+    while (true) {
+        // a batch for every field with queued requests, as the budget allows
+        for (auto &rq : queue) {
+            if (rq->cancelled) continue;
+            const uint64_t fid = rq->req.field;
+            if (workers.count(fid)) continue;
+            const size_t need = Batch::bytes_needed(rq->field->g, max_slots, rq->req.prec);
+            if (in_use + need > budget) continue;
+            auto w = std::make_unique<Worker>();
+            w->fid = fid;
+            w->field = rq->field;
+            w->bytes = need;
+            in_use += need;
+            Worker *wp = w.get();
+            workers.emplace(fid, std::move(w));
+            lk.unlock();
+            wp->B = std::make_unique<Batch>(c, wp->field, max_slots, opts, 200, 0, true);
+            dp_status s = wp->B->init();
+            std::string msg = s != DP_OK ? dp_last_error() : "";
+            lk.lock();
+            if (s != DP_OK) {
+                for (auto it = queue.begin(); it != queue.end();) {
+                    if ((*it)->req.field == fid) {
+                        finish(it->get(), s, msg.c_str());
+                        it = queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+                lk.unlock();
+                wp->B.reset();
+                lk.lock();
+                in_use -= wp->bytes;
+                workers.erase(fid);
+                done_cv.notify_all();
+                break;  // the queue changed under the loop
+            }
+            wp->th = std::thread([this, wp] { work(wp); });
+            break;  // the queue iterator may be stale after unlocking
+        }
+        // retire idle batches when other fields wait for memory
+        bool waiting_other = false;
+        for (auto &rq : queue)
+            if (!rq->cancelled && !workers.count(rq->req.field)) waiting_other = true;
+        for (auto &kv : workers) {
+            Worker &w = *kv.second;
+            bool queued_here = false;
+            for (auto &rq : queue)
+                if (rq->req.field == kv.first && !rq->cancelled) queued_here = true;
+            const bool idle = w.running == 0 && !queued_here;
+            if (idle && (waiting_other || stop)) w.stop = true;
+        }
+        for (auto it = workers.begin(); it != workers.end();) {
+            Worker &w = *it->second;
+            if (!w.finished) {
                 ++it;
                 continue;
             }
             lk.unlock();
-            dp_status s = B.admit(&rq->job);
+            if (w.th.joinable()) w.th.join();
+            w.B.reset();
             lk.lock();
-            if (s != DP_OK) {
-                rq->status = s;
-                rq->err = dp_last_error();
-                rq->done = true;
-                rq->t_done = Clock::now();
-                rq->field->users--;
-                it = queue.erase(it);
-                done_cv.notify_all();
-                continue;
-            }
-            rq->admitted = true;
-            it = queue.erase(it);
+            in_use -= w.bytes;
+            it = workers.erase(it);
         }
-        // one round per batch with work, then complete finished jobs
-        bool worked = false;
-        for (auto &kv : batches) {
-            Batch &B = *kv.second;
-            if (B.active_jobs() == 0) continue;
-            worked = true;
-            lk.unlock();
-            std::vector<Job *> fin;
-            dp_status s = B.round();
-            if (s == DP_OK) s = B.harvest(fin);
-            lk.lock();
-            for (Job *j : fin) {
-                Request *rq = static_cast<Request *>(j->user);
-                rq->status = (dp_status)j->res.status;
-                if (rq->status != DP_OK)
-                    rq->err = rq->status == DP_ERR_NOT_CONVERGED ? "solve did not reach the requested residue "
-                                                                   "or per-slice accuracy"
-                                                                 : "solve failed";
-                rq->done = true;
-                rq->t_done = Clock::now();
-                rq->field->users--;
-                completed++;
-                lat_ms.push_back(std::chrono::duration<double, std::milli>(rq->t_done - rq->t_submit).count());
-                if (completed == 1) first_done = rq->t_done;
-                last_done = rq->t_done;
-            }
-            if (s != DP_OK) {
-                // a failing batch fails its running jobs
-                for (auto &ar : all)
-                    if (ar.second->admitted && !ar.second->done &&
-                        ar.second->req.field == kv.first) {
-                        ar.second->status = s;
-                        ar.second->err = dp_last_error();
-                        ar.second->done = true;
-                        ar.second->t_done = Clock::now();
-                        ar.second->field->users--;
-                    }
-                kv.second.reset(new Batch(c, kv.second->field(), max_slots, opts, 200));
-                lk.unlock();
-                kv.second->init();
-                lk.lock();
-            }
-            if (!fin.empty()) done_cv.notify_all();
-        }
-        // release idle batches when other fields wait for memory
-        if (!queue.empty()) {
-            for (auto it = batches.begin(); it != batches.end();) {
-                bool waiting_here = false;
-                for (auto &rq : queue)
-                    if (rq->req.field == it->first) waiting_here = true;
-                if (it->second->active_jobs() == 0 && !waiting_here) {
-                    in_use -= it->second->bytes();
-                    lk.unlock();
-                    it->second.reset();
-                    lk.lock();
-                    it = batches.erase(it);
-                } else {
-                    ++it;
+        if (stop) {
+            if (!drain) {
+                for (auto &rq : queue) {
+                    if (rq->cancelled) continue;
+                    rq->cancelled = true;
+                    finish(rq.get(), DP_ERR_REJECTED, "scheduler stopped");
                 }
+                queue.clear();
+                done_cv.notify_all();
             }
+            if (queue.empty() && workers.empty()) break;
         }
-        if (stop && (queue.empty() || !drain)) {
-            bool running = false;
-            for (auto &kv : batches)
-                if (kv.second->active_jobs()) running = true;
-            if (!running) break;
-        }
-        if (!worked) {
-            if (stop && queue.empty()) break;
-            cv.wait_for(lk, std::chrono::milliseconds(queue.empty() ? 50 : 2));
-        }
+        cv.wait_for(lk, std::chrono::milliseconds(10));
     }
-    // cancel what is left
-    for (auto &rq : queue) {
-        rq->status = DP_ERR_REJECTED;
-        rq->done = true;
-        rq->cancelled = true;
-        rq->field->users--;
-    }
-    queue.clear();
     done_cv.notify_all();
-    lk.unlock();
-    for (auto &kv : batches) kv.second.reset();
-    batches.clear();
-    in_use = 0;
 }
 
 }  // namespace dp
@@ -441,6 +492,7 @@ dp_status dp_serve_stats_get(dp_ctx *ctx, dp_serve_stats *out)
     }
     out->hbm_budget = S.budget;
     out->hbm_in_use = S.in_use;
+    out->max_concurrent_batches = S.max_in_round;
     return DP_OK;
 }
 

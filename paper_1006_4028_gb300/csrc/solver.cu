@@ -50,8 +50,9 @@ struct Timed {
     Ctx *c;
     const char *name;
     cudaEvent_t ev;
-    Timed(Ctx *c_, const char *n) : c(c_), name(n) { c->time_begin(name, &ev); }
-    ~Timed() { c->time_end(name, ev); }
+    cudaStream_t st;
+    Timed(Ctx *c_, cudaStream_t s, const char *n) : c(c_), name(n), st(s) { c->time_begin(name, &ev, st); }
+    ~Timed() { c->time_end(name, ev, st); }
 };
 
 dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void *out,
@@ -74,7 +75,7 @@ dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void
     memcpy(P.grp_of, op.grp_of, sizeof P.grp_of);
     const char *name = op.pr == 0 ? "dslash_fp64" : "dslash_fp32";
     cudaEvent_t ev;
-    c->time_begin(name, &ev);
+    c->time_begin(name, &ev, op.st);
     const bool schur = epi == EPI_AINV || epi == EPI_XMY_AINV;
     const int rpt = schur ? op.rpt : (op.pr == 0 ? 1 : 2);
     // the Schur launches take the tuned shape; the adjoint's x - g5 D launch
@@ -82,8 +83,8 @@ dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void
     const bool shaped = schur || (epi == EPI_XMY_G5 && op.stages == 6);
     const int stages =
         shaped && dslash_staged_ok(op.pr, op.lf, epi, rpt, op.stages, op.block) ? op.stages : 0;
-    CK(launch_dslash(P, op.pr, op.lf, epi, op.block, rpt, c->stream, stages));
-    c->time_end(name, ev);
+    CK(launch_dslash(P, op.pr, op.lf, epi, op.block, rpt, op.st, stages));
+    c->time_end(name, ev, op.st);
     c->launches++;
     return DP_OK;
 }
@@ -129,9 +130,9 @@ dp_status apply_mhat_dag(Ctx *c, const Op &op, const Op &op_adj, int p, const vo
     cp.Vh = op.f->g.Vh;
     cp.nrhs = op.nrhs;
     cudaEvent_t ev;
-    c->time_begin("clover_apply", &ev);
-    CK(launch_clover_apply(cp, op.pr, c->stream));
-    c->time_end("clover_apply", ev);
+    c->time_begin("clover_apply", &ev, op.st);
+    CK(launch_clover_apply(cp, op.pr, op.st));
+    c->time_end("clover_apply", ev, op.st);
     c->launches++;
     dp_status s = dslash(c, op_adj, 1 - p, EPI_AINV, tmp_p, tmp_q, nullptr, state_mask(mask), kStateStride);
     if (s != DP_OK) return s;
@@ -141,20 +142,32 @@ dp_status apply_mhat_dag(Ctx *c, const Op &op, const Op &op_adj, int p, const vo
 }  // namespace
 
 Batch::Batch(Ctx *cc, std::shared_ptr<Field> ff, int nslots, const dp_solve_opts &o, int round_cap,
-             int schur_parity)
-    : c(cc), f(std::move(ff)), n(nslots), opts(o), round_iters(round_cap), sp(schur_parity & 1)
+             int schur_parity, bool own_stream)
+    : c(cc), f(std::move(ff)), own_stream_(own_stream), n(nslots), opts(o), round_iters(round_cap),
+      sp(schur_parity & 1)
 {
+    st_ = c->stream;
+    bc_ = c->bc;
+    hnact_ = c->h_nactive;
 }
 
 Batch::~Batch()
 {
+    if (own_stream_ && st_) cudaStreamSynchronize(st_);  // the memory below is in use there
     if (graph) cudaGraphExecDestroy(graph);
     for (void *p : owned) c->release(p);
+    if (own_stream_) {
+        if (st_) cudaStreamDestroy(st_);
+        if (hnact_) cudaFreeHost(hnact_);
+    }
 }
 
 void *Batch::get(size_t bytes)
 {
     void *p = c->alloc(bytes);
+    // pool memory is usable on another stream once the context stream has
+    // reached its allocation
+    if (p && own_stream_ && cudaStreamSynchronize(c->stream) != cudaSuccess) p = nullptr;
     if (p) {
         owned.push_back(p);
         total_bytes += bytes;
@@ -172,6 +185,21 @@ size_t Batch::bytes_needed(const Geom &g, int nslots, int prec)
 dp_status Batch::init()
 {
     const Geom &g = f->g;
+    if (own_stream_) {
+        st_ = nullptr;
+        hnact_ = nullptr;
+        CK(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
+        CK(cudaMallocHost(&hnact_, sizeof(int)));
+        bc_ = BlasCtx{};
+        bc_.blocks = c->bc.blocks;
+        bc_.partials = (double *)get((size_t)bc_.blocks * kMaxRhs * kRedWidth * sizeof(double));
+        bc_.counter = (unsigned int *)get(256);
+        bc_.n_active = (int *)get(256);
+        if (!bc_.partials || !bc_.counter || !bc_.n_active) {
+            set_error("out of device memory for a solver batch's reduction scratch");
+            return DP_ERR_OOM;
+        }
+    }
     mixed = opts.prec != DP_PREC_FP64;
     ipr = mixed ? 1 : 0;
     ilf = inner_link_format(opts.prec, opts.compress12);
@@ -223,19 +251,20 @@ dp_status Batch::init()
     slot_rr_prev.assign(n, 0.0);
     slot_stall.assign(n, 0);
     slots.assign(kMaxRhs, SlotInfo{});
-    CK(cudaMemsetAsync(outer, 0, sizeof(RhsState) * kMaxRhs, c->stream));
-    CK(cudaMemsetAsync(inner, 0, sizeof(RhsState) * kMaxRhs, c->stream));
-    CK(cudaMemsetAsync(alpha_d, 0, sizeof(double) * kMaxGroups * 4 * Lm, c->stream));
-    CK(cudaMemsetAsync(alpha_in_d, 0, sizeof(double) * kMaxGroups * 4 * Lm, c->stream));
-    if (hopin64_d) CK(cudaMemsetAsync(hopin64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, c->stream));
+    CK(cudaMemsetAsync(outer, 0, sizeof(RhsState) * kMaxRhs, st_));
+    CK(cudaMemsetAsync(inner, 0, sizeof(RhsState) * kMaxRhs, st_));
+    CK(cudaMemsetAsync(alpha_d, 0, sizeof(double) * kMaxGroups * 4 * Lm, st_));
+    CK(cudaMemsetAsync(alpha_in_d, 0, sizeof(double) * kMaxGroups * 4 * Lm, st_));
+    if (hopin64_d) CK(cudaMemsetAsync(hopin64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, st_));
     slice_h.assign((size_t)kMaxGroups * 2 * g.T, 0.0);
-    CK(cudaMemsetAsync(hop64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, c->stream));
-    CK(cudaMemsetAsync(hop32_d, 0, sizeof(float) * kMaxGroups * 8 * Lm, c->stream));
-    CK(cudaMemsetAsync(hopadj64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, c->stream));
-    CK(cudaMemsetAsync(hopadj32_d, 0, sizeof(float) * kMaxGroups * 8 * Lm, c->stream));
+    CK(cudaMemsetAsync(hop64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, st_));
+    CK(cudaMemsetAsync(hop32_d, 0, sizeof(float) * kMaxGroups * 8 * Lm, st_));
+    CK(cudaMemsetAsync(hopadj64_d, 0, sizeof(double) * kMaxGroups * 8 * Lm, st_));
+    CK(cudaMemsetAsync(hopadj32_d, 0, sizeof(float) * kMaxGroups * 8 * Lm, st_));
 
     op64 = Op{};
     op64.f = f.get();
+    op64.st = st_;
     op64.pr = 0;
     op64.lf = LINK_F64_18;
     op64.links[0] = f->l64[0];
@@ -284,7 +313,7 @@ dp_status Batch::init()
             set_error("out of device memory for the double-float outer operator");
             return DP_ERR_OOM;
         }
-        CK(cudaMemsetAsync(hopdf_d, 0, sizeof(float2) * kMaxGroups * 8 * Lm, c->stream));
+        CK(cudaMemsetAsync(hopdf_d, 0, sizeof(float2) * kMaxGroups * 8 * Lm, st_));
         opdf = op64;
         opdf.lf = LINK_DF_18;
         for (int p = 0; p < 2; p++) {
@@ -294,6 +323,13 @@ dp_status Batch::init()
         opdf.hop = hopdf_d;
     }
     check_every = opts.check_every > 0 ? opts.check_every : (Vh * n >= (1 << 20) ? 2 : 8);
+    if (own_stream_) {
+        // memory from the context's stream-ordered pool becomes usable on
+        // this batch's stream once the context stream has reached it
+        CK(cudaMemsetAsync(bc_.counter, 0, 256, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    CK(cudaStreamSynchronize(st_));
     return DP_OK;
 }
 
@@ -326,15 +362,15 @@ bool Batch::can_admit(int ncomp) const
 
 dp_status Batch::upload_mask(const std::vector<int> &m)
 {
-    CK(cudaMemcpyAsync(mask_d, m.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(mask_d, m.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st_));
     // the host vector may go away: make the copy complete before returning
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaStreamSynchronize(st_));
     return DP_OK;
 }
 
 dp_status Batch::admit(Job *j)
 {
-    Timed tm(c, "admit");
+    Timed tm(c, st_, "admit");
     const Geom &g = f->g;
     const int Lm = g.Lmax;
     int tab = -1, s0 = -1;
@@ -374,8 +410,8 @@ dp_status Batch::admit(Job *j)
     std::vector<double> hopa(hop.size());
     for (size_t k = 0; k < hop.size(); k++) hopa[k] = hop[k] != 0.0 ? 0.25 / hop[k] : 0.0;
     std::vector<float> hopaf(hopa.begin(), hopa.end());
-    CK(cudaMemcpyAsync(hopadj64_d + (size_t)tab * 8 * Lm, hopa.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(hopadj32_d + (size_t)tab * 8 * Lm, hopaf.data(), sizeof(float) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(hopadj64_d + (size_t)tab * 8 * Lm, hopa.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(hopadj32_d + (size_t)tab * 8 * Lm, hopaf.data(), sizeof(float) * 8 * Lm, cudaMemcpyHostToDevice, st_));
     if (hopdf_d) {
         // double-float hop factors: nearest float, then the nearest float of the rest
         std::vector<float2> hd(hop.size());
@@ -384,19 +420,19 @@ dp_status Batch::admit(Job *j)
             hd[k] = make_float2(hi, (float)(hop[k] - (double)hi));
         }
         CK(cudaMemcpyAsync(hopdf_d + (size_t)tab * 8 * Lm, hd.data(), sizeof(float2) * 8 * Lm,
-                           cudaMemcpyHostToDevice, c->stream));
+                           cudaMemcpyHostToDevice, st_));
         s = clover_inv_df(c, *f, *ci);
         if (s != DP_OK) return s;
         for (int p = 0; p < 2; p++) opdf.inv[p][tab] = ci->invdf[p];
     }
-    CK(cudaMemcpyAsync(alpha_d + (size_t)tab * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(alpha_in_d + (size_t)tab * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(alpha_d + (size_t)tab * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm, cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(alpha_in_d + (size_t)tab * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm, cudaMemcpyHostToDevice, st_));
     if (hopin64_d)
-        CK(cudaMemcpyAsync(hopin64_d + (size_t)tab * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(hop64_d + (size_t)tab * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(hop32_d + (size_t)tab * 8 * Lm, hopf.data(), sizeof(float) * 8 * Lm, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(hopin64_d + (size_t)tab * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(hop64_d + (size_t)tab * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm, cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(hop32_d + (size_t)tab * 8 * Lm, hopf.data(), sizeof(float) * 8 * Lm, cudaMemcpyHostToDevice, st_));
     const int ts = j->grp.src[0];
-    CK(cudaMemcpyAsync(tsrc_d + tab, &ts, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(tsrc_d + tab, &ts, sizeof(int), cudaMemcpyHostToDevice, st_));
     invs[tab] = ci;
     for (int p = 0; p < 2; p++) {
         op64.inv[p][tab] = ci->inv64[p];
@@ -420,7 +456,7 @@ dp_status Batch::admit(Job *j)
         slot_rr_prev[s0 + k] = 0;
         slot_stall[s0 + k] = 0;
     }
-    CK(cudaMemcpyAsync(slots_d + s0, &slots[s0], sizeof(SlotInfo) * j->ncomp, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(slots_d + s0, &slots[s0], sizeof(SlotInfo) * j->ncomp, cudaMemcpyHostToDevice, st_));
     j->tab = tab;
     j->slot0 = s0;
     j->src_scale = scale;
@@ -439,10 +475,10 @@ dp_status Batch::admit(Job *j)
     const long long Vh = g.Vh;
     // eta'_p -> y64, eta'_q -> to64 (p = Schur parity; only this job's slots
     // are non-zero)
-    CK(cudaMemsetAsync(y64, 0, v64, c->stream));
-    CK(cudaMemsetAsync(to64, 0, v64, c->stream));
+    CK(cudaMemsetAsync(y64, 0, v64, st_));
+    CK(cudaMemsetAsync(to64, 0, v64, st_));
     CK(launch_point_source(g, slots_d, n, mask_d, sp == 0 ? y64 : to64, sp == 0 ? to64 : y64,
-                           c->stream));
+                           st_));
     CloverApplyParams cp{};
     memcpy(cp.grp_of, op64.grp_of, sizeof cp.grp_of);
     cp.mask = mask_d;
@@ -455,20 +491,20 @@ dp_status Batch::admit(Job *j)
         for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[sp][k];
         cp.in = y64;
         cp.out = bh;
-        CK(blas_zero_masked(bh, Vh, n, mask_d, c->stream));
-        CK(launch_clover_point(cp, g, slots_d, sp, c->stream));
+        CK(blas_zero_masked(bh, Vh, n, mask_d, st_));
+        CK(launch_clover_point(cp, g, slots_d, sp, st_));
     } else {
         // to64 <- A_qq^-1 eta'_q (in place, at the source site), bhat =
         // A_pp^-1 (eta'_p - D_pq to64)
         for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[1 - sp][k];
         cp.in = to64;
         cp.out = to64;
-        CK(launch_clover_point(cp, g, slots_d, 1 - sp, c->stream));
+        CK(launch_clover_point(cp, g, slots_d, 1 - sp, st_));
         s = dslash(c, op64, sp, EPI_AINV_XMY, to64, bh, y64, mask_d, 1);
         if (s != DP_OK) return s;
     }
-    CK(blas_zero_masked(x, Vh, n, mask_d, c->stream));
-    CK(blas_zero_masked(t64, Vh, n, mask_d, c->stream));
+    CK(blas_zero_masked(x, Vh, n, mask_d, st_));
+    CK(blas_zero_masked(t64, Vh, n, mask_d, st_));
     // outer state rows: active, fresh (r = bhat, |bhat|^2 sets the threshold)
     for (int k = 0; k < j->ncomp; k++) {
         RhsState st{};
@@ -477,33 +513,33 @@ dp_status Batch::admit(Job *j)
         st.tol2 = j->r * j->r;
         hs[s0 + k] = st;
     }
-    CK(cudaMemcpyAsync(outer + s0, &hs[s0], sizeof(RhsState) * j->ncomp, cudaMemcpyHostToDevice, c->stream));
-    CK(blas_residual64(c->bc, bh, y64, r64, Vh, n, outer, mask_d, c->stream));
+    CK(cudaMemcpyAsync(outer + s0, &hs[s0], sizeof(RhsState) * j->ncomp, cudaMemcpyHostToDevice, st_));
+    CK(blas_residual64(bc_, bh, y64, r64, Vh, n, outer, mask_d, st_));
     c->launches += 5;
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaStreamSynchronize(st_));
     return DP_OK;
 }
 
 dp_status Batch::bicgstab(int max_iter, int *iters_done)
 {
-    BlasCtx &bc = c->bc;
+    BlasCtx &bc = bc_;
     const int pr = opin.pr;
     const long long Vh = f->g.Vh;
     // FP32: the p update rides in the x, r update pass (blas32_update_p)
     const bool fused = pr == 1;
     if (fused) {
-        CK(cudaMemsetAsync(in.x, 0, vin, c->stream));
-        CK(cudaMemsetAsync(in.v, 0, vin, c->stream));
-        CK(blas32_init(bc, in.rh, in.r, in.rh, Vh, n, inner, c->stream, in.p));
-        CK(blas_count_active(bc, inner, n, c->stream));
+        CK(cudaMemsetAsync(in.x, 0, vin, st_));
+        CK(cudaMemsetAsync(in.v, 0, vin, st_));
+        CK(blas32_init(bc, in.rh, in.r, in.rh, Vh, n, inner, st_, in.p));
+        CK(blas_count_active(bc, inner, n, st_));
     } else {
-        CK(blas_bicg_init(bc, pr, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, c->stream));
+        CK(blas_bicg_init(bc, pr, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, st_));
     }
     c->launches += 2;
-    CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(hnact_, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
     int it = 0;
-    if (*c->h_nactive == 0) {
+    if (*hnact_ == 0) {
         *iters_done = 0;
         return DP_OK;
     }
@@ -511,23 +547,23 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
         dp_status s = apply_mhat(c, opin, sp, in.p, in.v, in.to, inner);
         if (s != DP_OK) return s;
         {
-            Timed tm(c, "blas_inner");
-            CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, c->stream));
+            Timed tm(c, st_, "blas_inner");
+            CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, st_));
         }
         {
-            Timed tm(c, "blas_inner");
-            CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, c->stream));
+            Timed tm(c, st_, "blas_inner");
+            CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, st_));
         }
         s = apply_mhat(c, opin, sp, in.s, in.t, in.to, inner);
         if (s != DP_OK) return s;
         {
-            Timed tm(c, "blas_inner");
-            CK(blas32_omega_rho(bc, in.t, in.s, in.rh, Vh, n, inner, c->stream));
+            Timed tm(c, st_, "blas_inner");
+            CK(blas32_omega_rho(bc, in.t, in.s, in.rh, Vh, n, inner, st_));
         }
         {
-            Timed tm(c, "blas_inner");
+            Timed tm(c, st_, "blas_inner");
             CK(blas32_update_p(bc, in.x, in.r, in.p, in.s, in.t, in.v, Vh, n, inner, max_iter,
-                               c->stream));
+                               st_));
         }
         c->launches += 5;
         return DP_OK;
@@ -535,29 +571,29 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
     auto body = [&](int first) -> dp_status {
         if (fused) return body_fused();
         {
-            Timed tm(c, "blas_inner");
-            CK(blas_bicg_p(bc, pr, in.r, in.p, in.v, Vh, n, inner, first, c->stream));
+            Timed tm(c, st_, "blas_inner");
+            CK(blas_bicg_p(bc, pr, in.r, in.p, in.v, Vh, n, inner, first, st_));
         }
         dp_status s = apply_mhat(c, opin, sp, in.p, in.v, in.to, inner);
         if (s != DP_OK) return s;
         {
-            Timed tm(c, "blas_inner");
-            CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, c->stream));
+            Timed tm(c, st_, "blas_inner");
+            CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, st_));
         }
         {
-            Timed tm(c, "blas_inner");
-            CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, c->stream));
+            Timed tm(c, st_, "blas_inner");
+            CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, st_));
         }
         s = apply_mhat(c, opin, sp, in.s, in.t, in.to, inner);
         if (s != DP_OK) return s;
         {
-            Timed tm(c, "blas_inner");
-            CK(blas_bicg_omega(bc, pr, in.t, in.s, Vh, n, inner, c->stream));
+            Timed tm(c, st_, "blas_inner");
+            CK(blas_bicg_omega(bc, pr, in.t, in.s, Vh, n, inner, st_));
         }
         {
-            Timed tm(c, "blas_inner");
+            Timed tm(c, st_, "blas_inner");
             CK(blas_bicg_update(bc, pr, in.x, in.r, in.p, in.s, in.t, in.rh, Vh, n, inner, max_iter,
-                                c->stream));
+                                st_));
         }
         c->launches += 6;
         return DP_OK;
@@ -570,10 +606,10 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
         } else {
             if (!graph) {
                 cudaGraph_t gr;
-                CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
                 const long before = c->launches.load();
                 dp_status s = body(0);
-                cudaError_t ce = cudaStreamEndCapture(c->stream, &gr);
+                cudaError_t ce = cudaStreamEndCapture(st_, &gr);
                 c->launches = before;
                 if (s != DP_OK) return s;
                 CK(ce);
@@ -581,15 +617,15 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
                 cudaGraphDestroy(gr);
                 graph_max_iter = max_iter;
             }
-            CK(cudaGraphLaunch(graph, c->stream));
+            CK(cudaGraphLaunch(graph, st_));
             c->launches += fused ? 9 : 10;
         }
         it++;
         if (it >= max_iter) break;
         if (it % check_every == 0) {
-            CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
-            if (*c->h_nactive == 0) break;
+            CK(cudaMemcpyAsync(hnact_, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, st_));
+            CK(cudaStreamSynchronize(st_));
+            if (*hnact_ == 0) break;
         }
     }
     *iters_done = it;
@@ -599,8 +635,8 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
 dp_status Batch::sap(const void *r, void *z)
 {
     const long long Vh = f->g.Vh;
-    CK(cudaMemsetAsync(z, 0, vin, c->stream));
-    CK(cudaMemcpyAsync(in.s, r, vin, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(z, 0, vin, st_));
+    CK(cudaMemcpyAsync(in.s, r, vin, cudaMemcpyDeviceToDevice, st_));
     SapParams P{};
     P.res = in.s;
     P.z = z;
@@ -625,14 +661,14 @@ dp_status Batch::sap(const void *r, void *z)
             P.colour = colour;
             cudaEvent_t ev;
             c->time_begin("sap_block", &ev);
-            CK(launch_sap_block(P, opin.lf, c->stream));
+            CK(launch_sap_block(P, opin.lf, st_));
             c->time_end("sap_block", ev);
             c->launches++;
             if (cyc == opts.sap_ncy - 1 && colour == 1) break;
             // global residual of the correction so far: res = r - Mhat z
             dp_status s = apply_mhat(c, opin, sp, z, in.v, in.to, inner);
             if (s != DP_OK) return s;
-            CK(blas32_xmy(r, in.v, in.s, Vh, n, c->stream));
+            CK(blas32_xmy(r, in.v, in.s, Vh, n, st_));
             c->launches++;
         }
     return DP_OK;
@@ -643,14 +679,14 @@ dp_status Batch::sap(const void *r, void *z)
 // combinations applied to z_k), then x += <w_k, r> z_k, r -= <w_k, r> w_k
 dp_status Batch::sap_gcr(int max_iter, int *iters_done)
 {
-    BlasCtx &bc = c->bc;
+    BlasCtx &bc = bc_;
     const long long Vh = f->g.Vh;
-    CK(blas_bicg_init(bc, 1, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, c->stream));
+    CK(blas_bicg_init(bc, 1, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, st_));
     c->launches += 2;
-    CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(hnact_, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
     *iters_done = 0;
-    if (*c->h_nactive == 0) return DP_OK;
+    if (*hnact_ == 0) return DP_OK;
     int it = 0;
     while (it < max_iter) {
         for (int k = 0; k < opts.gcr_nkv && it < max_iter; k++) {
@@ -659,18 +695,18 @@ dp_status Batch::sap_gcr(int max_iter, int *iters_done)
             s = apply_mhat(c, opin, sp, zk[k], wk[k], in.to, inner);
             if (s != DP_OK) return s;
             for (int i = 0; i < k; i++) {
-                CK(blas32_dotv(bc, wk[i], wk[k], Vh, n, inner, coef_d, c->stream));
-                CK(blas32_mgs(bc, wk[k], zk[k], wk[i], zk[i], Vh, n, inner, coef_d, c->stream));
+                CK(blas32_dotv(bc, wk[i], wk[k], Vh, n, inner, coef_d, st_));
+                CK(blas32_mgs(bc, wk[k], zk[k], wk[i], zk[i], Vh, n, inner, coef_d, st_));
             }
-            CK(blas32_norm2v(bc, wk[k], Vh, n, inner, nrm2_d, c->stream));
-            CK(blas32_normalise(bc, wk[k], zk[k], Vh, n, inner, nrm2_d, c->stream));
-            CK(blas32_dotv(bc, wk[k], in.r, Vh, n, inner, coef_d, c->stream));
-            CK(blas32_gcr_update(bc, in.x, in.r, zk[k], wk[k], Vh, n, inner, coef_d, max_iter, c->stream));
+            CK(blas32_norm2v(bc, wk[k], Vh, n, inner, nrm2_d, st_));
+            CK(blas32_normalise(bc, wk[k], zk[k], Vh, n, inner, nrm2_d, st_));
+            CK(blas32_dotv(bc, wk[k], in.r, Vh, n, inner, coef_d, st_));
+            CK(blas32_gcr_update(bc, in.x, in.r, zk[k], wk[k], Vh, n, inner, coef_d, max_iter, st_));
             c->launches += 2 * k + 5;
             it++;
-            CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
-            if (*c->h_nactive == 0) {
+            CK(cudaMemcpyAsync(hnact_, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, st_));
+            CK(cudaStreamSynchronize(st_));
+            if (*hnact_ == 0) {
                 *iters_done = it;
                 return DP_OK;
             }
@@ -688,7 +724,7 @@ dp_status Batch::contract_hl(const Job &h, const Job &l, double *out_dev)
     }
     const Geom &g = f->g;
     CK(launch_contract_hl(sp == 0 ? x : y64, sp == 0 ? y64 : x, g, n, alpha_d, h.tab, l.tab, h.slot0,
-                          l.slot0, h.grp.src[0], cpart, out_dev, c->stream));
+                          l.slot0, h.grp.src[0], cpart, out_dev, st_));
     c->launches += 2;
     return DP_OK;
 }
@@ -701,7 +737,7 @@ dp_status Batch::outer_mhat()
     const Geom &g = f->g;
     const long long cnt = g.Vh * 12 * n;
     const int *mask = state_mask(outer);
-    CK(launch_to_df(x, xdf, cnt, mask, n, kStateStride, c->stream));
+    CK(launch_to_df(x, xdf, cnt, mask, n, kStateStride, st_));
     DslashParams P{};
     P.links[0] = opdf.links[0];
     P.links[1] = opdf.links[1];
@@ -717,15 +753,15 @@ dp_status Batch::outer_mhat()
     for (int k = 0; k < kMaxGroups; k++) P.clov[k] = opdf.inv[1 - sp][k];
     P.in = xdf;
     P.out = tdf;
-    CK(launch_dslash_df(P, EPI_AINV, 128, c->stream));
+    CK(launch_dslash_df(P, EPI_AINV, 128, st_));
     P.parity = sp;
     for (int k = 0; k < kMaxGroups; k++) P.clov[k] = opdf.inv[sp][k];
     P.in = tdf;
     P.x = xdf;
     P.out = y64;
-    CK(launch_dslash_df(P, EPI_XMY_AINV, 128, c->stream));
+    CK(launch_dslash_df(P, EPI_XMY_AINV, 128, st_));
     c->time_end("dslash_df", ev);
-    CK(launch_from_df(tdf, t64, cnt, mask, n, kStateStride, c->stream));
+    CK(launch_from_df(tdf, t64, cnt, mask, n, kStateStride, st_));
     c->launches += 4;
     return DP_OK;
 }
@@ -734,15 +770,15 @@ dp_status Batch::outer_mhat()
 // residual of Mhat x = b itself (recursively updated r = b - Mhat x)
 dp_status Batch::cgne(int max_iter, int *iters_done)
 {
-    BlasCtx &bc = c->bc;
+    BlasCtx &bc = bc_;
     const int pr = opin.pr;
     const long long Vh = f->g.Vh;
-    CK(blas_bicg_init(bc, pr, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, c->stream));
+    CK(blas_bicg_init(bc, pr, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, st_));
     c->launches += 2;
-    CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(hnact_, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
     int it = 0;
-    if (*c->h_nactive == 0) {
+    if (*hnact_ == 0) {
         *iters_done = 0;
         return DP_OK;
     }
@@ -750,12 +786,12 @@ dp_status Batch::cgne(int max_iter, int *iters_done)
     auto body = [&](int first) -> dp_status {
         dp_status s = apply_mhat_dag(c, opin, opin_adj, sp, in.r, in.s, in.t, in.to, inner);
         if (s != DP_OK) return s;
-        CK(blas_cg_gamma(bc, pr, in.s, Vh, n, inner, first, c->stream));
-        CK(blas_cg_p(bc, pr, in.s, in.p, Vh, n, inner, c->stream));
+        CK(blas_cg_gamma(bc, pr, in.s, Vh, n, inner, first, st_));
+        CK(blas_cg_p(bc, pr, in.s, in.p, Vh, n, inner, st_));
         s = apply_mhat(c, opin, sp, in.p, in.v, in.to, inner);
         if (s != DP_OK) return s;
-        CK(blas_cg_alpha(bc, pr, in.v, Vh, n, inner, c->stream));
-        CK(blas_cg_update(bc, pr, in.x, in.r, in.p, in.v, Vh, n, inner, max_iter, c->stream));
+        CK(blas_cg_alpha(bc, pr, in.v, Vh, n, inner, st_));
+        CK(blas_cg_update(bc, pr, in.x, in.r, in.p, in.v, Vh, n, inner, max_iter, st_));
         c->launches += 5;
         return DP_OK;
     };
@@ -767,10 +803,10 @@ dp_status Batch::cgne(int max_iter, int *iters_done)
         } else {
             if (!graph) {
                 cudaGraph_t gr;
-                CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
                 const long before = c->launches.load();
                 dp_status s = body(0);
-                cudaError_t ce = cudaStreamEndCapture(c->stream, &gr);
+                cudaError_t ce = cudaStreamEndCapture(st_, &gr);
                 c->launches = before;
                 if (s != DP_OK) return s;
                 CK(ce);
@@ -778,15 +814,15 @@ dp_status Batch::cgne(int max_iter, int *iters_done)
                 cudaGraphDestroy(gr);
                 graph_max_iter = max_iter;
             }
-            CK(cudaGraphLaunch(graph, c->stream));
+            CK(cudaGraphLaunch(graph, st_));
             c->launches += 10;
         }
         it++;
         if (it >= max_iter) break;
         if (it % check_every == 0) {
-            CK(cudaMemcpyAsync(c->h_nactive, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
-            if (*c->h_nactive == 0) break;
+            CK(cudaMemcpyAsync(hnact_, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, st_));
+            CK(cudaStreamSynchronize(st_));
+            if (*hnact_ == 0) break;
         }
     }
     *iters_done = it;
@@ -795,13 +831,13 @@ dp_status Batch::cgne(int max_iter, int *iters_done)
 
 dp_status Batch::round()
 {
-    Timed tm(c, "round");
+    Timed tm(c, st_, "round");
     const long long Vh = f->g.Vh;
     const int max_outer = 200;
     // per-RHS stop rules on the host: stagnation of the true residual, round
     // and iteration caps
-    CK(cudaMemcpyAsync(hs.data(), outer, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(hs.data(), outer, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
     int nact = 0;
     bool changed = false;
     for (int k = 0; k < n; k++) {
@@ -818,32 +854,32 @@ dp_status Batch::round()
             nact++;
         }
     }
-    if (changed) CK(cudaMemcpyAsync(outer, hs.data(), sizeof(RhsState) * n, cudaMemcpyHostToDevice, c->stream));
+    if (changed) CK(cudaMemcpyAsync(outer, hs.data(), sizeof(RhsState) * n, cudaMemcpyHostToDevice, st_));
     if (nact == 0) return DP_OK;
     for (int k = 0; k < n; k++)
         if (slot_job[k] && hs[k].active) slot_outer[k]++;
     const bool refine = any_refining();
     const Geom &g = f->g;
     {
-        Timed tm(c, "outer_blas");
+        Timed tm(c, st_, "outer_blas");
         // refined RHS: |R r| in the inner solver's metric first (it may flag
         // a non-finite RHS before the inner state is set up)
         if (refine) {
-            CK(blas_ratio_norm(c->bc, r64, g, sp, n, alpha_d, alpha_in_d, slots_d, outer, c->stream));
+            CK(blas_ratio_norm(bc_, r64, g, sp, n, alpha_d, alpha_in_d, slots_d, outer, st_));
             c->launches++;
         }
-        CK(blas_inner_setup(outer, inner, n, opts.inner_tol, 0.0, c->stream));
+        CK(blas_inner_setup(outer, inner, n, opts.inner_tol, 0.0, st_));
         if (mixed)
-            CK(blas_to_f32_scaled(r64, (float4 *)in.rh, Vh, n, outer, c->stream));
+            CK(blas_to_f32_scaled(r64, (float4 *)in.rh, Vh, n, outer, st_));
         else
-            CK(blas_scale64(r64, (double2 *)in.rh, Vh, n, outer, c->stream));
+            CK(blas_scale64(r64, (double2 *)in.rh, Vh, n, outer, st_));
         if (refine) {
             if (mixed)
                 CK(blas_to_f32_ratio(r64, (float4 *)in.rh, g, sp, n, alpha_d, alpha_in_d, slots_d, outer,
-                                     c->stream));
+                                     st_));
             else
                 CK(blas_scale64_ratio(r64, (double2 *)in.rh, g, sp, n, alpha_d, alpha_in_d, slots_d,
-                                      outer, c->stream));
+                                      outer, st_));
             c->launches++;
         }
     }
@@ -855,8 +891,8 @@ dp_status Batch::round()
                   : opts.solver == DP_SOLVER_SAP_GCR ? sap_gcr(budget, &done)
                                                      : bicgstab(budget, &done);
     if (s != DP_OK) return s;
-    CK(cudaMemcpyAsync(hin.data(), inner, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(hin.data(), inner, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
     bool bad = false;
     for (int k = 0; k < n; k++) {
         if (!slot_job[k] || !hs[k].active) continue;
@@ -867,20 +903,20 @@ dp_status Batch::round()
             bad = true;
         }
     }
-    if (bad) CK(cudaMemcpyAsync(outer, hs.data(), sizeof(RhsState) * n, cudaMemcpyHostToDevice, c->stream));
+    if (bad) CK(cudaMemcpyAsync(outer, hs.data(), sizeof(RhsState) * n, cudaMemcpyHostToDevice, st_));
     {
-        Timed tm(c, "outer_blas");
+        Timed tm(c, st_, "outer_blas");
         if (mixed)
-            CK(blas_acc_f32(x, (const float4 *)in.x, Vh, n, outer, c->stream));
+            CK(blas_acc_f32(x, (const float4 *)in.x, Vh, n, outer, st_));
         else
-            CK(blas_acc64(x, (const double2 *)in.x, Vh, n, outer, c->stream));
+            CK(blas_acc64(x, (const double2 *)in.x, Vh, n, outer, st_));
         if (refine) {
             if (mixed)
                 CK(blas_acc_f32_ratio(x, (const float4 *)in.x, g, sp, n, alpha_d, alpha_in_d, slots_d,
-                                      outer, c->stream));
+                                      outer, st_));
             else
                 CK(blas_acc64_ratio(x, (const double2 *)in.x, g, sp, n, alpha_d, alpha_in_d, slots_d,
-                                    outer, c->stream));
+                                    outer, st_));
             c->launches++;
         }
     }
@@ -889,8 +925,8 @@ dp_status Batch::round()
     s = outer_mhat();
     if (s != DP_OK) return s;
     {
-        Timed tm(c, "outer_blas");
-        CK(blas_residual64(c->bc, bh, y64, r64, Vh, n, outer, nullptr, c->stream));
+        Timed tm(c, st_, "outer_blas");
+        CK(blas_residual64(bc_, bh, y64, r64, Vh, n, outer, nullptr, st_));
     }
     c->launches += 3;
     return DP_OK;
@@ -929,21 +965,21 @@ dp_status Batch::set_inner_profile(const Job &j, const double *xx)
     if (s != DP_OK) return s;
     for (size_t k = 0; k < hop.size(); k++) hopa[k] = hop[k] != 0.0 ? 0.25 / hop[k] : 0.0;
     CK(cudaMemcpyAsync(alpha_in_d + (size_t)m * 4 * Lm, alpha.data(), sizeof(double) * 4 * Lm,
-                       cudaMemcpyHostToDevice, c->stream));
+                       cudaMemcpyHostToDevice, st_));
     if (ipr == 0) {
         CK(cudaMemcpyAsync(hopin64_d + (size_t)m * 8 * Lm, hop.data(), sizeof(double) * 8 * Lm,
-                           cudaMemcpyHostToDevice, c->stream));
+                           cudaMemcpyHostToDevice, st_));
         CK(cudaMemcpyAsync(hopadj64_d + (size_t)m * 8 * Lm, hopa.data(), sizeof(double) * 8 * Lm,
-                           cudaMemcpyHostToDevice, c->stream));
+                           cudaMemcpyHostToDevice, st_));
     } else {
         std::vector<float> hf(hop.begin(), hop.end()), haf(hopa.begin(), hopa.end());
         CK(cudaMemcpyAsync(hop32_d + (size_t)m * 8 * Lm, hf.data(), sizeof(float) * 8 * Lm,
-                           cudaMemcpyHostToDevice, c->stream));
+                           cudaMemcpyHostToDevice, st_));
         CK(cudaMemcpyAsync(hopadj32_d + (size_t)m * 8 * Lm, haf.data(), sizeof(float) * 8 * Lm,
-                           cudaMemcpyHostToDevice, c->stream));
-        CK(cudaStreamSynchronize(c->stream));  // the float vectors go away
+                           cudaMemcpyHostToDevice, st_));
+        CK(cudaStreamSynchronize(st_));  // the float vectors go away
     }
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaStreamSynchronize(st_));
     return DP_OK;
 }
 
@@ -980,14 +1016,14 @@ dp_status Batch::slice_check(bool *changed)
     dp_status s = upload_mask(m);
     if (s != DP_OK) return s;
     {
-        Timed tm(c, "slice_norms");
+        Timed tm(c, st_, "slice_norms");
         CK(launch_slice_norms(x, r64, g, sp, n, alpha_d, slots_d, ng, mask_d, cpart, slice_d,
-                              c->stream));
+                              st_));
     }
     c->launches += 2;
     CK(cudaMemcpyAsync(slice_h.data(), slice_d, sizeof(double) * ng * T * 2, cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+                       st_));
+    CK(cudaStreamSynchronize(st_));
     std::vector<double> xx(T);
     for (Job *j : cand) {
         const double *h = slice_h.data() + (size_t)j->tab * T * 2;
@@ -1056,18 +1092,18 @@ dp_status Batch::slice_check(bool *changed)
 
 dp_status Batch::harvest(std::vector<Job *> &finished)
 {
-    Timed tm(c, "harvest");
+    Timed tm(c, st_, "harvest");
     const Geom &g = f->g;
     const long long Vh = g.Vh;
-    CK(cudaMemcpyAsync(hs.data(), outer, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(hs.data(), outer, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
     {
         bool changed = false;
         dp_status s = slice_check(&changed);
         if (s != DP_OK) return s;
         if (changed) {
-            CK(cudaMemcpyAsync(outer, hs.data(), sizeof(RhsState) * n, cudaMemcpyHostToDevice, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
+            CK(cudaMemcpyAsync(outer, hs.data(), sizeof(RhsState) * n, cudaMemcpyHostToDevice, st_));
+            CK(cudaStreamSynchronize(st_));
         }
     }
     for (int tab = 0; tab < kMaxGroups; tab++) {
@@ -1086,10 +1122,10 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
         // from the last FP64 Schur application (x_p final): no extra dslash
         // only this job's slots: the other parity of jobs finished earlier
         // stays in y64 (heavy-light contractions read it)
-        CK(blas_zero_masked(y64, Vh, n, mask_d, c->stream));
-        CK(blas_zero_masked(to64, Vh, n, mask_d, c->stream));
+        CK(blas_zero_masked(y64, Vh, n, mask_d, st_));
+        CK(blas_zero_masked(to64, Vh, n, mask_d, st_));
         CK(launch_point_source(g, slots_d, n, mask_d, sp == 0 ? y64 : to64, sp == 0 ? to64 : y64,
-                               c->stream));
+                               st_));
         CloverApplyParams cp{};
         memcpy(cp.grp_of, op64.grp_of, sizeof cp.grp_of);
         cp.mask = mask_d;
@@ -1098,8 +1134,8 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
         for (int k = 0; k < kMaxGroups; k++) cp.mat[k] = op64.inv[1 - sp][k];
         cp.in = to64;
         cp.out = to64;
-        CK(launch_clover_point(cp, g, slots_d, 1 - sp, c->stream));
-        CK(blas_sub64_masked(to64, t64, y64, Vh, n, mask_d, c->stream));
+        CK(launch_clover_point(cp, g, slots_d, 1 - sp, st_));
+        CK(blas_sub64_masked(to64, t64, y64, Vh, n, mask_d, st_));
         // residual report: the full residual of (D'+M)S' = eta' is (A_pp rhat, 0)
         // with x_q rebuilt from x_p, so |A_pp rhat| / |eta'| (a few digits:
         // FP32 products, FP64 sums)
@@ -1109,11 +1145,12 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
         }
         cp.in = r64;
         cp.out = nullptr;
-        CK(launch_clover_norm(c->bc, cp, nrm_d, c->stream));
+        CK(launch_clover_norm(bc_, cp, nrm_d, st_));
         double2 *prop_d = nullptr;
         void *prop_tmp = nullptr;
         if (j->prop_host) {
             prop_tmp = c->alloc((size_t)g.V * 24 * sizeof(double) * n);
+            if (prop_tmp && own_stream_) CK(cudaStreamSynchronize(c->stream));
             if (!prop_tmp) {
                 set_error("out of device memory for the propagator");
                 return DP_ERR_OOM;
@@ -1121,17 +1158,17 @@ dp_status Batch::harvest(std::vector<Job *> &finished)
             prop_d = (double2 *)prop_tmp;
         }
         CK(launch_restore_contract(sp == 0 ? x : y64, sp == 0 ? y64 : x, g, n, alpha_d, slots_d,
-                                   kMaxGroups, tsrc_d, mask_d, cpp_d, cpart, prop_d, c->stream,
+                                   kMaxGroups, tsrc_d, mask_d, cpp_d, cpart, prop_d, st_,
                                    j->cap_dst ? cap_d : nullptr));
-        if (j->cpp_dst) CK(launch_cpp_commit(cpp_d + (size_t)tab * g.T, j->cpp_dst, g.T, j->accumulate, c->stream));
-        if (j->cap_dst) CK(launch_cpp_commit(cap_d + (size_t)tab * g.T, j->cap_dst, g.T, j->accumulate, c->stream));
-        if (j->cpp_host) CK(cudaMemcpyAsync(j->cpp_host, cpp_d + (size_t)tab * g.T, sizeof(double) * g.T, cudaMemcpyDeviceToHost, c->stream));
+        if (j->cpp_dst) CK(launch_cpp_commit(cpp_d + (size_t)tab * g.T, j->cpp_dst, g.T, j->accumulate, st_));
+        if (j->cap_dst) CK(launch_cpp_commit(cap_d + (size_t)tab * g.T, j->cap_dst, g.T, j->accumulate, st_));
+        if (j->cpp_host) CK(cudaMemcpyAsync(j->cpp_host, cpp_d + (size_t)tab * g.T, sizeof(double) * g.T, cudaMemcpyDeviceToHost, st_));
         if (prop_d)
             CK(cudaMemcpyAsync(j->prop_host, prop_d + (size_t)j->slot0 * g.V * 12,
-                               sizeof(double) * 24 * g.V * j->ncomp, cudaMemcpyDeviceToHost, c->stream));
+                               sizeof(double) * 24 * g.V * j->ncomp, cudaMemcpyDeviceToHost, st_));
         std::vector<double> nr(n);
-        CK(cudaMemcpyAsync(nr.data(), nrm_d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaMemcpyAsync(nr.data(), nrm_d, sizeof(double) * n, cudaMemcpyDeviceToHost, st_));
+        CK(cudaStreamSynchronize(st_));
         if (prop_tmp) c->release(prop_tmp);
         c->launches += 6;
         SolveResult &R = j->res;
@@ -1462,6 +1499,7 @@ dp_status dp_schur_dev(dp_ctx *ctx, dp_field field, double M, const dp_profile *
     const int lf = inner_link_format(prec, compress12);
     Op op{};
     op.f = &f;
+    op.st = c.stream;
     op.pr = pr;
     op.lf = lf;
     op.nrhs = nrhs;

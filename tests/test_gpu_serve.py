@@ -110,3 +110,91 @@ def test_rejected_when_budget_too_small():
     with pytest.raises(dp.DpError):
         dp.dp_submit(c, f, 0.5, ("cosh_t", 0.4), (0, 0, 0, 0), 1e-8)
     dp.dp_destroy(c)
+
+
+def test_mixed_volumes_overlap_and_match_oracle():
+    """Two resident fields of different volumes, requests for both in flight
+    at once: each field's batch runs on its own stream and worker, so their
+    rounds overlap (the scheduler reports two batches inside a round at the
+    same time).  Served results against the oracle: the 32x16^3 multi-mass
+    workload's field at the origin source (stored oracle results, one request
+    per mass with its own profile), and random 16x8^3 requests against live
+    oracle solves; 1e-6 per slice out to T/2."""
+    import json
+    import os
+
+    require_gpu()
+    c = dp.dp_create(0)
+    try:
+        g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                        "cpp_32x16_multimass.json")))
+        dims_l = tuple(g["dims"])
+        fl = dp.dp_field_load(c, field(dims_l, g["eps"], g["seed"]), dims_l, g["bc_t"])
+        dp.dp_field_set_csw(c, fl, g["csw"])
+        dims_s = (16, 8, 8, 8)
+        Us = field(dims_s, 0.3, 101)
+        fs = dp.dp_field_load(c, Us, dims_s, -1)
+        dp.dp_field_set_csw(c, fs, 1.7)
+        op_s = oracle.WilsonClover(Us, dims_s, 1.7, -1)
+        dp.dp_serve_start(c, 0, 24)
+        rng = np.random.default_rng(7)
+        big, small = [], []
+        for k, m in enumerate(g["masses"]):
+            prof = ("cosh_t", 0.4 if m["M"] < 0.65 else 0.5) if m["M"] >= 0.3 else ("cosh_4d", 0.2)
+            big.append((dp.dp_submit(c, fl, m["M"], prof, (0, 0, 0, 0), 1e-10), m))
+            M = float(rng.uniform(0.05, 0.8))
+            prof_s = ("cosh_t", 0.4) if M >= 0.3 else ("cosh_4d", 0.2)
+            src = tuple(int(rng.integers(0, d)) for d in dims_s)
+            small.append((dp.dp_submit(c, fs, M, prof_s, src, 1e-10), M, prof_s, src))
+        for t, m in big:
+            cpp, info = dp.dp_wait(c, t, dims_l[0], timeout_s=300, allow=())
+            assert slice_rel(cpp, np.asarray(m["cpp"]), dims_l[0] // 2) < 1e-6, m["M"]
+        for t, M, prof_s, src in small:
+            cpp, info = dp.dp_wait(c, t, dims_s[0], timeout_s=300, allow=())
+            ref, _, _ = oracle.solve_point(op_s, M, prof_s[0], prof_s[1], src, tol=1e-13)
+            assert slice_rel(cpp, ref, dims_s[0] // 2) < 1e-6, (M, prof_s, src)
+        st = dp.dp_serve_stats_get(c)
+        assert st["completed"] == 8
+        assert st["max_concurrent_batches"] == 2
+        dp.dp_serve_stop(c, 1)
+    finally:
+        dp.dp_destroy(c)
+
+
+def test_interleaved_submits_while_batches_run():
+    """Requests for two fields submitted one by one with short random gaps
+    while both fields' workers admit and run rounds (the queue changes under
+    them): every request completes, and each result equals the same request
+    solved directly through dp_solve_point within 1e-6 per slice."""
+    require_gpu()
+    c = dp.dp_create(0)
+    try:
+        specs = [((8, 4, 4, 4), 0.3, 201), ((12, 4, 4, 6), 0.4, 202)]
+        fields = []
+        for dims, eps, seed in specs:
+            f = dp.dp_field_load(c, field(dims, eps, seed), dims, -1)
+            dp.dp_field_set_csw(c, f, 1.7)
+            fields.append((f, dims))
+        dp.dp_serve_start(c, 0, 24)
+        rng = np.random.default_rng(11)
+        reqs = []
+        for k in range(40):
+            f, dims = fields[k % 2]
+            M = float(rng.uniform(0.05, 0.8))
+            prof = ("cosh_t", 0.4) if M >= 0.3 else ("cosh_4d", 0.2)
+            src = tuple(int(rng.integers(0, d)) for d in dims)
+            reqs.append((dp.dp_submit(c, f, M, prof, src, 1e-10), f, dims, M, prof, src))
+            time.sleep(float(rng.uniform(0.0, 0.004)))
+        served = []
+        for t, f, dims, M, prof, src in reqs:
+            cpp, info = dp.dp_wait(c, t, dims[0], timeout_s=300, allow=())
+            served.append(cpp)
+        st = dp.dp_serve_stats_get(c)
+        dp.dp_serve_stop(c, 1)
+        assert st["completed"] == 40
+        for cpp, (t, f, dims, M, prof, src) in zip(served, reqs):
+            ref, _, _ = dp.dp_solve_point(c, f, M, prof, src, 1e-10,
+                                          {"prec": "mixed_fp32", "batched": 1}, T=dims[0])
+            assert slice_rel(cpp, ref, dims[0] // 2) < 1e-6
+    finally:
+        dp.dp_destroy(c)

@@ -67,7 +67,7 @@ def test_refinement_meets_per_slice_accuracy(setup, opts):
     assert info["status"] == 0, info
     if opts is MIXED:  # the case shown to fail without the check
         assert info["refine_rounds"] >= 1
-    assert 0 < info["slice_residue"] <= 10 * r
+    assert 0 < info["slice_residue"] <= max(10 * r, 1e-8)  # the default target
     assert slice_rel(cpp, ref, DIMS[0] // 2) < 1e-6
 
 
@@ -86,7 +86,7 @@ def test_matched_profile_needs_no_refinement(setup):
                                      T=DIMS[0])
     assert info["status"] == 0
     assert info["refine_rounds"] <= 1
-    assert 0 < info["slice_residue"] <= 1e-9
+    assert 0 < info["slice_residue"] <= 1e-8
     assert slice_rel(cpp, ref, DIMS[0] // 2) < 1e-6
 
 
