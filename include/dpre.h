@@ -469,12 +469,18 @@ typedef struct {
     double solves_per_s;            /* completions / (last - first completion) */
     size_t hbm_budget, hbm_in_use;
     int max_concurrent_batches;     /* most field batches inside a round at once */
+    long yields;                    /* inner solves ended at a convergence check to
+                                       admit a waiting request                     */
 } dp_serve_stats;
 
 /* Start the scheduler.  One solver batch per field with work, each on a
  * CUDA stream of its own and driven by a host thread of its own, so rounds of
  * different fields run concurrently on the device; requests join their
- * field's batch between defect-correction rounds as slots free up.
+ * field's batch between defect-correction rounds as slots free up.  When a
+ * request arrives for a field whose batch has free slots while a round runs,
+ * the inner solve ends at its next convergence check (after at least 8
+ * iterations; the partial correction is a valid defect-correction step) and
+ * the request is admitted at once instead of after the whole round.
  * hbm_budget: bytes of solver state the scheduler may hold for admitted
  * requests (0: 80% of free memory); max_slots: RHS slots per field batch
  * (multiple of 12, 0: 48).  Per-kernel timing (dp_timing_*) covers work on

@@ -93,7 +93,7 @@ class ServeStats(C.Structure):
                 ("in_flight", C.c_long), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
                 ("mean_ms", C.c_double), ("solves_per_s", C.c_double),
                 ("hbm_budget", C.c_size_t), ("hbm_in_use", C.c_size_t),
-                ("max_concurrent_batches", C.c_int)]
+                ("max_concurrent_batches", C.c_int), ("yields", C.c_long)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1,6 +1,7 @@
 // Slot-based solver batch: see solver.cu.
 #pragma once
 
+#include <functional>
 #include <memory>
 #include <vector>
 
@@ -83,6 +84,16 @@ class Batch {
     int active_jobs() const;
     // at most this many jobs at once (0: as many as the slots hold)
     void set_max_jobs(int m) { max_jobs = m; }
+    // called at the inner solver's convergence checks (after at least
+    // min_iter iterations of the round's inner solve): returning true ends
+    // the inner solve there, so the round closes early (the partial
+    // correction is a valid defect-correction step) and a waiting request can
+    // be admitted at once
+    void set_yield(std::function<bool()> fn, int min_iter = 8)
+    {
+        yield_check = std::move(fn);
+        yield_min = min_iter;
+    }
     size_t bytes() const { return total_bytes; }
     const std::shared_ptr<Field> &field() const { return f; }
 
@@ -115,6 +126,8 @@ class Batch {
     int round_iters;
     int sp = 0;
     int max_jobs = 0;
+    std::function<bool()> yield_check;
+    int yield_min = 8;
     int mixed = 1, ipr = 1, ilf = LINK_F32_12;
     int check_every = 4;
     size_t v64 = 0, vin = 0, total_bytes = 0;

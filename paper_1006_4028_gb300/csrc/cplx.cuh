@@ -132,17 +132,23 @@ __device__ __forceinline__ void load_link<LINK_F64_18, double>(const void *base,
     }
 }
 
+// 18-real FP32 storage: entries 0-7 as four float4 [mu][k][s] (two complex
+// entries each), entry 8 as a float2 [mu][s] after them (72 bytes a link)
 template <>
 __device__ __forceinline__ void load_link<LINK_F32_18, float>(const void *base, long long Vh,
                                                              long long site, int mu,
                                                              Cx<float> u[9])
 {
-    const float2 *l = static_cast<const float2 *>(base) + (long long)mu * 9 * Vh + site;
+    const float4 *l = static_cast<const float4 *>(base) + (long long)mu * 4 * Vh + site;
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
-        float2 v = __ldg(l + k * Vh);
-        u[k] = {v.x, v.y};
+    for (int k = 0; k < 4; k++) {
+        const float4 v = __ldg(l + k * Vh);
+        u[2 * k] = {v.x, v.y};
+        u[2 * k + 1] = {v.z, v.w};
     }
+    const float2 w = __ldg(reinterpret_cast<const float2 *>(static_cast<const float4 *>(base) + 16 * Vh) +
+                           (long long)mu * Vh + site);
+    u[8] = {w.x, w.y};
 }
 
 // 12-real storage: rows 0 and 1; row 2 = conj(row0 x row1) (unitary, det 1)

@@ -8,7 +8,8 @@
 //     (6 per spinor, FP32) or double2 (12 per spinor, FP64); the 24 reals of a
 //     spinor are (spin, colour, re/im) in that order, spin-major.
 //   links of one parity: [mu][chunk][s]; FP64: 9 double2 (18 reals);
-//     FP32: 9 float2 (18 reals) or 3 float4 (12 reals: rows 0 and 1).
+//     FP32: 18 reals as 4 float4 per link ([mu][4][s], entries 0-7) followed by
+//     a float2 [mu][s] (entry 8), or 12 reals as 3 float4 (rows 0 and 1).
 //   clover (and its inverse) of one parity: [slot][chunk][s]; 72 reals per
 //     site = two Hermitian 6x6 chiral blocks (spins 0,1 and spins 2,3), each
 //     packed as 6 real diagonal entries then the 15 upper-triangle entries

@@ -660,10 +660,11 @@ __device__ __forceinline__ void prefetch_link(const void *lk, long long Vh, long
     if constexpr (LF == LINK_F32_12) {
         prefetch3(static_cast<const float4 *>(lk) + (long long)mu * 3 * Vh + lsite, Vh * 16);
     } else if constexpr (LF == LINK_F32_18) {
-        const float2 *l = static_cast<const float2 *>(lk) + (long long)mu * 9 * Vh + lsite;
-        prefetch3(l, Vh * 8);
-        prefetch3(l + 3 * Vh, Vh * 8);
-        prefetch3(l + 6 * Vh, Vh * 8);
+        const float4 *l = static_cast<const float4 *>(lk) + (long long)mu * 4 * Vh + lsite;
+        prefetch3(l, Vh * 16);
+        prefetch_l1(l + 3 * Vh);
+        prefetch_l1(reinterpret_cast<const float2 *>(static_cast<const float4 *>(lk) + 16 * Vh) +
+                    (long long)mu * Vh + lsite);
     } else {
         prefetch3(static_cast<const uint2 *>(lk) + (long long)mu * 3 * Vh + lsite, Vh * 8);
         prefetch_l1(reinterpret_cast<const float *>(static_cast<const uint2 *>(lk) + 12 * Vh) +

@@ -39,16 +39,21 @@ __global__ void k_pack_links(const double2 *lex, Geom g, double2 *l64e, double2 
     const long long s = i >> 1;
     const double2 *u = lex + (i * 4 + mu) * 9;
     double2 *o64 = (par ? l64o : l64e) + (long long)mu * 9 * g.Vh + s;
-    float2 *o32 = (par ? l32fo : l32fe) + (long long)mu * 9 * g.Vh + s;
+    // FP32 18-real: entries 0-7 as float4 [mu][4][s], entry 8 as float2 [mu][s]
+    float4 *o32 = reinterpret_cast<float4 *>(par ? l32fo : l32fe) + (long long)mu * 4 * g.Vh + s;
+    float2 *o32t = reinterpret_cast<float2 *>(reinterpret_cast<float4 *>(par ? l32fo : l32fe) + 16 * g.Vh) +
+                   (long long)mu * g.Vh + s;
     float4 *oc = (par ? l32co : l32ce) + (long long)mu * 3 * g.Vh + s;
     double2 v[9];
 #pragma unroll
     for (int k = 0; k < 9; k++) v[k] = u[k];
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
-        o64[k * g.Vh] = v[k];
-        o32[k * g.Vh] = make_float2((float)v[k].x, (float)v[k].y);
-    }
+    for (int k = 0; k < 9; k++) o64[k * g.Vh] = v[k];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        o32[k * g.Vh] = make_float4((float)v[2 * k].x, (float)v[2 * k].y, (float)v[2 * k + 1].x,
+                                    (float)v[2 * k + 1].y);
+    o32t[0] = make_float2((float)v[8].x, (float)v[8].y);
 #pragma unroll
     for (int k = 0; k < 3; k++)
         oc[k * g.Vh] = make_float4((float)v[2 * k].x, (float)v[2 * k].y, (float)v[2 * k + 1].x,

@@ -67,6 +67,11 @@ struct Scheduler {
     std::vector<double> lat_ms;
     Clock::time_point first_done, last_done;
     int in_round = 0, max_in_round = 0;  // batches inside a round at once
+    long yields = 0;                     // inner solves cut short to admit a request
+
+    // a running batch's convergence-check hook: true (the inner solve yields)
+    // when a request of its field waits and the batch has free slots
+    void install_yield(Worker *w);
     dp_solve_opts opts{};
 
     void run();            // coordinator
@@ -76,6 +81,20 @@ struct Scheduler {
 };
 
 void SchedDeleter::operator()(Scheduler *s) const { delete s; }
+
+void Scheduler::install_yield(Worker *w)
+{
+    w->B->set_yield([this, w] {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!w->B->can_admit(12)) return false;
+        for (auto &rq : queue)
+            if (!rq->cancelled && rq->req.field == w->fid) {
+                yields++;
+                return true;
+            }
+        return false;
+    });
+}
 
 void Scheduler::finish(Request *rq, dp_status s, const char *why)
 {
@@ -155,6 +174,7 @@ void Scheduler::work(Worker *w)
             lk.unlock();
             w->B.reset(new Batch(c, w->field, max_slots, opts, 200, 0, true));
             dp_status e = w->B->init();
+            install_yield(w);
             lk.lock();
             done_cv.notify_all();
             if (e != DP_OK) break;
@@ -207,6 +227,7 @@ void Scheduler::run()
                 done_cv.notify_all();
                 break;  // the queue changed under the loop
             }
+            install_yield(wp);
             wp->th = std::thread([this, wp] { work(wp); });
             break;  // the queue iterator may be stale after unlocking
         }
@@ -493,6 +514,7 @@ dp_status dp_serve_stats_get(dp_ctx *ctx, dp_serve_stats *out)
     out->hbm_budget = S.budget;
     out->hbm_in_use = S.in_use;
     out->max_concurrent_batches = S.max_in_round;
+    out->yields = S.yields;
     return DP_OK;
 }
 

@@ -626,6 +626,7 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
             CK(cudaMemcpyAsync(hnact_, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, st_));
             CK(cudaStreamSynchronize(st_));
             if (*hnact_ == 0) break;
+            if (yield_check && it >= yield_min && yield_check()) break;
         }
     }
     *iters_done = it;
@@ -706,7 +707,7 @@ dp_status Batch::sap_gcr(int max_iter, int *iters_done)
             it++;
             CK(cudaMemcpyAsync(hnact_, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, st_));
             CK(cudaStreamSynchronize(st_));
-            if (*hnact_ == 0) {
+            if (*hnact_ == 0 || (yield_check && it >= yield_min && yield_check())) {
                 *iters_done = it;
                 return DP_OK;
             }
@@ -823,6 +824,7 @@ dp_status Batch::cgne(int max_iter, int *iters_done)
             CK(cudaMemcpyAsync(hnact_, bc.n_active, sizeof(int), cudaMemcpyDeviceToHost, st_));
             CK(cudaStreamSynchronize(st_));
             if (*hnact_ == 0) break;
+            if (yield_check && it >= yield_min && yield_check()) break;
         }
     }
     *iters_done = it;

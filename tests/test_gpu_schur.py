@@ -170,3 +170,46 @@ def test_schur_bad_arguments(ctx, setup):
     with pytest.raises(dp.DpError):  # odd nrhs in FP32
         dp.dp_schur_dev(ctx, f, M, None, None, "mixed_fp32", 1, 0, 0, x.data_ptr(),
                         x.data_ptr() + 64, 3)
+
+
+# the launch shapes of the FP32 kernels the tuner chooses from (RHS per
+# thread, staging, threads per block), 12-real and 18-real links
+FUSED_SHAPES = [(1, 2, 6, 128), (1, 2, 6, 64), (1, 2, 0, 64), (1, 2, 2, 64), (1, 2, 5, 128),
+                (0, 2, 6, 128), (0, 2, 0, 64)]
+
+
+@pytest.mark.parametrize("c12,rpt,stages,block", FUSED_SHAPES)
+def test_fused_ainv_dslash_per_site(ctx, setup, c12, rpt, stages, block):
+    """The benchmark's launch A_ee^-1 D_eo psi_o (FP32, fused clover-inverse
+    epilogue) directly against the oracle: its hopping term on the odd-parity
+    input, then the inverse of the site matrix A = 4 + M + clover, per site
+    and right-hand side at 1e-6 (the oracle takes the FP32-rounded input)."""
+    f, op, A = setup
+    prof = ("cosh_4d", 0.3)
+    psi = li.random_spinor(DIMS, 12, 81).astype(np.complex64).astype(np.complex128)
+    ev, od = dp.pack_half_spinors(psi, DIMS)
+    xin = to_dev(od, "mixed_fp32")
+    out = torch.zeros_like(xin)
+    dp.dp_dslash_dev(ctx, f, M, prof, "mixed_fp32", c12, 0, xin.data_ptr(), out.data_ptr(), 12,
+                     block, rpt, 1, stages=stages)
+    torch.cuda.synchronize()
+    got = full_of(from_dev(out, "mixed_fp32", ev.shape[1], 12), 0)
+    par = parity_mask()
+    t = op.hop(full_of(od, 1), (prof[0], prof[1], (0, 0, 0, 0)))
+    t[:, par != 0] = 0
+    ref = ainv(A, t)
+    assert per_site_rel(got[:, par == 0], ref[:, par == 0]) < 1e-6
+
+
+@pytest.mark.parametrize("prof,src", PROFILES)
+@pytest.mark.parametrize("p", [0, 1])
+def test_mhat_fp32_per_site(ctx, setup, prof, src, p):
+    """Mhat in FP32 (its second launch is the fused x - A^-1 D epilogue) per
+    site against the oracle's Schur complement at 1e-6."""
+    f, op, A = setup
+    psi = li.random_spinor(DIMS, 12, 90 + p).astype(np.complex64).astype(np.complex128)
+    h = half_of(psi, p)
+    got = full_of(schur(ctx, f, prof, src, "mixed_fp32", p, 0, h), p)
+    ref = oracle_mhat(op, A, full_of(h, p), p, prof, src)
+    par = parity_mask()
+    assert per_site_rel(got[:, par == p], ref[:, par == p]) < 1e-6

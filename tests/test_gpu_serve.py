@@ -198,3 +198,35 @@ def test_interleaved_submits_while_batches_run():
             assert slice_rel(cpp, ref, dims[0] // 2) < 1e-6
     finally:
         dp.dp_destroy(c)
+
+
+def test_request_admitted_at_a_convergence_check():
+    """A request that arrives while its field's batch is inside a round (and
+    has free slots) ends the running inner solve at its next convergence
+    check and is admitted at once; both results still equal direct solves
+    (1e-6 per slice)."""
+    require_gpu()
+    c = dp.dp_create(0)
+    try:
+        dims = (48, 24, 24, 24)
+        f = dp.dp_field_load(c, field(dims, 0.3, 1), dims, -1)
+        dp.dp_field_set_csw(c, f, 1.7)
+        dp.dp_serve_start(c, 0, 24)
+        reqs = [(0.5, ("cosh_t", 0.4), (0, 0, 0, 0)), (0.6, ("cosh_t", 0.4), (5, 3, 2, 1))]
+        yielded = False
+        for delay in (0.04, 0.02, 0.06):
+            t0 = dp.dp_submit(c, f, *reqs[0], 1e-10)
+            time.sleep(delay)  # the first request is inside its first round
+            t1 = dp.dp_submit(c, f, *reqs[1], 1e-10)
+            out = [dp.dp_wait(c, t, dims[0], timeout_s=300, allow=())[0] for t in (t0, t1)]
+            if dp.dp_serve_stats_get(c)["yields"] >= 1:
+                yielded = True
+                break
+        dp.dp_serve_stop(c, 1)
+        assert yielded
+        for cpp, (M, prof, src) in zip(out, reqs):
+            ref, _, _ = dp.dp_solve_point(c, f, M, prof, src, 1e-10,
+                                          {"prec": "mixed_fp32", "batched": 1}, T=dims[0])
+            assert slice_rel(cpp, ref, dims[0] // 2) < 1e-6
+    finally:
+        dp.dp_destroy(c)
