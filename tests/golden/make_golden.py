@@ -25,7 +25,10 @@ a JSON file in this directory with the inputs that produced it.
   cpp_32x16_multimass.json : the same for the 32x16^3 multi-mass workload
       (eps = 0.4, seed 3, c_sw = 1.7, M in {0.01, 0.1, 0.5, 0.8}).
 
-Run:  python tests/golden/make_golden.py [heavy|free|light64|multimass32]
+  oracle_iters_48x24_r1e-11.json : the oracle's BiCGStab iteration count for
+      one right-hand side of the 48x24^3 heavy-quark workload at r = 1e-11.
+
+Run:  python tests/golden/make_golden.py [heavy|free|light64|multimass32|iters48]
 """
 import json
 import os
@@ -99,6 +102,27 @@ def multimass_32x16():
     _certified((32, 16, 16, 16), 0.4, 3, 1.7, [0.01, 0.1, 0.5, 0.8], "cpp_32x16_multimass.json")
 
 
+def iters_48x24():
+    """Oracle BiCGStab iterations of one right-hand side (source component 0
+    at the origin) of the 48x24^3 heavy-quark workload to r = 1e-11, the
+    benchmark's residue (the reference arm's iteration count)."""
+    dims = (48, 24, 24, 24)
+    eps, seed, csw, M, alpha0, tol = 0.3, 1, 1.7, 0.5, 0.4, 1e-11
+    U = li.su3_links(dims, eps, seed)
+    op = oracle.WilsonClover(U, dims, csw, -1)
+    al = oracle.profile_alpha("cosh_t", alpha0, dims)
+    eta = oracle.point_sources(dims, (0, 0, 0, 0), al[0][0])[:1]
+    t0 = time.time()
+    _, iters, rel, ok = op.solve(eta, M, ("cosh_t", alpha0, (0, 0, 0, 0)), tol=tol)
+    out = {"what": "oracle BiCGStab iterations, one RHS (component 0, origin source)",
+           "dims": list(dims), "eps": eps, "seed": seed, "csw": csw, "M": M,
+           "profile": "cosh_t", "alpha0": alpha0, "tol": tol, "iters": int(iters[0]),
+           "relres": float(rel[0]), "converged": bool(ok), "seconds": time.time() - t0,
+           "oracle_threads": oracle.num_threads()}
+    with open(os.path.join(HERE, "oracle_iters_48x24_r1e-11.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
 def free_16x8():
     dims, M = (16, 8, 8, 8), 0.5
     cpp = oracle.free_cpp(dims, M, -1)
@@ -120,3 +144,5 @@ if __name__ == "__main__":
         multimass_32x16()
     if "light64" in which:
         light_64x32()
+    if "iters48" in which:
+        iters_48x24()
