@@ -61,3 +61,21 @@ def test_reference_arm_on_a_non_zero_rank_exits_quietly():
                        timeout=300, cwd=ROOT)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_gpus_flag_spawns_local_ranks_or_refuses(monkeypatch):
+    """`bench.py --gpus N` without a torchrun environment starts N local ranks
+    through torch.distributed.run on 127.0.0.1 (one per GPU, the same
+    arguments), and refuses when fewer GPUs are visible."""
+    calls = []
+    monkeypatch.setattr(bench.subprocess, "call", lambda cmd: calls.append(cmd) or 0)
+    monkeypatch.setattr(torch.cuda, "device_count", lambda: 4)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--gpus", "2", "--steps", "3"])
+    assert bench.spawn_local_ranks(2) == 0
+    cmd = calls[0]
+    assert cmd[1:4] == ["-m", "torch.distributed.run", "--nnodes=1"]
+    assert cmd[cmd.index("--nproc-per-node") + 1] == "2"
+    assert cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
+    assert cmd[-4:] == ["--gpus", "2", "--steps", "3"]
+    monkeypatch.setattr(torch.cuda, "device_count", lambda: 1)
+    assert bench.spawn_local_ranks(2) == 2 and len(calls) == 1
