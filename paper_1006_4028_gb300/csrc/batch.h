@@ -104,8 +104,9 @@ class Batch {
     // starts, continues or ends their refinement (updates hs; sets *changed)
     dp_status slice_check(bool *changed);
     // inner solver's profile of a job: a time table that flattens the
-    // restored per-slice norms xx[t] (absolute t) of its current solution
-    dp_status set_inner_profile(const Job &j, const double *xx);
+    // restored per-slice norms of its current solution; h[2t] = |x_t|^2,
+    // h[2t + 1] = |r_t|^2 (absolute t)
+    dp_status set_inner_profile(const Job &j, const double *h);
     dp_status bicgstab(int max_iter, int *iters_done);
     dp_status cgne(int max_iter, int *iters_done);
     dp_status sap_gcr(int max_iter, int *iters_done);

@@ -941,21 +941,32 @@ bool Batch::any_refining() const
     return false;
 }
 
-dp_status Batch::set_inner_profile(const Job &j, const double *xx)
+dp_status Batch::set_inner_profile(const Job &j, const double *h)
 {
     const Geom &g = f->g;
     const int Lm = g.Lmax, T = g.T, m = j.tab;
-    // alpha_B,t(t) = |x_src|/|x_t| in the restored metric (a slice without a
-    // usable norm keeps its neighbour's factor), times 1 in space
+    // alpha_B,t(t) = |x_src|/|x_t| in the restored metric, times 1 in space,
+    // walking away from the source.  Only slices the solution already resolves
+    // (their own residual below a tenth of their norm) say how fast the
+    // propagator falls; an unresolved slice holds noise (or nothing yet), so it
+    // continues the slice-to-slice factor of the last resolved step (between
+    // 1 and e^1.5).  No step exceeds e^{+-2}.
+    constexpr double kStep = 7.389056098930650;   // e^2
+    constexpr double kGrowMax = 4.481689070338065; // e^1.5
     std::vector<double> tt(T), one(Lm, 1.0);
     const int ts = j.grp.src[0];
-    const double ref = xx[ts];
-    double prev = 1.0;
+    const double ref = h[2 * ts] > 0 && std::isfinite(h[2 * ts]) ? h[2 * ts] : 1.0;
+    double prev = 1.0, growth = 1.0;
     for (int k = 0; k < T; k++) {
         const int t = (ts + k) % T;
-        const double v = xx[t];
-        double a = (v > 0 && ref > 0 && std::isfinite(v)) ? std::sqrt(ref / v) : prev;
+        const double v = h[2 * t], rr = h[2 * t + 1];
+        const bool resolved = v > 0 && std::isfinite(v) && std::isfinite(rr) && rr <= 0.01 * v;
+        double a = resolved ? std::sqrt(ref / v) : prev * growth;
         if (!(a > 0) || !std::isfinite(a)) a = prev;
+        if (k > 0) {
+            a = std::min(std::max(a, prev / kStep), prev * kStep);
+            if (resolved) growth = std::min(std::max(a / prev, 1.0), kGrowMax);
+        }
         tt[t] = prev = a;
     }
     dp_profile pf{};
@@ -1026,14 +1037,14 @@ dp_status Batch::slice_check(bool *changed)
     CK(cudaMemcpyAsync(slice_h.data(), slice_d, sizeof(double) * ng * T * 2, cudaMemcpyDeviceToHost,
                        st_));
     CK(cudaStreamSynchronize(st_));
-    std::vector<double> xx(T);
     for (Job *j : cand) {
         const double *h = slice_h.data() + (size_t)j->tab * T * 2;
         double worst = 0;
         for (int t = 0; t < T; t++) {
             const double a = h[2 * t], b = h[2 * t + 1];
-            xx[t] = a;
-            const double rho = a > 0 ? std::sqrt(b / a) : (b > 0 ? INFINITY : 0.0);
+            // a slice the solution has not reached (zero norm, residual left)
+            // counts as far from its target, not as a non-finite result
+            const double rho = a > 0 ? std::sqrt(b / a) : (b > 0 ? 1e300 : 0.0);
             if (!(rho <= worst)) worst = rho;  // NaN propagates
         }
         j->slice_res = worst;
@@ -1069,7 +1080,7 @@ dp_status Batch::slice_check(bool *changed)
             j->refine_rounds = 0;
             j->slice_best = worst;
             j->slice_stall = 0;
-            s = set_inner_profile(*j, xx.data());
+            s = set_inner_profile(*j, h);
             if (s != DP_OK) return s;
             set_all(1, 0, 1);
         } else {
@@ -1083,7 +1094,7 @@ dp_status Batch::slice_check(bool *changed)
                 set_all(0, std::isfinite(worst) ? 4 : 3, 0);
                 j->refining = false;
             } else {
-                s = set_inner_profile(*j, xx.data());
+                s = set_inner_profile(*j, h);
                 if (s != DP_OK) return s;
                 set_all(1, 0, 1);  // the next round's tolerance
             }
