@@ -53,6 +53,8 @@ struct Op {
 struct InnerVecs {
     void *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr,
          *x = nullptr, *to = nullptr;
+    // FP32 BiCGStab: rhat' = Mhat^dag rhat and the per-site omega sums
+    void *rh2 = nullptr, *dots = nullptr;
 };
 
 class Batch {

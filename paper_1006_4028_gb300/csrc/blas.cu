@@ -477,7 +477,7 @@ cudaError_t blas_bicg_init(BlasCtx &bc, int prec, const void *b, void *r, void *
 cudaError_t blas_bicg_p(BlasCtx &bc, int prec, const void *r, void *p, const void *v,
                         long long Vh, int nrhs, const RhsState *st, int first, cudaStream_t s)
 {
-    if (prec != 0) return cudaErrorInvalidValue;  // FP32: the p update rides in blas32_update_p
+    if (prec != 0) return cudaErrorInvalidValue;  // FP32: the p update rides in blas32_update_pa
     const Cfg c = cfg_wave(bc, k_bicg_p, Vh, nrhs);
     k_bicg_p<<<c.grid, c.block, 0, s>>>(c, r, p, v, Vh, nrhs, st, first);
     return cudaGetLastError();
@@ -495,7 +495,7 @@ cudaError_t blas_bicg_alpha(BlasCtx &bc, int prec, const void *rhat, const void 
 cudaError_t blas_bicg_s(BlasCtx &bc, int prec, const void *r, const void *v, void *sv,
                         long long Vh, int nrhs, const RhsState *st, cudaStream_t s)
 {
-    if (prec != 0) return blas32_s(bc, r, v, sv, Vh, nrhs, st, s);
+    if (prec != 0) return cudaErrorInvalidValue;  // FP32: blas32_s_dots
     const Cfg c = cfg_wave(bc, k_bicg_s, Vh, nrhs);
     k_bicg_s<<<c.grid, c.block, 0, s>>>(c, r, v, sv, Vh, nrhs, st);
     return cudaGetLastError();
@@ -504,7 +504,7 @@ cudaError_t blas_bicg_s(BlasCtx &bc, int prec, const void *r, const void *v, voi
 cudaError_t blas_bicg_omega(BlasCtx &bc, int prec, const void *t, const void *sv,
                             long long Vh, int nrhs, RhsState *st, cudaStream_t s)
 {
-    if (prec != 0) return cudaErrorInvalidValue;  // FP32: blas32_omega_rho
+    if (prec != 0) return cudaErrorInvalidValue;  // FP32: blas32_omega_dots
     const Cfg c = cfg_wave(bc, k_bicg_omega, Vh, nrhs);
     k_bicg_omega<<<c.grid, c.block, 0, s>>>(c, t, sv, Vh, nrhs, st, bc.partials, bc.counter);
     return cudaGetLastError();
@@ -516,7 +516,7 @@ cudaError_t blas_bicg_update(BlasCtx &bc, int prec, void *x, void *r, const void
 {
     cudaError_t e;
     if (prec != 0) {
-        return cudaErrorInvalidValue;  // FP32: blas32_update_p
+        return cudaErrorInvalidValue;  // FP32: blas32_update_pa
     } else {
         const Cfg c = cfg_wave(bc, k_bicg_update, Vh, nrhs);
         k_bicg_update<<<c.grid, c.block, 0, s>>>(c, x, r, p, sv, t, rhat, Vh, nrhs, st, max_iter,

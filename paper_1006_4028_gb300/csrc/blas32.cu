@@ -115,21 +115,6 @@ __global__ void __launch_bounds__(kMaxBlock) k32_alpha(Cfg c, const void *rh, co
     finish_alpha(st[2 * q + 1], acc[2], acc[3]);
 }
 
-__global__ void __launch_bounds__(kMaxBlock) k32_s(Cfg c, const void *rv, const void *vv, void *sv, long long Vh, int nrhs,
-                      const RhsState *st)
-{
-    const int qq = threadIdx.x % (nrhs / 2);
-    const C2 mal = neg(lanes(st[2 * qq].alpha, st[2 * qq + 1].alpha));
-    PAIR_LOOP
-    {
-        const long long me = s * P + q;
-        P12 r = ldp(rv, cs, me), v = ldp(vv, cs, me);
-#pragma unroll
-        for (int k = 0; k < 12; k++) r.c[k] = c2_lanefma(mal, v.c[k], r.c[k]);
-        stp(sv, cs, me, r);
-    }
-}
-
 // keep the lanes of `old` whose RHS is inactive
 __device__ __forceinline__ f2 blend(f2 nw, f2 old, f2 m) { return (nw & m) | (old & ~m); }
 
@@ -157,107 +142,142 @@ __global__ void __launch_bounds__(kMaxBlock) k32_init(Cfg c, const void *bv, voi
     finish_init(st[2 * q + 1], acc[1]);
 }
 
-// ---- BiCGStab with the p update fused into the x, r update ----
+// ---- BiCGStab with the shadow image rhat' = Mhat^dag rhat ----
 //
-// omega = <t, s>/|t|^2 and rho' = <rhat, s> - omega <rhat, t> from one pass
-// over t, s, rhat; then one pass x += alpha p + omega s, r = s - omega t,
-// p = r + beta (p - omega v), |r|^2: 16 vector streams per iteration
-// instead of 18 (and one launch fewer).
+// <rhat, v> = <rhat', p> is formed where p is written (update_pa), <rhat, t>
+// = <rhat', s> where s is written (s_dots), <t, s> and |t|^2 in the
+// x - A^-1 D launch that forms t (per-site sums, totalled by omega_dots):
+// 14 vector streams per iteration (s_dots: r, v, rhat, rhat' -> s; update:
+// x, p, s, t, v, rhat' -> x, r, p) and no separate alpha or omega pass.
 
-__global__ void __launch_bounds__(kMaxBlock) k32_omega_rho(Cfg c, const void *tv, const void *sv,
-                                                           const void *rh, long long Vh, int nrhs,
-                                                           RhsState *st, double *partials,
-                                                           unsigned int *counter)
+__global__ void __launch_bounds__(kMaxBlock) k32_s_dots(Cfg c, const void *rv, const void *vv,
+                                                        void *sv, const void *rh, const void *rh2,
+                                                        long long Vh, int nrhs, RhsState *st,
+                                                        double *partials, unsigned int *counter)
 {
-    double acc[14];
+    double acc[8];
 #pragma unroll
-    for (int k = 0; k < 14; k++) acc[k] = 0;
+    for (int k = 0; k < 8; k++) acc[k] = 0;
     {
-        f2 sum0 = 0ull, sum1 = 0ull, sum2 = 0ull, sum3 = 0ull, sum4 = 0ull, sum5 = 0ull, sum6 = 0ull;
+        const int qq = threadIdx.x % (nrhs / 2);
+        const C2 mal = neg(lanes(st[2 * qq].alpha, st[2 * qq + 1].alpha));
+        f2 sum0 = 0ull, sum1 = 0ull, sum2 = 0ull, sum3 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
-            f2 tsr = 0ull, tsi = 0ull, tt = 0ull, rsr = 0ull, rsi = 0ull, rtr = 0ull, rti = 0ull;
+            f2 rsr = 0ull, rsi = 0ull, rtr = 0ull, rti = 0ull;
 #pragma unroll 4
             for (int k = 0; k < 12; k++) {
-                const C2 t = ld1(tv, cs, me, k), sx = ld1(sv, cs, me, k), h = ld1(rh, cs, me, k);
-                tsr = ffma2(t.re, sx.re, tsr);
-                tsr = ffma2(t.im, sx.im, tsr);
-                tsi = ffma2(t.re, sx.im, tsi);
-                tsi = ffma2(fneg2(t.im), sx.re, tsi);
-                tt = ffma2(t.re, t.re, tt);
-                tt = ffma2(t.im, t.im, tt);
+                // every load ahead of the store (the pointers may alias, so a
+                // later load could not be moved above it)
+                const C2 r = ld1(rv, cs, me, k), v = ld1(vv, cs, me, k);
+                const C2 h = ld1(rh, cs, me, k), h2 = ld1(rh2, cs, me, k);
+                const C2 sx = c2_lanefma(mal, v, r);
+                st1(sv, cs, me, k, sx);
                 rsr = ffma2(h.re, sx.re, rsr);
                 rsr = ffma2(h.im, sx.im, rsr);
                 rsi = ffma2(h.re, sx.im, rsi);
                 rsi = ffma2(fneg2(h.im), sx.re, rsi);
-                rtr = ffma2(h.re, t.re, rtr);
-                rtr = ffma2(h.im, t.im, rtr);
-                rti = ffma2(h.re, t.im, rti);
-                rti = ffma2(fneg2(h.im), t.re, rti);
+                rtr = ffma2(h2.re, sx.re, rtr);
+                rtr = ffma2(h2.im, sx.im, rtr);
+                rti = ffma2(h2.re, sx.im, rti);
+                rti = ffma2(fneg2(h2.im), sx.re, rti);
             }
-            sum0 = fadd2(sum0, tsr);
-            sum1 = fadd2(sum1, tsi);
-            sum2 = fadd2(sum2, tt);
-            sum3 = fadd2(sum3, rsr);
-            sum4 = fadd2(sum4, rsi);
-            sum5 = fadd2(sum5, rtr);
-            sum6 = fadd2(sum6, rti);
+            sum0 = fadd2(sum0, rsr);
+            sum1 = fadd2(sum1, rsi);
+            sum2 = fadd2(sum2, rtr);
+            sum3 = fadd2(sum3, rti);
         }
-        add_lanes(acc[0], acc[7], sum0, a0, a1);
-        add_lanes(acc[1], acc[8], sum1, a0, a1);
-        add_lanes(acc[2], acc[9], sum2, a0, a1);
-        add_lanes(acc[3], acc[10], sum3, a0, a1);
-        add_lanes(acc[4], acc[11], sum4, a0, a1);
-        add_lanes(acc[5], acc[12], sum5, a0, a1);
-        add_lanes(acc[6], acc[13], sum6, a0, a1);
+        add_lanes(acc[0], acc[4], sum0, a0, a1);
+        add_lanes(acc[1], acc[5], sum1, a0, a1);
+        add_lanes(acc[2], acc[6], sum2, a0, a1);
+        add_lanes(acc[3], acc[7], sum3, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
-    if (!reduce_last<7, 2>(acc, c, partials, counter, nrhs / 2)) return;
-    finish_omega_rho(st[2 * q], acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], acc[6]);
-    finish_omega_rho(st[2 * q + 1], acc[7], acc[8], acc[9], acc[10], acc[11], acc[12], acc[13]);
+    if (!reduce_last<4, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    finish_s_dots(st[2 * q], acc[0], acc[1], acc[2], acc[3]);
+    finish_s_dots(st[2 * q + 1], acc[4], acc[5], acc[6], acc[7]);
+}
+
+__global__ void __launch_bounds__(kMaxBlock) k32_omega_dots(Cfg c, const void *dots, long long Vh,
+                                                            int nrhs, RhsState *st,
+                                                            double *partials, unsigned int *counter)
+{
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    {
+        const f2 *d = static_cast<const f2 *>(dots);
+        f2 sum0 = 0ull, sum1 = 0ull, sum2 = 0ull;
+        PAIR_LOOP
+        {
+            const long long me = s * P + q;
+            sum0 = fadd2(sum0, __ldg(d + me));
+            sum1 = fadd2(sum1, __ldg(d + cs + me));
+            sum2 = fadd2(sum2, __ldg(d + 2 * cs + me));
+        }
+        add_lanes(acc[0], acc[3], sum0, a0, a1);
+        add_lanes(acc[1], acc[4], sum1, a0, a1);
+        add_lanes(acc[2], acc[5], sum2, a0, a1);
+    }
+    const int q = threadIdx.x % (nrhs / 2);
+    if (!reduce_last<3, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    finish_omega_shadow(st[2 * q], acc[0], acc[1], acc[2]);
+    finish_omega_shadow(st[2 * q + 1], acc[3], acc[4], acc[5]);
 }
 
 __global__ void __launch_bounds__(kMaxBlock)
-k32_update_p(Cfg c, void *xv, void *rv, void *pv, const void *sv, const void *tv, const void *vv,
-             long long Vh, int nrhs, RhsState *st, int max_iter, double *partials,
-             unsigned int *counter)
+k32_update_pa(Cfg c, void *xv, void *rv, void *pv, const void *sv, const void *tv, const void *vv,
+              const void *rh2, long long Vh, int nrhs, RhsState *st, int max_iter,
+              double *partials, unsigned int *counter)
 {
-    double acc[2] = {0, 0};
+    double acc[6] = {0, 0, 0, 0, 0, 0};
     {
         const int qq = threadIdx.x % (nrhs / 2);
         const C2 al = lanes(st[2 * qq].alpha, st[2 * qq + 1].alpha);
         const C2 om = lanes(st[2 * qq].omega, st[2 * qq + 1].omega);
         const C2 be = lanes(st[2 * qq].beta, st[2 * qq + 1].beta);
         const C2 mom = neg(om);
-        f2 sum0 = 0ull;
+        f2 sum0 = 0ull, sum1 = 0ull, sum2 = 0ull;
         PAIR_LOOP
         {
             const long long me = s * P + q;
             const f2 m = (a0 ? 0x00000000ffffffffull : 0ull) | (a1 ? 0xffffffff00000000ull : 0ull);
-            f2 nn = 0ull;
+            f2 nn = 0ull, rpr = 0ull, rpi = 0ull;
 #pragma unroll 4
             for (int k = 0; k < 12; k++) {
                 const C2 x = ld1(xv, cs, me, k), p = ld1(pv, cs, me, k), sx = ld1(sv, cs, me, k);
                 const C2 t = ld1(tv, cs, me, k), v = ld1(vv, cs, me, k);
+                const C2 h2 = ld1(rh2, cs, me, k);  // with the others, ahead of the stores
                 C2 xn = c2_lanefma(om, sx, c2_lanefma(al, p, x));
                 xn.re = blend(xn.re, x.re, m);
                 xn.im = blend(xn.im, x.im, m);
                 st1(xv, cs, me, k, xn);
                 const C2 r = c2_lanefma(mom, t, sx);
                 st1(rv, cs, me, k, r);
-                st1(pv, cs, me, k, c2_lanefma(be, c2_lanefma(mom, v, p), r));
+                const C2 pn = c2_lanefma(be, c2_lanefma(mom, v, p), r);
+                st1(pv, cs, me, k, pn);
                 nn = ffma2(r.re, r.re, nn);
                 nn = ffma2(r.im, r.im, nn);
+                rpr = ffma2(h2.re, pn.re, rpr);
+                rpr = ffma2(h2.im, pn.im, rpr);
+                rpi = ffma2(h2.re, pn.im, rpi);
+                rpi = ffma2(fneg2(h2.im), pn.re, rpi);
             }
             sum0 = fadd2(sum0, nn);
+            sum1 = fadd2(sum1, rpr);
+            sum2 = fadd2(sum2, rpi);
         }
-        add_lanes(acc[0], acc[1], sum0, a0, a1);
+        add_lanes(acc[0], acc[3], sum0, a0, a1);
+        add_lanes(acc[1], acc[4], sum1, a0, a1);
+        add_lanes(acc[2], acc[5], sum2, a0, a1);
     }
     const int q = threadIdx.x % (nrhs / 2);
-    if (!reduce_last<1, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    if (!reduce_last<3, 2>(acc, c, partials, counter, nrhs / 2)) return;
+    // convergence on |r|^2, then the next alpha = rho' / <rhat', p> for the
+    // RHS still iterating
     finish_update_rr(st[2 * q], acc[0], max_iter);
-    finish_update_rr(st[2 * q + 1], acc[1], max_iter);
+    finish_alpha(st[2 * q], acc[1], acc[2]);
+    finish_update_rr(st[2 * q + 1], acc[3], max_iter);
+    finish_alpha(st[2 * q + 1], acc[4], acc[5]);
 }
 
 // ---- CGNE on the normal equations: real per-RHS scalars, per lane ----
@@ -601,23 +621,32 @@ cudaError_t blas32_init(BlasCtx &bc, const void *b, void *r, void *rh, long long
     return cudaGetLastError();
 }
 
-cudaError_t blas32_omega_rho(BlasCtx &bc, const void *t, const void *sv, const void *rh,
-                             long long Vh, int nrhs, RhsState *st, cudaStream_t s)
+cudaError_t blas32_s_dots(BlasCtx &bc, const void *r, const void *v, void *sv, const void *rh,
+                          const void *rh2, long long Vh, int nrhs, RhsState *st, cudaStream_t s)
 {
     if (nrhs % 2) return cudaErrorInvalidValue;
-    const Cfg c = cfg_wave(bc, k32_omega_rho, Vh, nrhs / 2);
-    k32_omega_rho<<<c.grid, c.block, 0, s>>>(c, t, sv, rh, Vh, nrhs, st, bc.partials, bc.counter);
+    const Cfg c = cfg_wave(bc, k32_s_dots, Vh, nrhs / 2);
+    k32_s_dots<<<c.grid, c.block, 0, s>>>(c, r, v, sv, rh, rh2, Vh, nrhs, st, bc.partials, bc.counter);
     return cudaGetLastError();
 }
 
-cudaError_t blas32_update_p(BlasCtx &bc, void *x, void *r, void *p, const void *sv, const void *t,
-                            const void *v, long long Vh, int nrhs, RhsState *st, int max_iter,
-                            cudaStream_t s)
+cudaError_t blas32_omega_dots(BlasCtx &bc, const void *dots, long long Vh, int nrhs, RhsState *st,
+                              cudaStream_t s)
 {
     if (nrhs % 2) return cudaErrorInvalidValue;
-    const Cfg c = cfg_wave(bc, k32_update_p, Vh, nrhs / 2);
-    k32_update_p<<<c.grid, c.block, 0, s>>>(c, x, r, p, sv, t, v, Vh, nrhs, st, max_iter,
-                                            bc.partials, bc.counter);
+    const Cfg c = cfg_wave(bc, k32_omega_dots, Vh, nrhs / 2);
+    k32_omega_dots<<<c.grid, c.block, 0, s>>>(c, dots, Vh, nrhs, st, bc.partials, bc.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t blas32_update_pa(BlasCtx &bc, void *x, void *r, void *p, const void *sv, const void *t,
+                             const void *v, const void *rh2, long long Vh, int nrhs, RhsState *st,
+                             int max_iter, cudaStream_t s)
+{
+    if (nrhs % 2) return cudaErrorInvalidValue;
+    const Cfg c = cfg_wave(bc, k32_update_pa, Vh, nrhs / 2);
+    k32_update_pa<<<c.grid, c.block, 0, s>>>(c, x, r, p, sv, t, v, rh2, Vh, nrhs, st, max_iter,
+                                             bc.partials, bc.counter);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return blas_count_active(bc, st, nrhs, s);
@@ -629,15 +658,6 @@ cudaError_t blas32_alpha(BlasCtx &bc, const void *rh, const void *v, long long V
     if (nrhs % 2) return cudaErrorInvalidValue;
     const Cfg c = cfg_wave(bc, k32_alpha, Vh, nrhs / 2);
     k32_alpha<<<c.grid, c.block, 0, s>>>(c, rh, v, Vh, nrhs, st, bc.partials, bc.counter);
-    return cudaGetLastError();
-}
-
-cudaError_t blas32_s(BlasCtx &bc, const void *r, const void *v, void *sv, long long Vh, int nrhs,
-                     const RhsState *st, cudaStream_t s)
-{
-    if (nrhs % 2) return cudaErrorInvalidValue;
-    const Cfg c = cfg_wave(bc, k32_s, Vh, nrhs / 2);
-    k32_s<<<c.grid, c.block, 0, s>>>(c, r, v, sv, Vh, nrhs, st);
     return cudaGetLastError();
 }
 

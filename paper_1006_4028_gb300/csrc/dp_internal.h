@@ -80,6 +80,10 @@ struct DslashParams {
     int parity;             // output parity
     int nrhs;
     int8_t grp_of[kMaxRhs]; // RHS -> group
+    // NULL, or (FP32, x - A^-1 D epilogue) per-site partial sums of the
+    // BiCGStab omega: f2 (one lane per RHS of a pair) [3][Vh][nrhs/2] holding
+    // Re <out, x>, Im <out, x> and |out|^2 over the 12 components of a site
+    void *dots;
 };
 
 // ---- launch wrappers (dslash.cu) ----
@@ -196,9 +200,10 @@ struct RhsState {        // per RHS, device resident
     int iters;
     int status;           // 0 running, 1 converged, 2 breakdown, 3 non-finite, 4 max-iter
     int fresh;            // 1: x = 0, next residual call sets |b|^2 and tol2
-    int brk;              // fused FP32 BiCGStab: breakdown found by the omega reduction
+    int brk;              // FP32 BiCGStab: breakdown found by the omega reduction
     int refine;           // FP64 outer loop: per-slice refinement (the inner solve runs in
                           // another profile's metric; the global test does not stop it)
+    double2 rs, rt;       // FP32 BiCGStab: <rhat, s> and <rhat', s> = <rhat, Mhat s>
 };
 
 constexpr int kRedWidth = 8;  // values per RHS in a block's reduction partials
@@ -214,8 +219,9 @@ struct BlasCtx {
 cudaError_t blas_bicg_init(BlasCtx &bc, int prec, const void *b, void *r, void *rhat, void *p,
                            void *v, void *x, long long Vh, int nrhs, RhsState *st, double tol,
                            cudaStream_t s);
-// p, omega and update: FP64 only (the FP32 solver uses blas32_omega_rho and
-// blas32_update_p, which carry the p update); alpha and s: both precisions
+// p, s, omega and update: FP64 only (the FP32 solver uses blas32_s_dots,
+// blas32_omega_dots and blas32_update_pa, which carry the p update); alpha:
+// both precisions
 cudaError_t blas_bicg_p(BlasCtx &bc, int prec, const void *r, void *p, const void *v,
                         long long Vh, int nrhs, const RhsState *st, int first, cudaStream_t s);
 cudaError_t blas_bicg_alpha(BlasCtx &bc, int prec, const void *rhat, const void *v,
@@ -230,20 +236,25 @@ cudaError_t blas_bicg_update(BlasCtx &bc, int prec, void *x, void *r, const void
 // FP32 inner solver on the paired layout (blas32.cu); nrhs even
 cudaError_t blas32_init(BlasCtx &bc, const void *b, void *r, void *rh, long long Vh, int nrhs,
                         RhsState *st, cudaStream_t s, void *p = nullptr);
-// BiCGStab with the p update fused into the x, r update (FP32 inner solver):
-// init r = rhat = p = b (x = 0); per iteration v = Mhat p, alpha, s = r -
-// alpha v, t = Mhat s, then omega_rho (omega, rho' = <rhat,s> - omega
-// <rhat,t>, beta) and update_p (x += alpha p + omega s, r = s - omega t,
-// p = r + beta (p - omega v), |r|^2 decides convergence)
-cudaError_t blas32_omega_rho(BlasCtx &bc, const void *t, const void *sv, const void *rh,
-                             long long Vh, int nrhs, RhsState *st, cudaStream_t s);
-cudaError_t blas32_update_p(BlasCtx &bc, void *x, void *r, void *p, const void *sv, const void *t,
-                            const void *v, long long Vh, int nrhs, RhsState *st, int max_iter,
-                            cudaStream_t s);
 cudaError_t blas32_alpha(BlasCtx &bc, const void *rh, const void *v, long long Vh, int nrhs,
                          RhsState *st, cudaStream_t s);
-cudaError_t blas32_s(BlasCtx &bc, const void *r, const void *v, void *sv, long long Vh, int nrhs,
-                     const RhsState *st, cudaStream_t s);
+// BiCGStab with the shadow image rhat' = Mhat^dag rhat (formed once per
+// inner solve), so that <rhat, v> = <rhat', p> and <rhat, t> = <rhat', s>
+// ride in passes that already read p and s, and <t, s>, |t|^2 in the
+// x - A^-1 D launch that forms t (DslashParams::dots).  Init: blas32_init,
+// rhat' = Mhat^dag rhat, alpha = rho / <rhat', p> (blas32_alpha).  Per
+// iteration: v = Mhat p; s_dots (s = r - alpha v, <rhat, s>, <rhat', s>);
+// t = Mhat s with the dots; omega_dots (omega, rho' = <rhat, s> -
+// omega <rhat', s>, beta); update_pa (x += alpha p + omega s, r = s - omega t,
+// p = r + beta (p - omega v), |r|^2 decides convergence, next alpha =
+// rho' / <rhat', p>): 14 vector streams and 7 launches per iteration
+cudaError_t blas32_s_dots(BlasCtx &bc, const void *r, const void *v, void *sv, const void *rh,
+                          const void *rh2, long long Vh, int nrhs, RhsState *st, cudaStream_t s);
+cudaError_t blas32_omega_dots(BlasCtx &bc, const void *dots, long long Vh, int nrhs, RhsState *st,
+                              cudaStream_t s);
+cudaError_t blas32_update_pa(BlasCtx &bc, void *x, void *r, void *p, const void *sv, const void *t,
+                             const void *v, const void *rh2, long long Vh, int nrhs, RhsState *st,
+                             int max_iter, cudaStream_t s);
 // CGNE (CG on the normal equations Mhat^dag Mhat x = Mhat^dag b), per RHS,
 // real scalars in the .x parts of rho / alpha / beta.  Init: blas_bicg_init
 // (r = b, x = p = 0, |b|^2).  Per iteration, with z = Mhat^dag r and

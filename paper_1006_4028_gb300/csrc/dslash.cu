@@ -356,10 +356,35 @@ __device__ __forceinline__ void finish32(const DslashParams &p, C2 (&acc)[PPT][1
     for (int k = 0; k < PPT; k++) {
         if (!act[k]) continue;
         if (EPI == EPI_XMY_AINV) {
-            C2 v[12];
-            load_pair(xin + k, cs, v);
+            const ulonglong2 *xp = reinterpret_cast<const ulonglong2 *>(xin + k);
+            if (p.dots) {
+                // BiCGStab's <t, s> and |t|^2 for this site (t = out, s = x),
+                // component by component so that x is not held whole
+                f2 tsr = 0ull, tsi = 0ull, tt = 0ull;
 #pragma unroll
-            for (int j = 0; j < 12; j++) acc[k][j] = c2_sub(v[j], acc[k][j]);
+                for (int j = 0; j < 12; j++) {
+                    const ulonglong2 w = __ldg(xp + j * cs);
+                    const C2 v = {w.x, w.y};
+                    const C2 t = c2_sub(v, acc[k][j]);
+                    acc[k][j] = t;
+                    tsr = ffma2(t.re, v.re, tsr);
+                    tsr = ffma2(t.im, v.im, tsr);
+                    tsi = ffma2(t.re, v.im, tsi);
+                    tsi = ffma2(fneg2(t.im), v.re, tsi);
+                    tt = ffma2(t.re, t.re, tt);
+                    tt = ffma2(t.im, t.im, tt);
+                }
+                f2 *d = static_cast<f2 *>(p.dots) + me + k;
+                d[0] = tsr;
+                d[cs] = tsi;
+                d[2 * cs] = tt;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 12; j++) {
+                    const ulonglong2 w = __ldg(xp + j * cs);
+                    acc[k][j] = c2_sub(C2{w.x, w.y}, acc[k][j]);
+                }
+            }
         }
         store_pair(out + k, cs, acc[k]);
     }

@@ -109,6 +109,43 @@ __device__ __forceinline__ void finish_omega(RhsState &S, double re, double im, 
     S.omega = tt > 0 ? make_double2(re / tt, im / tt) : make_double2(0.0, 0.0);
 }
 
+// FP32 BiCGStab with the shadow image rhat' = Mhat^dag rhat: the s pass keeps
+// <rhat, s> and <rhat', s> (= <rhat, t>) for the omega step
+__device__ __forceinline__ void finish_s_dots(RhsState &S, double rs_re, double rs_im, double rt_re,
+                                              double rt_im)
+{
+    if (!S.active) return;
+    S.rs = make_double2(rs_re, rs_im);
+    S.rt = make_double2(rt_re, rt_im);
+    if (!(zfinite(S.rs) && zfinite(S.rt))) {
+        S.status = 3;
+        S.active = 0;
+    }
+}
+
+// omega = <t, s>/|t|^2 from the x - A^-1 D epilogue's sums, rho' = <rhat, s> -
+// omega <rhat', s>, beta = (rho'/rho)(alpha/omega); a breakdown is flagged
+// for the update pass (finish_update_rr)
+__device__ __forceinline__ void finish_omega_shadow(RhsState &S, double ts_re, double ts_im, double tt)
+{
+    if (!S.active) return;
+    if (!(isfinite(ts_re) && isfinite(ts_im) && isfinite(tt))) {
+        S.status = 3;
+        S.active = 0;
+        return;
+    }
+    S.omega = tt > 0 ? make_double2(ts_re / tt, ts_im / tt) : make_double2(0.0, 0.0);
+    const double2 wrt = zmul(S.omega, S.rt);
+    const double2 rho_new = make_double2(S.rs.x - wrt.x, S.rs.y - wrt.y);
+    if ((S.omega.x == 0.0 && S.omega.y == 0.0) || (rho_new.x == 0.0 && rho_new.y == 0.0)) {
+        S.brk = 1;
+        S.beta = make_double2(0.0, 0.0);
+    } else {
+        S.beta = zmul(zdiv(rho_new, S.rho), zdiv(S.alpha, S.omega));
+        S.rho = rho_new;
+    }
+}
+
 // iteration count, convergence, cap, breakdown; beta = (rho'/rho)(alpha/omega)
 __device__ __forceinline__ void finish_update(RhsState &S, double re, double im, double rr,
                                               int max_iter)
@@ -135,36 +172,8 @@ __device__ __forceinline__ void finish_update(RhsState &S, double re, double im,
     }
 }
 
-// The FP32 inner BiCGStab with the p update fused into the x, r update:
-// omega and the next rho come from one reduction, rho' = <rhat, r'> =
-// <rhat, s> - omega <rhat, t> (r' = s - omega t), so beta is known before the
-// update pass.  A breakdown found here (omega or rho' zero) is reported by
-// the update's finisher unless that pass converges.
-__device__ __forceinline__ void finish_omega_rho(RhsState &S, double ts_re, double ts_im, double tt,
-                                                 double rs_re, double rs_im, double rt_re,
-                                                 double rt_im)
-{
-    if (!S.active) return;
-    if (!(isfinite(ts_re) && isfinite(ts_im) && isfinite(tt) && isfinite(rs_re) && isfinite(rs_im) &&
-          isfinite(rt_re) && isfinite(rt_im))) {
-        S.status = 3;
-        S.active = 0;
-        return;
-    }
-    S.omega = tt > 0 ? make_double2(ts_re / tt, ts_im / tt) : make_double2(0.0, 0.0);
-    const double2 wrt = zmul(S.omega, make_double2(rt_re, rt_im));
-    const double2 rho_new = make_double2(rs_re - wrt.x, rs_im - wrt.y);
-    if ((S.omega.x == 0.0 && S.omega.y == 0.0) || (rho_new.x == 0.0 && rho_new.y == 0.0)) {
-        S.brk = 1;
-        S.beta = make_double2(0.0, 0.0);
-    } else {
-        S.beta = zmul(zdiv(rho_new, S.rho), zdiv(S.alpha, S.omega));
-        S.rho = rho_new;
-    }
-}
-
 // iteration count, convergence, cap, and a breakdown flagged by
-// finish_omega_rho
+// finish_omega_shadow
 __device__ __forceinline__ void finish_update_rr(RhsState &S, double rr, int max_iter)
 {
     if (!S.active) return;

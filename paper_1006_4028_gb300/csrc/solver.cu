@@ -56,12 +56,13 @@ struct Timed {
 };
 
 dp_status dslash(Ctx *c, const Op &op, int parity, int epi, const void *in, void *out,
-                 const void *x, const int *mask, int mask_stride)
+                 const void *x, const int *mask, int mask_stride, void *dots = nullptr)
 {
     DslashParams P{};
     P.in = in;
     P.out = out;
     P.x = x;
+    P.dots = dots;
     const Field &f = *op.f;
     P.links[0] = op.links[0];
     P.links[1] = op.links[1];
@@ -101,13 +102,15 @@ void set_shape(Op &op, const Shape &sh)
 const int *state_mask(const RhsState *st) { return st ? &st[0].active : nullptr; }
 
 // Schur operator on parity p (q = 1 - p):
-// y = Mhat x = x - A_pp^-1 D_pq A_qq^-1 D_qp x ; tmp (parity q) keeps A_qq^-1 D_qp x
+// y = Mhat x = x - A_pp^-1 D_pq A_qq^-1 D_qp x ; tmp (parity q) keeps A_qq^-1 D_qp x;
+// dots (FP32, or NULL): the second launch also leaves the per-site sums of
+// <y, x> and |y|^2 there (DslashParams::dots)
 dp_status apply_mhat(Ctx *c, const Op &op, int p, const void *x, void *y, void *tmp,
-                     const RhsState *mask)
+                     const RhsState *mask, void *dots = nullptr)
 {
     dp_status s = dslash(c, op, 1 - p, EPI_AINV, x, tmp, nullptr, state_mask(mask), kStateStride);
     if (s != DP_OK) return s;
-    return dslash(c, op, p, EPI_XMY_AINV, tmp, y, x, state_mask(mask), kStateStride);
+    return dslash(c, op, p, EPI_XMY_AINV, tmp, y, x, state_mask(mask), kStateStride, dots);
 }
 
 // Adjoint Schur operator.  With the hopping part H(alpha_B) and the clover
@@ -179,7 +182,9 @@ size_t Batch::bytes_needed(const Geom &g, int nslots, int prec)
 {
     const size_t v64 = (size_t)g.Vh * nslots * 24 * sizeof(double);
     const size_t vin = (size_t)g.Vh * nslots * 24 * (prec == DP_PREC_FP64 ? 8 : 4);
-    return 6 * v64 + 8 * vin + ((size_t)1 << 20);
+    // FP32 BiCGStab: rhat' and the omega sums (vin / 8) besides the 8 vectors
+    const size_t shadow = prec == DP_PREC_FP64 ? 0 : vin + vin / 8;
+    return 6 * v64 + 8 * vin + shadow + ((size_t)1 << 20);
 }
 
 dp_status Batch::init()
@@ -218,6 +223,11 @@ dp_status Batch::init()
     for (auto pp : iv) {
         *pp = get(vin);
         ok = ok && *pp;
+    }
+    if (mixed && opts.solver == DP_SOLVER_BICGSTAB) {
+        in.rh2 = get(vin);
+        in.dots = get(vin / 8);
+        ok = ok && in.rh2 && in.dots;
     }
     outer = (RhsState *)get(sizeof(RhsState) * kMaxRhs);
     inner = (RhsState *)get(sizeof(RhsState) * kMaxRhs);
@@ -525,13 +535,18 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
     BlasCtx &bc = bc_;
     const int pr = opin.pr;
     const long long Vh = f->g.Vh;
-    // FP32: the p update rides in the x, r update pass (blas32_update_p)
+    // FP32: the shadow form (blas32_s_dots / omega_dots / update_pa), with the
+    // p update in the x, r update pass and rhat' = Mhat^dag rhat
     const bool fused = pr == 1;
     if (fused) {
         CK(cudaMemsetAsync(in.x, 0, vin, st_));
         CK(cudaMemsetAsync(in.v, 0, vin, st_));
         CK(blas32_init(bc, in.rh, in.r, in.rh, Vh, n, inner, st_, in.p));
+        dp_status s = apply_mhat_dag(c, opin, opin_adj, sp, in.rh, in.rh2, in.s, in.to, inner);
+        if (s != DP_OK) return s;
+        CK(blas32_alpha(bc, in.rh2, in.p, Vh, n, inner, st_));
         CK(blas_count_active(bc, inner, n, st_));
+        c->launches += 1;
     } else {
         CK(blas_bicg_init(bc, pr, in.rh, in.r, in.rh, in.p, in.v, in.x, Vh, n, inner, 0.0, st_));
     }
@@ -547,51 +562,47 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
         dp_status s = apply_mhat(c, opin, sp, in.p, in.v, in.to, inner);
         if (s != DP_OK) return s;
         {
-            Timed tm(c, st_, "blas_inner");
-            CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, st_));
+            Timed tm(c, st_, "blas_s");
+            CK(blas32_s_dots(bc, in.r, in.v, in.s, in.rh, in.rh2, Vh, n, inner, st_));
         }
-        {
-            Timed tm(c, st_, "blas_inner");
-            CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, st_));
-        }
-        s = apply_mhat(c, opin, sp, in.s, in.t, in.to, inner);
+        s = apply_mhat(c, opin, sp, in.s, in.t, in.to, inner, in.dots);
         if (s != DP_OK) return s;
         {
-            Timed tm(c, st_, "blas_inner");
-            CK(blas32_omega_rho(bc, in.t, in.s, in.rh, Vh, n, inner, st_));
+            Timed tm(c, st_, "blas_omega");
+            CK(blas32_omega_dots(bc, in.dots, Vh, n, inner, st_));
         }
         {
-            Timed tm(c, st_, "blas_inner");
-            CK(blas32_update_p(bc, in.x, in.r, in.p, in.s, in.t, in.v, Vh, n, inner, max_iter,
-                               st_));
+            Timed tm(c, st_, "blas_update");
+            CK(blas32_update_pa(bc, in.x, in.r, in.p, in.s, in.t, in.v, in.rh2, Vh, n, inner,
+                                max_iter, st_));
         }
-        c->launches += 5;
+        c->launches += 4;
         return DP_OK;
     };
     auto body = [&](int first) -> dp_status {
         if (fused) return body_fused();
         {
-            Timed tm(c, st_, "blas_inner");
+            Timed tm(c, st_, "blas_p");
             CK(blas_bicg_p(bc, pr, in.r, in.p, in.v, Vh, n, inner, first, st_));
         }
         dp_status s = apply_mhat(c, opin, sp, in.p, in.v, in.to, inner);
         if (s != DP_OK) return s;
         {
-            Timed tm(c, st_, "blas_inner");
+            Timed tm(c, st_, "blas_alpha");
             CK(blas_bicg_alpha(bc, pr, in.rh, in.v, Vh, n, inner, st_));
         }
         {
-            Timed tm(c, st_, "blas_inner");
+            Timed tm(c, st_, "blas_s");
             CK(blas_bicg_s(bc, pr, in.r, in.v, in.s, Vh, n, inner, st_));
         }
         s = apply_mhat(c, opin, sp, in.s, in.t, in.to, inner);
         if (s != DP_OK) return s;
         {
-            Timed tm(c, st_, "blas_inner");
+            Timed tm(c, st_, "blas_omega");
             CK(blas_bicg_omega(bc, pr, in.t, in.s, Vh, n, inner, st_));
         }
         {
-            Timed tm(c, st_, "blas_inner");
+            Timed tm(c, st_, "blas_update");
             CK(blas_bicg_update(bc, pr, in.x, in.r, in.p, in.s, in.t, in.rh, Vh, n, inner, max_iter,
                                 st_));
         }
@@ -618,7 +629,7 @@ dp_status Batch::bicgstab(int max_iter, int *iters_done)
                 graph_max_iter = max_iter;
             }
             CK(cudaGraphLaunch(graph, st_));
-            c->launches += fused ? 9 : 10;
+            c->launches += fused ? 8 : 10;
         }
         it++;
         if (it >= max_iter) break;
