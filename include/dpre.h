@@ -445,8 +445,12 @@ dp_status dp_tune_set(dp_ctx *ctx, dp_field field, int prec, int compress12, int
  * solvers make; statistics accumulate per kernel name until reset. */
 dp_status dp_timing_enable(dp_ctx *ctx, int on);
 dp_status dp_timing_reset(dp_ctx *ctx);
-/* Statistics of kernel class `name` ("dslash_fp32", "dslash_fp64", "blas",
- * "reduce", ...): launches and total milliseconds.  Synchronises the stream. */
+/* Statistics of kernel class `name`: launches and total milliseconds of
+ * stream time while timing is on.  Classes: "dslash_fp32", "dslash_fp64",
+ * "dslash_df" (operator launches), "clover_apply", "sap_block", the inner
+ * solvers' BLAS passes ("blas_alpha", "blas_s", "blas_omega", "blas_update",
+ * "blas_p"), "outer_blas", "slice_norms", and the solver phases "admit",
+ * "round", "harvest".  Synchronises the stream. */
 dp_status dp_timing_get(dp_ctx *ctx, const char *name, long *launches, double *total_ms);
 /* Kernel launches made by this context since creation. */
 long dp_launch_count(dp_ctx *ctx);

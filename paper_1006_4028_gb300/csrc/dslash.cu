@@ -1068,8 +1068,9 @@ bool dslash_staged_ok(int prec, int link_fmt, int epi, int rpt, int stages, int 
         block % 32 == 0 && (epi == EPI_AINV || epi == EPI_XMY_AINV) &&
         (link_fmt == LINK_F32_12 || link_fmt == LINK_H16_12 || link_fmt == LINK_B16_12))
         return true;
+    // the spinor-staged kernel also serves the adjoint's x - g5 D launch
     if (prec == 1 && rpt == 2 && stages == 6 && (block == 64 || block == 96 || block == 128) &&
-        (epi == EPI_AINV || epi == EPI_XMY_AINV || epi == EPI_XMY_G5) && link_fmt == LINK_F32_18)
+        (epi == EPI_AINV || epi == EPI_XMY_AINV || epi == EPI_XMY_G5))
         return true;
     return prec == 1 && rpt == 2 && ((stages >= 2 && stages <= 4) || stages == 6) &&
            (block == 64 || block == 96 || block == 128) &&
