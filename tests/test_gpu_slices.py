@@ -29,6 +29,8 @@ FP64_BATCHED = {"prec": "fp64", "batched": 1, "use_graph": 0}
 MIXED_FP16 = {"prec": "mixed_fp16", "batched": 1, "use_graph": 1}
 CGNE_MIXED = {"prec": "mixed_fp32", "solver": "cgne", "batched": 1, "use_graph": 1}
 SAP_GCR = {"prec": "mixed_fp32", "solver": "sap_gcr", "batched": 1, "use_graph": 0}
+# the outer residual in double-float arithmetic instead of FP64
+MIXED_DF = {"prec": "mixed_fp32", "batched": 1, "use_graph": 1, "outer_df": 1}
 
 
 @pytest.fixture(scope="module")
@@ -59,13 +61,14 @@ def test_global_residue_alone_leaves_far_slices_wrong(setup):
     assert slice_rel(cpp, ref, DIMS[0] // 2) > 1e-4
 
 
-@pytest.mark.parametrize("opts", [MIXED, PLAIN, FP64_BATCHED, MIXED_FP16, CGNE_MIXED, SAP_GCR])
+@pytest.mark.parametrize("opts", [MIXED, PLAIN, FP64_BATCHED, MIXED_FP16, CGNE_MIXED, SAP_GCR,
+                                  MIXED_DF])
 def test_refinement_meets_per_slice_accuracy(setup, opts):
     ctx, f, ref = setup
     r = 1e-10
     cpp, _, info = dp.dp_solve_point(ctx, f, M, STEEP, (0, 0, 0, 0), r, opts, T=DIMS[0])
     assert info["status"] == 0, info
-    if opts is MIXED:  # the case shown to fail without the check
+    if opts is MIXED or opts is MIXED_DF:  # the case shown to fail without the check
         assert info["refine_rounds"] >= 1
     assert 0 < info["slice_residue"] <= max(10 * r, 1e-8)  # the default target
     assert slice_rel(cpp, ref, DIMS[0] // 2) < 1e-6
