@@ -386,6 +386,29 @@ def slice_err(cpp, ref, upto):
     return float(np.max(np.abs(c / r - 1)))
 
 
+def oracle_dslash_rate(U, dims, csw, M, prof, reps=3):
+    """The CPU oracle's full-lattice (D+M) application on one RHS at this
+    volume, timed on the host cores (a reported baseline): ms per
+    application, sites/s, and GB/s of algorithmic bytes V x (48 + 72 + 72)
+    x 8 (spinor in and out, the 4 links of a site read once as 18 reals
+    each, 72 reals of clover per site)."""
+    import lattice_inputs as li
+    import oracle
+
+    op = oracle.WilsonClover(U, dims, csw, -1)
+    psi = li.random_spinor(dims, 1, 5)
+    p3 = (prof[0], prof[1], (0, 0, 0, 0))
+    op.apply(psi, M, p3)  # builds the clover matrices outside the timing
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        op.apply(psi, M, p3)
+    dt = (time.perf_counter() - t0) / reps
+    V = int(np.prod(dims))
+    return op, {"ms_per_application": dt * 1e3, "sites_per_s": V / dt,
+                "algorithmic_gbs": V * (48 + 72 + 72) * 8 / dt / 1e9,
+                "cores": oracle.num_threads(), "kind": "oracle"}
+
+
 def _timed(fn):
     import torch
 
@@ -424,6 +447,18 @@ def config_free16(dp, ctx, args):
                      "per_slice_rel_err_vs_exact_all": slice_err(cpp, gold, 15),
                      "effective_mass_0_7": meff}
     dp.dp_field_free(ctx, f)
+    # the CPU oracle on the whole workload (12 components, FP64 BiCGStab)
+    import oracle
+
+    op, rate = oracle_dslash_rate(li.unit_links(dims), dims, 1.7, 0.5, ("exp_t", 0.4))
+    t0 = time.perf_counter()
+    cpp_o, _, oinfo = oracle.solve_point(op, 0.5, "exp_t", 0.4, (0, 0, 0, 0), tol=1e-11)
+    to = time.perf_counter() - t0
+    res["cpu_baseline"] = {"value": 1.0 / to, "unit": "solves/s", "cores": oracle.num_threads(),
+                           "kind": "oracle", "sample": "the whole workload: one solve of all 12 "
+                           "components to r = 1e-11, %.2f s" % to,
+                           "per_slice_rel_err_vs_exact_max_to_T2": slice_err(cpp_o, gold, 8),
+                           "dslash": rate}
     return {"workload": "free theory 16x8^3 (U = 1), M = 0.5, exp_t alpha0 = 0.4, r = 1e-11",
             "reference": "exact momentum-space C_PP (tests/golden/free_16x8_M0.5.json)", **res}
 
@@ -442,6 +477,10 @@ def config_light64(dp, ctx, args):
     dims = (64, 32, 32, 32)
     U = li.su3_links(dims, 0.5, 7)
     f = dp.dp_field_load(ctx, U, dims, -1)
+    # the CPU oracle's operator at this volume (a full solve of one RHS of
+    # the light quark takes minutes on the host; the application rate is the
+    # reported baseline)
+    _, oracle_rate = oracle_dslash_rate(U, dims, 1.9, 0.005, ("cosh_4d", 0.2), reps=2)
     del U
     dp.dp_field_set_csw(ctx, f, 1.9)
     prec = args.prec if args.prec != "mixed_fp32" else "mixed_fp16"
@@ -502,7 +541,7 @@ def config_light64(dp, ctx, args):
     return {"workload": "light-quark solves 64x32^3 (eps 0.5, seed 7, c_sw 1.9), r = 1e-10",
             "sap_gcr": sap_rows,
             "inner": "%s (%s) in FP64 defect correction" % (prec, LINKS[prec]), "solves": rows,
-            "per_slice_checked": checked}
+            "per_slice_checked": checked, "cpu_oracle_dslash": oracle_rate}
 
 
 def config_multimass32(dp, ctx, args):
@@ -514,11 +553,30 @@ def config_multimass32(dp, ctx, args):
 
     import lattice_inputs as li
 
+    import oracle
+
     dims = (32, 16, 16, 16)
-    f = dp.dp_field_load(ctx, li.su3_links(dims, 0.4, 3), dims, -1)
+    U = li.su3_links(dims, 0.4, 3)
+    f = dp.dp_field_load(ctx, U, dims, -1)
     dp.dp_field_set_csw(ctx, f, 1.7)
     Ms = [0.01, 0.1, 0.5, 0.8]
     profs = [heavy_or_light(M) for M in Ms]
+    # the CPU oracle on a bounded sample: its operator at this volume, and
+    # one full solve of one RHS (component 0, the heavy mass 0.5) to the
+    # workload's residue, scaled to one mass x 12 RHS
+    op, rate = oracle_dslash_rate(U, dims, 1.7, 0.5, heavy_or_light(0.5))
+    del U
+    hp = heavy_or_light(0.5)
+    al = oracle.profile_alpha(hp[0], hp[1], dims, (3, 5, 7, 9))
+    eta = oracle.point_sources(dims, (3, 5, 7, 9), al[0][3] * al[1][5] * al[2][7] * al[3][9])[:1]
+    t0 = time.perf_counter()
+    _, oit, _, _ = op.solve(eta, 0.5, (hp[0], hp[1], (3, 5, 7, 9)), tol=1e-10)
+    to = time.perf_counter() - t0
+    del op
+    cpu = {"value": 1.0 / (12 * to), "unit": "solves/s (one mass x 12 RHS)",
+           "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "one full oracle BiCGStab solve of 1 of the 12 RHS of M = 0.5 to r = 1e-10 "
+                     "(%.1f s, %d iterations), x 12" % (to, int(oit[0])), "dslash": rate}
     out = torch.zeros(4 * 32, dtype=torch.float64, device="cuda")
     src = (3, 5, 7, 9)
     res = {}
@@ -564,7 +622,8 @@ def config_multimass32(dp, ctx, args):
                       "note": "inputs %d MB > 129 MB L2 only in part at this volume" % (nb >> 20)}
     dp.dp_field_free(ctx, f)
     return {"workload": "multi-mass 32x16^3 (eps 0.4, seed 3), 12 RHS x 4 masses in one batch, "
-                        "r = 1e-10", "masses": Ms, "profiles": [list(p) for p in profs], **res}
+                        "r = 1e-10", "masses": Ms, "profiles": [list(p) for p in profs],
+            "cpu_baseline": cpu, **res}
 
 
 def config_sf48(dp, ctx, args):
