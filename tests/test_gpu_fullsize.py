@@ -10,7 +10,8 @@ T/2 at the 1e-6 tolerance of the solved correlators, through the C ABI.
   light-quark profile cosh-4d alpha0 in {0.2, 0.4}, FP16-stored links in the
   FP32 inner solver, r = 1e-10.  The steepening profile leaves the far slices
   wrong under the global residue alone; the library's per-slice check must
-  bring them within tolerance.
+  bring them within tolerance;
+* the serving path on the 48x24^3 and 64x32^3 fields at once.
 
 The references (tests/golden/, written by make_golden.py from the oracle
 only) are full-lattice FP64 BiCGStab solves to 1e-13 whose per-slice
@@ -83,3 +84,38 @@ def test_light_64x32_matches_stored_oracle(ctx, alpha0):
     assert info["status"] == 0, info
     assert slice_rel(cpp, np.asarray(m["cpp"]), dims[0] // 2) < 1e-6
     dp.dp_field_free(ctx, f)
+
+
+def test_served_48x24_and_64x32_match_stored_oracle(ctx):
+    """The serving path at the two large volumes of the serving mix, both
+    fields resident and their batches running at once: the 48x24^3 heavy
+    quark (M = 0.5, cosh-t alpha0 = 0.4) and the 64x32^3 light quark
+    (M = 0.005 with the serving mix's light profile, cosh-4d alpha0 = 0.2),
+    origin sources, r = 1e-10 and the default per-slice target; C_PP against
+    the stored oracle results at 1e-6 per slice out to T/2."""
+    gh = _load("cpp_48x24_M0.5_cosh0.4.json")
+    gl = _load("cpp_64x32_M0.005.json")
+    ml = gl["masses"][0]
+    fields = []
+    for g in (gh, gl):
+        dims = tuple(g["dims"])
+        U = li.su3_links(dims, g["eps"], g["seed"])
+        f = dp.dp_field_load(ctx, U, dims, g["bc_t"])
+        del U
+        dp.dp_field_set_csw(ctx, f, g["csw"])
+        fields.append((f, dims))
+    dp.dp_serve_start(ctx, 0, 12)
+    try:
+        th = dp.dp_submit(ctx, fields[0][0], gh["M"], ("cosh_t", 0.4), (0, 0, 0, 0), 1e-10)
+        tl = dp.dp_submit(ctx, fields[1][0], ml["M"], ("cosh_4d", 0.2), (0, 0, 0, 0), 1e-10)
+        cpp_h, ih = dp.dp_wait(ctx, th, fields[0][1][0], timeout_s=600, allow=())
+        cpp_l, il = dp.dp_wait(ctx, tl, fields[1][1][0], timeout_s=600, allow=())
+        st = dp.dp_serve_stats_get(ctx)
+    finally:
+        dp.dp_serve_stop(ctx, 1)
+    assert ih["status"] == 0 and il["status"] == 0, (ih, il)
+    assert st["completed"] == 2
+    assert slice_rel(cpp_h, np.asarray(gh["cpp"]), fields[0][1][0] // 2) < 1e-6
+    assert slice_rel(cpp_l, np.asarray(ml["cpp"]), fields[1][1][0] // 2) < 1e-6
+    for f, _ in fields:
+        dp.dp_field_free(ctx, f)
