@@ -4,9 +4,9 @@
 // products are summed in FP32 over the sites one thread visits (24 terms a
 // site, a few tens of sites: one packed f32x2 add per site and value, where
 // an FP64 add per site would run on GB300's 1/64-rate FP64 pipe) and across
-// threads and blocks in FP64 per RHS; the reductions and scalar recurrences
-// are those of the FP64 kernels (reduce.cuh), so every decision stays per
-// RHS.
+// threads and blocks in FP64 per RHS; the reductions and the scalar
+// recurrences (those the FP64 kernels share, and the shadow-form BiCGStab's
+// own) are in reduce.cuh, so every decision stays per RHS.
 //
 // A pair is processed while either of its RHS is active; an inactive lane's
 // solution x is never changed (lane blend), and its terms are excluded from

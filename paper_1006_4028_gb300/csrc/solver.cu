@@ -9,9 +9,11 @@
 //      read as a relative L2 norm on the preconditioned system): an FP64
 //      defect-correction loop (true Schur residual in FP64 every round) around
 //      an inner solver in FP32 (mixed precision) or FP64 (plain): BiCGStab
-//      (the FP32 one with the p update fused into the x, r pass), CG on the
-//      normal equations, or GCR preconditioned by the Schwarz alternating
-//      procedure (sap.cu);
+//      (the FP32 one in shadow form: rhat' = Mhat^dag rhat once per inner
+//      solve, so its inner products ride in the passes that form s and p and
+//      in the dslash launch that forms t, and the p update in the x, r
+//      pass), CG on the normal equations, or GCR preconditioned by the
+//      Schwarz alternating procedure (sap.cu);
 //   4. x_o = A_oo^-1 (eta'_o - D_oe x_e);
 //   5. restore S = S'/alpha_B per site and contract C_PP(y0) (Sec. II eq.
 //      backcorrection; Sec. III: restore before contracting).
