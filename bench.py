@@ -10,15 +10,18 @@ inside the FP64 defect-correction loop, then odd-site reconstruction, 1/alpha
 restore and the C_PP contraction.  Each step uses a new seeded random source
 site.  Metric: solves/s (higher is better).
 
-Also reported: the dslash roofline (HBM) of the dominant kernel from CUDA
-events around every dslash launch (recorded in the timed region itself with
---graphs 0; with CUDA-graph iterations, the default, in a pass of three
-solves without graphs right after it), the plain single-RHS FP64 GPU solver
-on the same workload, the end-to-end number through the host-buffer C-ABI
-call, the CPU oracle baseline (a timed full oracle solve of one of the 12
-right-hand sides), the cost of the library's per-slice accuracy check
-against the paper's global stopping rule alone, and the SM clocks seen
-during the timed region.
+Also reported: the dslash roofline (HBM) of the dominant kernel, its
+A^-1 D launch with all 12 RHS active timed with CUDA events on the
+launching stream right after the timed region (the same launches inside the
+solve beside it, from CUDA events around every dslash launch of a pass
+without graphs), with the DRAM traffic of a stored ncu capture of that
+launch shape, labelled as such; the plain single-RHS FP64 GPU solver on the
+same workload; the end-to-end number through the host-buffer C-ABI call;
+the CPU oracle baseline (a timed full oracle solve of one of the 12
+right-hand sides); the cost of the library's per-slice accuracy check
+against the paper's global stopping rule alone; the double-float outer
+residual; the four-field serving stream (p50/p99 against FP64 plain); and
+the SM clocks seen during the timed region.
 
 --gpus N without a torchrun environment starts N local ranks itself (one
 per GPU, torch.distributed.run on 127.0.0.1); each rank runs an independent
