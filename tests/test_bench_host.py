@@ -32,3 +32,21 @@ def test_tune_cache_round_trip(tmp_path):
     bench.save_tune_cache("none", {"x": [1, 2, 3]})
     assert not os.path.exists("none")
     assert bench.load_tune_cache("none") == {}
+
+
+def test_oracle_operator_timing_reports_rate():
+    """The per-workload CPU baseline helper: one timed full-lattice (D+M)
+    application of the oracle on a small lattice, with its rate and the
+    operator it built (reused by the workloads' timed oracle solves)."""
+    import lattice_inputs as li
+
+    dims = (4, 4, 4, 4)
+    op, rate = bench.oracle_dslash_rate(li.su3_links(dims, 0.3, 1), dims, 1.7, 0.5,
+                                        ("cosh_t", 0.4), reps=1)
+    assert rate["kind"] == "oracle" and rate["cores"] >= 1
+    assert rate["ms_per_application"] > 0
+    V = 4 ** 4
+    assert math.isclose(rate["sites_per_s"], V / (rate["ms_per_application"] / 1e3), rel_tol=1e-9)
+    assert math.isclose(rate["algorithmic_gbs"],
+                        V * 192 * 8 / (rate["ms_per_application"] / 1e3) / 1e9, rel_tol=1e-9)
+    assert op.dims == dims
