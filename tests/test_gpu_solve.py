@@ -333,3 +333,26 @@ def test_full_size_48x24_solve_matches_stored_oracle(ctx):
     assert info["status"] == 0 and info["true_rel_residue"] < 1e-11
     assert slice_rel(cpp, g["cpp"], dims[0] // 2) < 1e-6
     dp.dp_field_free(ctx, f)
+
+
+@pytest.mark.parametrize("M,prof", [(0.5, ("cosh_t", 0.4)), (0.1, ("cosh_4d", 0.2)),
+                                    (0.5, ("none", 0.0))])
+def test_fp32_bicgstab_iterations_track_fp64(ctx, M, prof):
+    """The FP32 inner BiCGStab in shadow form (rhat' = Mhat^dag rhat once per
+    inner solve; <t, s> and |t|^2 summed in the x - A^-1 D epilogue) makes
+    the iterates of the FP64 BiCGStab in exact arithmetic, so at a residue
+    one inner solve reaches long before FP32 rounding matters (r = 1e-4)
+    their iteration counts agree.  A wrong inner product would cost
+    iterations, not accuracy (the FP64 outer loop corrects the answer), so
+    the parity tests alone would not see it."""
+    dims = (16, 8, 8, 8)
+    f = dp.dp_field_load(ctx, field(dims, 0.3, 2), dims, -1)
+    dp.dp_field_set_csw(ctx, f, 1.7)
+    its = {}
+    for prec in ("mixed_fp32", "fp64"):
+        o = {"prec": prec, "batched": 1, "use_graph": 0, "slice_tol": -1.0}
+        _, _, info = dp.dp_solve_point(ctx, f, M, prof, (0, 0, 0, 0), 1e-4, o, T=dims[0])
+        assert info["status"] == 0 and info["iters_outer"] == 1, (prec, info)
+        its[prec] = info["iters_inner"]
+    assert abs(its["mixed_fp32"] - its["fp64"]) <= 1, its
+    dp.dp_field_free(ctx, f)
